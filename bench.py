@@ -1,0 +1,266 @@
+"""Benchmark of the two-body macro-ion PIC step on GB300.
+
+Workload (default): the 3D neutral medium -- 512 x 256 x 256 cells,
+dx = lambda/16, 8 two-body ions per cell over x cells [4, 508) (y, z
+periodic, x open), thermal momenta sigma = 1e-3, omega_b = 3, n_b = 0.02 n_c,
+a0 = 1e-3 Gaussian pulse with waist 6 lambda: 264,241,152 ions.  A step is the
+whole hot path: re-sort check, B half step, gather + internal force + Boris
++ drift + Esirkepov deposit, current-box sum with the antenna, B half step,
+E step with Mur faces.
+
+Metric: two-body ion pushes per second (ions x steps / time), whole job.
+One JSON line on rank 0.  Multi-GPU: independent replicas (the step is not
+sharded across GPUs), weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/fwd ratio"
+UNIT = "ion-pushes/s"
+
+
+def workload_cfg2():
+    from paper_2208_08038_gb300 import synth
+    wl = synth.cfg2_neutral_3d(build_particles=False)
+    m = wl.meta
+    n_ion = m["ppc"] * (m["hi"][0] - m["lo"][0]) * (m["hi"][1] - m["lo"][1]) * (m["hi"][2] - m["lo"][2])
+    return wl, n_ion
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_cfg2(seconds_target: float = 10.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: a
+    32^3-cell periodic box with the workload's dx, dt, ppc, momenta and
+    omega_b (262,144 ions), timed over whole steps."""
+    import oracle as O
+    from paper_2208_08038_gb300 import synth
+    n = (32, 32, 32)
+    wl = synth.cfg2_neutral_3d(n=n, margin=0)
+    wl.bc = (0, 0, 0)
+    sp = wl.species[0]
+    s = O.Sim(3, n, wl.dx, wl.dt, wl.bc)
+    sid = s.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    s.load(sid, sp.x, sp.u)
+    t0 = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t0
+    k = max(1, min(20, int(seconds_target / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    s.step(k)
+    el = time.perf_counter() - t0
+    s.close()
+    threads = 1  # the particle loop is serial; field loops use OpenMP only above 65,536 cells
+    return {"value": len(sp.x) * k / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"32^3-cell periodic box of the 3D workload ({len(sp.x)} ions, 8/cell), {k} steps, FP64"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    base = cpu_baseline_cfg2(seconds_target=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    # bounded sample per step, the whole run within minutes
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg2_neutral_3d sample", "sample": base["sample"]},
+            "cpu_baseline": {k: base[k] for k in ("kind", "cores", "sample", "value", "unit")},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="sorted", choices=["sorted", "atomic"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_
+
+    from paper_2208_08038_gb300 import binding as B
+    from paper_2208_08038_gb300 import build_lib
+    if not os.path.exists(B.LIB_PATH):
+        build_lib.build()
+
+    wl, n_ion = workload_cfg2()
+    mode = B.BP_DEPOSIT_SORTED if args.mode == "sorted" else B.BP_DEPOSIT_ATOMIC
+    stream = torch.cuda.current_stream()
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=mode, tile=wl.tile)
+    sp = wl.species[0]
+    m = wl.meta
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    ctx.set_medium(sid, m["lo"], m["hi"], m["ppc"], m["seed"] + rank, m["sigma_u"])
+    for L in wl.lasers:
+        ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    ctx.step(args.warmup)
+    ctx.sync()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.time_push(True)
+    launches0 = ctx.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    ctx.sync()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.kernel_launches() - launches0
+    push_ms, push_n = ctx.push_time()
+    ctx.time_push(False)
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: every step's result (the
+    # E_y field) is read back to pinned host memory; inputs need no upload per
+    # step, the initial state is already resident (h2d 0)
+    e2e = None
+    if args.e2e_steps > 0:
+        nx, ny, nz = wl.n
+        host = torch.empty(nx * ny * nz, dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.step(1)
+            B.lib().bp_read_field(ctx._h, B.EY, B._ptr(host.data_ptr()), 0)
+        ctx.sync()
+        el = time.perf_counter() - t0
+        e2e = {"value": n_ion * args.e2e_steps / el * world, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": nx * ny * nz * 4}
+
+    hbm, src = peaks()
+    # algorithmic bytes of one push launch: every ion's state read and written
+    # (2 x 52 B: cell, 3 offsets, r, u1, u2), E and B read once (24 B/cell),
+    # J written once (12 B/cell)
+    alg = n_ion * 104 + (wl.n[0] * wl.n[1] * wl.n[2]) * 36
+    push_avg = push_ms / max(push_n, 1)
+    achieved = alg / (push_avg * 1e-3) / 1e9
+    value = n_ion * args.steps / (ms * 1e-3) * world
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cfg2_neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
+                               f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, "
+                               f"{args.mode} deposit", "l2": "inputs larger than L2 (particles 13.7 GB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_push<3,sorted>",
+                     "peak_source": src, "push_ms_per_launch": push_avg},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_cfg2()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

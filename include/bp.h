@@ -1,0 +1,193 @@
+/*
+ * bp.h -- C ABI of the GB300 two-body macro-ion particle-in-cell step.
+ *
+ * Method: An, Chen, Sheng, Zhang, "Modeling of bound electron effects in
+ * particle-in-cell simulation" (arXiv 2208.08038).  A partially ionised
+ * macro-ion is a two-body particle: a nucleus (q1, m1) and a combined bound
+ * electron (q2, m2) joined by a modified Coulomb force (Sec. 2).  Each step
+ * gathers the Yee-staggered E and B at both bodies, Boris-pushes both under
+ * the external fields plus the internal field, deposits the charge-conserving
+ * (Esirkepov, quadratic shape) current and advances Maxwell's equations with
+ * Yee FDTD.  Every step runs in the library's own sm_103a kernels.
+ *
+ * Units are normalised: c = 1, lengths in 1/k0 (lambda0 = 2 pi), times in
+ * 1/omega0, E in m_e c omega0 / e (so a0 = |E|), B in m_e omega0 / e,
+ * densities in n_c, charges in e, masses in m_e.
+ *
+ * Memory: the context owns its device buffers and obtains them through the
+ * caller's allocator (or cudaMalloc when none is given).  Every array passed
+ * in is owned by the caller and is only read during the call; every
+ * destination is owned by the caller.  Host pointers unless a function says
+ * otherwise.  Row-major ("[n][3]" = three consecutive values per item).
+ *
+ * Errors: every function returns a bp_status.  Nothing crosses the ABI as an
+ * exception.  Kernels report problems through a device status word that
+ * bp_sync() returns; bp_last_error() gives a message for the last failure.
+ *
+ * Concurrency: a context is used by one host thread at a time; all its work
+ * is issued on the stream given to bp_create.
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_ctx bp_ctx;
+
+typedef enum {
+  BP_OK = 0,
+  BP_ERR_ARG = -1,       /* invalid argument */
+  BP_ERR_OOM = -2,       /* the allocator returned NULL */
+  BP_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+  BP_ERR_CFL = -4,       /* dt violates the Courant limit or omega_b dt >= 2 */
+  BP_ERR_NONFINITE = -5, /* a non-finite momentum was produced */
+  BP_ERR_DOMAIN = -6,    /* a particle left the region its tile can handle */
+  BP_ERR_TIMEOUT = -7,   /* a bounded device wait gave up */
+  BP_ERR_IO = -8,        /* save/load file error or checksum mismatch */
+  BP_ERR_STATE = -9      /* call not valid in the current state */
+} bp_status;
+
+enum { BP_PERIODIC = 0, BP_OPEN = 1 };
+enum { BP_DEPOSIT_ATOMIC = 0, BP_DEPOSIT_SORTED = 1 };
+enum { BP_TWO_BODY = 0, BP_FREE = 1 };
+enum { BP_EX = 0, BP_EY, BP_EZ, BP_BX, BP_BY, BP_BZ, BP_JX, BP_JY, BP_JZ };
+
+/* Device memory provider.  alloc(bytes, stream, user) returns device memory
+ * usable on `stream` or NULL; free(ptr, stream, user) releases it.  Both are
+ * called only from bp_create, bp_add_*, bp_load_particles, bp_set_*,
+ * bp_forward_ckpt and bp_destroy -- never from bp_step. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, void *stream, void *user);
+  void *user;
+} bp_allocator;
+
+/* Grid.  The simulated axes are x, (y), (z); Yee stagger: E_x at (i+1/2, j, k),
+ * E_y at (i, j+1/2, k), E_z at (i, j, k+1/2), B_x at (i, j+1/2, k+1/2), B_y at
+ * (i+1/2, j, k+1/2), B_z at (i+1/2, j+1/2, k); J with E.  Open axes use Mur
+ * first-order absorbing faces on the tangential E; periodic axes wrap.
+ * n[a] must be a multiple of tile[a]. */
+typedef struct {
+  int dims;           /* 1, 2 or 3 */
+  int64_t n[3];       /* cells per axis (1 on unused axes) */
+  double dx[3];       /* cell size per axis */
+  double dt;          /* time step; must satisfy dt < 1/sqrt(sum 1/dx^2) */
+  int boundary[3];    /* BP_PERIODIC or BP_OPEN per axis */
+  int deposit_mode;   /* BP_DEPOSIT_ATOMIC (FP32 shared atomics) or
+                         BP_DEPOSIT_SORTED (integer fixed point: bit-exact reruns) */
+  int tile[3];        /* cells per tile per axis; 0 picks 64 / 32x32 / 8x8x8 */
+} bp_grid_desc;
+
+/* Species.  BP_TWO_BODY follows Sec. 2: q2 = -Zb, m2 = Zb, q1 = qc - q2,
+ * m1 = mc - m2; omega_b[i] is the natural frequency of parameter index i,
+ * mapped to the softening a_c by w_c^2 = |q1 q2| kappa / (m_r a_c^3)
+ * (Sec. 3.1), kappa = r_e 2 pi / lambda0_m.  BP_FREE is a single body of
+ * charge q and mass m.  weight: each macro-particle adds q * weight * S to
+ * the charge density, S the quadratic shape (sums to 1). */
+typedef struct {
+  int kind;
+  double Zb, qc, mc;
+  double q, m;
+  double weight;
+  double lambda0_m;
+  const double *omega_b; /* [n_omega], copied */
+  int n_omega;
+} bp_species_desc;
+
+/* Laser launched by a current sheet on the x node plane ia: a sheet K
+ * radiates E = -K/2 on either side, so J = -(2/dx) f(t, y, z) (times
+ * cos(theta) for comp = 2) launches f forward, with
+ *   f = a0 env(tau) prof(y, z) sin(omega tau + phase),  tau = t - (y - yc) sin(theta),
+ *   env = exp(-2 ln2 (tau - t0)^2 / fwhm^2)            (fwhm > 0: intensity FWHM)
+ *       = sin^2(pi tau / (2 ramp)) for 0 < tau < ramp, 1 after, 0 before  (fwhm = 0)
+ *   prof = exp(-(((y - yc) cos(theta))^2 + (z - zc)^2) / waist^2)  (waist > 0), else 1.
+ * comp 1 drives J_y (p-polarised in the x-y plane), comp 2 drives J_z. */
+typedef struct {
+  int comp;
+  double a0, omega, theta, waist, fwhm, t0, ramp, phase;
+  int64_t ia;
+  double yc, zc;
+} bp_laser_desc;
+
+/* Create a context on the calling thread's current CUDA device.  stream is
+ * a cudaStream_t (NULL: legacy default stream).  allocator may be NULL. */
+int bp_create(const bp_grid_desc *grid, const bp_allocator *allocator, void *stream, bp_ctx **out);
+void bp_destroy(bp_ctx *ctx);
+const char *bp_last_error(const bp_ctx *ctx);
+
+int bp_add_species(bp_ctx *ctx, const bp_species_desc *desc, int *species_id);
+
+/* Load macro-particles from host arrays: ion positions x [n][dims] and
+ * momenta u = p/(m c) [n][3] (NULL: at rest), parameter index per ion
+ * param_idx [n] (NULL: all 0).  Two-body ions get the initial conditions of
+ * Sec. 2: r1 = r2 = x, p1 + p2 = p_c, q1 v1 + q2 v2 = 0 (u1 = u2 = u for
+ * neutral ions; non-relativistic split otherwise).  Particles are then
+ * sorted by tile.  May be called once per species. */
+int bp_load_particles(bp_ctx *ctx, int species_id, const double *x, const double *u,
+                      const int32_t *param_idx, int64_t n);
+
+/* Generate a medium on the device: ppc ions per cell over the cell box
+ * [lo, hi), at seeded uniform in-cell positions and Gaussian momenta of
+ * standard deviation sigma_u per component, with the counter-based
+ * SplitMix64 streams that the input module of this package also implements
+ * (ion g = cell rank * ppc + p takes uniforms 3g+a and normals 3g+a). */
+int bp_set_medium(bp_ctx *ctx, int species_id, const int64_t lo[3], const int64_t hi[3], int ppc,
+                  uint64_t seed, double sigma_u);
+
+int bp_add_laser(bp_ctx *ctx, const bp_laser_desc *laser);
+
+/* Probe: records field component comp (BP_EX..BP_JZ) at the given linear
+ * node indices (i + nx (j + ny k)) after every step, up to capacity samples. */
+int bp_add_probe(bp_ctx *ctx, int comp, const int64_t *nodes, int64_t npts, int64_t capacity,
+                 int *probe_id);
+
+/* Advance n_steps leapfrog steps (asynchronous on the context stream):
+ *   B^n = B^{n-1/2} - dt/2 curl E^n; gather; internal field; Boris; drift;
+ *   J^{n+1/2} (Esirkepov + antenna); B^{n+1/2}; E^{n+1} = E^n + dt (curl B - J). */
+int bp_step(bp_ctx *ctx, int64_t n_steps);
+
+/* Wait for the stream and return the device status word as a bp_status. */
+int bp_sync(bp_ctx *ctx);
+
+/* Copy field component comp (nz*ny*nx floats, x fastest) to dst: a device
+ * pointer when on_device != 0, else a host pointer.  Synchronous. */
+int bp_read_field(bp_ctx *ctx, int comp, float *dst, int on_device);
+
+/* Overwrite field component comp from src (nz*ny*nx floats; device pointer
+ * when on_device != 0).  Synchronous.  Used to start from given fields. */
+int bp_write_field(bp_ctx *ctx, int comp, const float *src, int on_device);
+
+/* Copy up to cap samples of probe probe_id ([samples][npts] floats) to host
+ * dst; *n receives the number of samples recorded. */
+int bp_read_probe(bp_ctx *ctx, int probe_id, float *dst, int64_t cap, int64_t *n);
+
+/* Copy the bodies' states to host arrays in load order: x1, x2 positions
+ * [n][3] (simulated axes reduced to the box for periodic axes; body 2 at
+ * x1 - r), u1, u2 [n][3]; *n receives the number alive.  Any pointer may be
+ * NULL.  Free particles fill x1, u1 only. */
+int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, double *u1, double *u2,
+                      int64_t cap, int64_t *n);
+
+/* Gauss-law residual R = div E - rho at every node, in FP64 on the device
+ * (rho deposited in FP64 from the stored FP32 positions with the quadratic
+ * shape).  dst holds nz*ny*nx doubles (device pointer if on_device). */
+int bp_residual(bp_ctx *ctx, double *dst, int on_device);
+
+/* Number of own-kernel launches issued since creation (for accounting). */
+int64_t bp_kernel_launches(const bp_ctx *ctx);
+
+/* Per-kernel CUDA-event timing of the push/deposit launches: when enabled,
+ * bp_step records events around each push launch; bp_push_time returns
+ * the summed milliseconds and launch count since the last reset. */
+int bp_time_push(bp_ctx *ctx, int enable);
+int bp_push_time(bp_ctx *ctx, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BP_H */

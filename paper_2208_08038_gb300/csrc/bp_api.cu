@@ -1,0 +1,724 @@
+// bp_api.cu -- the C ABI (include/bp.h): context, species set-up (species
+// split and a_c mapping of arXiv 2208.08038 Sec. 2 / Sec. 3.1, initial
+// conditions of Sec. 2), and the step schedule on the caller's stream.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bp_internal.cuh"
+
+int sort_scan_blocks(const GridP &g);
+int sort_launches();
+
+namespace {
+
+const double R_E = 2.8179403262e-15;  // classical electron radius [m]
+
+struct Species {
+  SpecP sp;
+  PartP p;
+  long long n = 0;       // particles loaded (before any removal)
+  bool loaded = false;
+  bool has_pidx = false;
+  std::vector<double> omega;
+};
+
+struct Probe {
+  int comp;
+  long long npts, cap, count;
+  long long *nodes;
+  float *buf;
+};
+
+}  // namespace
+
+struct bp_ctx {
+  GridP g;
+  int det = 1;
+  bp_allocator alloc{};
+  bool have_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  float *F[9] = {};
+  float *jbox = nullptr;
+  unsigned char *occ = nullptr;
+  float *frame = nullptr;
+  int *status = nullptr;
+  std::vector<Species> sp;
+  std::vector<LaserP> las;
+  std::vector<Probe> pr;
+  SortBufs sb{};
+  long long sort_cap = 0;  // particles the sort scratch can hold
+  long long step = 0;
+  long long launches = 0;
+  double *rho = nullptr;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double push_ms = 0.0;
+  long long push_launches = 0;
+  std::vector<void *> owned;
+  std::string err;
+  float jscale = 0.0f, jinv = 0.0f;
+};
+
+namespace {
+
+int fail(bp_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(bp_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, BP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dalloc(bp_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (c->have_alloc) {
+    p = c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    c->owned.push_back(p);
+    cudaMemsetAsync(p, 0, bytes, c->stream);
+  }
+  return p;
+}
+
+void dfree(bp_ctx *c, void *p) {
+  if (!p) return;
+  auto it = std::find(c->owned.begin(), c->owned.end(), p);
+  if (it != c->owned.end()) c->owned.erase(it);
+  if (c->have_alloc) c->alloc.free(p, (void *)c->stream, c->alloc.user);
+  else cudaFree(p);
+}
+
+int check_launch(bp_ctx *c, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return BP_OK;
+}
+
+// fixed-point scale of the sorted deposit: a power of two such that one
+// particle's largest contribution (|q w| max(1, dx/dt)) maps to about 2^40
+void update_jscale(bp_ctx *c) {
+  if (!c->det) {
+    c->jscale = c->jinv = 0.0f;
+    return;
+  }
+  double B = 0.0, f = 1.0;
+  for (int a = 0; a < c->g.D; ++a) f = std::max(f, c->g.dxd[a] / c->g.dtd);
+  for (auto &s : c->sp) B = std::max({B, std::fabs(s.sp.q1d * s.sp.wd), std::fabs(s.sp.q2d * s.sp.wd)});
+  if (B <= 0) B = 1.0;
+  int k = 40 - (int)std::ceil(std::log2(B * f));
+  k = std::max(-100, std::min(100, k));
+  c->jscale = std::ldexp(1.0f, k);
+  c->jinv = std::ldexp(1.0f, -k);
+}
+
+// FP64 position (normalised length) to (cell, FP32 offset in [0, 1))
+void to_cell(double x, double dx, int &cell, float &f) {
+  double X = x / dx;
+  double fl = std::floor(X);
+  f = (float)(X - fl);
+  cell = (int)fl;
+  if (f >= 1.0f) {
+    f = 0.0f;
+    cell += 1;
+  }
+}
+
+int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
+  const int D = c->g.D;
+  const bool two = s.sp.kind == BP_TWO_BODY;
+  long long cap = std::max(1LL, n);
+  PartP &p = s.p;
+  p.cap = cap;
+  p.cell = (int *)dalloc(c, sizeof(int) * cap);
+  p.off = (float *)dalloc(c, sizeof(float) * D * cap);
+  p.u1 = (float *)dalloc(c, sizeof(float) * 3 * cap);
+  p.id = (int *)dalloc(c, sizeof(int) * cap);
+  p.tstart = (int *)dalloc(c, sizeof(int) * (c->g.ntiles + 1));
+  if (two) {
+    p.r = (float *)dalloc(c, sizeof(float) * 3 * cap);
+    p.u2 = (float *)dalloc(c, sizeof(float) * 3 * cap);
+  } else {
+    p.r = p.u2 = nullptr;
+  }
+  p.pidx = pidx ? (int *)dalloc(c, sizeof(int) * cap) : nullptr;
+  if (!p.cell || !p.off || !p.u1 || !p.id || !p.tstart || (two && (!p.r || !p.u2)) || (pidx && !p.pidx))
+    return fail(c, BP_ERR_OOM, "particle arrays (%lld particles)", n);
+  // sort scratch, shared by all species
+  const int nf = D + (two ? 9 : 3);
+  if (!c->sb.hist) {
+    c->sb.hist = (int *)dalloc(c, sizeof(int) * (c->g.ncell + 1));
+    c->sb.bsum = (int *)dalloc(c, sizeof(int) * (sort_scan_blocks(c->g) + 4));
+    if (!c->sb.hist || !c->sb.bsum) return fail(c, BP_ERR_OOM, "sort scratch");
+  }
+  long long need_f = (long long)(D + 9) * cap;
+  if (cap > c->sort_cap) {
+    dfree(c, c->sb.tmp_cell);
+    dfree(c, c->sb.tmp_f);
+    dfree(c, c->sb.tmp_i);
+    c->sb.tmp_cell = (int *)dalloc(c, sizeof(int) * cap);
+    c->sb.tmp_f = (float *)dalloc(c, sizeof(float) * need_f);
+    c->sb.tmp_i = (int *)dalloc(c, sizeof(int) * 2 * cap);
+    if (!c->sb.tmp_cell || !c->sb.tmp_f || !c->sb.tmp_i) return fail(c, BP_ERR_OOM, "sort buffers");
+    c->sort_cap = cap;
+  }
+  (void)nf;
+  return BP_OK;
+}
+
+// one-time full sort after a load: mark every particle as living in tile 0
+// (tstart[ntiles] = n) and run the sort pipeline
+int initial_sort(bp_ctx *c, Species &s, long long n) {
+  std::vector<int> ts(c->g.ntiles + 1, 0);
+  ts[c->g.ntiles] = (int)n;
+  cudaMemcpyAsync(s.p.tstart, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice, c->stream);
+  launch_set_sort_flag(c->status, c->stream);
+  launch_sort(c->g, s.sp, s.p, c->sb, c->status, c->stream);
+  launch_clear_sort_flag(c->status, c->stream);
+  c->launches += 2 + sort_launches();
+  return check_launch(c, "initial sort");
+}
+
+}  // namespace
+
+extern "C" {
+
+int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_ctx **out) {
+  if (!gd || !out) return BP_ERR_ARG;
+  *out = nullptr;
+  bp_ctx *c = new bp_ctx();
+  GridP &g = c->g;
+  memset(&g, 0, sizeof g);
+  const int D = gd->dims;
+  if (D < 1 || D > 3) {
+    delete c;
+    return BP_ERR_ARG;
+  }
+  g.D = D;
+  static const int def_tile[4][3] = {{1, 1, 1}, {64, 1, 1}, {32, 32, 1}, {8, 8, 8}};
+  static const int def_margin[4] = {0, 8, 2, 1};
+  g.M = def_margin[D];
+  double inv2 = 0.0;
+  long long ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      if (gd->n[a] < 4 || gd->dx[a] <= 0) {
+        delete c;
+        return BP_ERR_ARG;
+      }
+      g.n[a] = (int)gd->n[a];
+      g.bc[a] = gd->boundary[a] == BP_OPEN ? BP_OPEN : BP_PERIODIC;
+      g.dxd[a] = gd->dx[a];
+      g.L[a] = gd->tile[a] > 0 ? gd->tile[a] : def_tile[D][a];
+      if (g.n[a] % g.L[a] != 0 || g.L[a] < g.M + 3) {
+        delete c;
+        return BP_ERR_ARG;
+      }
+      inv2 += 1.0 / (gd->dx[a] * gd->dx[a]);
+      g.og[a] = g.M + 2;
+      g.gb[a] = g.L[a] + 2 * g.M + 5;
+      g.oj[a] = g.M + 3;
+      g.jb[a] = g.L[a] + 2 * g.M + 7;
+    } else {
+      g.n[a] = 1;
+      g.bc[a] = BP_PERIODIC;
+      g.dxd[a] = 1.0;
+      g.L[a] = 1;
+      g.og[a] = 0;
+      g.gb[a] = 1;
+      g.oj[a] = 0;
+      g.jb[a] = 1;
+    }
+    g.dx[a] = (float)g.dxd[a];
+    g.idx[a] = (float)(1.0 / g.dxd[a]);
+    g.nt[a] = g.n[a] / g.L[a];
+    ncell *= g.n[a];
+  }
+  if (!(gd->dt > 0) || gd->dt * std::sqrt(inv2) >= 1.0) {
+    delete c;
+    return BP_ERR_CFL;
+  }
+  if (ncell >= (1LL << 31) - 1) {
+    delete c;
+    return BP_ERR_ARG;
+  }
+  g.dtd = gd->dt;
+  g.dt = (float)gd->dt;
+  g.ncell = ncell;
+  g.ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+  g.cpt = g.L[0] * g.L[1] * g.L[2];
+  g.gcells = g.gb[0] * g.gb[1] * g.gb[2];
+  g.jcells = g.jb[0] * g.jb[1] * g.jb[2];
+  c->det = gd->deposit_mode == BP_DEPOSIT_ATOMIC ? 0 : 1;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  if (al && al->alloc && al->free) {
+    c->alloc = *al;
+    c->have_alloc = true;
+  }
+  for (int k = 0; k < 9; ++k) {
+    c->F[k] = (float *)dalloc(c, sizeof(float) * ncell);
+    if (!c->F[k]) {
+      bp_destroy(c);
+      return BP_ERR_OOM;
+    }
+  }
+  c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
+  c->occ = (unsigned char *)dalloc(c, g.ntiles);
+  c->status = (int *)dalloc(c, sizeof(int) * 4);
+  long long nf = frame_floats(g);
+  c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
+  if (!c->jbox || !c->occ || !c->status || (nf && !c->frame)) {
+    bp_destroy(c);
+    return BP_ERR_OOM;
+  }
+  if (push_prepare(g, 0) || push_prepare(g, 1)) {
+    bp_destroy(c);
+    return BP_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    bp_destroy(c);
+    return BP_ERR_CUDA;
+  }
+  *out = c;
+  return BP_OK;
+}
+
+void bp_destroy(bp_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto e : c->ev) cudaEventDestroy(e);
+  std::vector<void *> all = c->owned;
+  for (void *p : all) dfree(c, p);
+  delete c;
+}
+
+const char *bp_last_error(const bp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int bp_add_species(bp_ctx *c, const bp_species_desc *d, int *id) {
+  if (!c || !d) return BP_ERR_ARG;
+  if ((int)c->sp.size() >= BP_MAX_SPECIES) return fail(c, BP_ERR_ARG, "too many species");
+  Species s;
+  SpecP &p = s.sp;
+  memset(&p, 0, sizeof p);
+  p.kind = d->kind == BP_FREE ? BP_FREE : BP_TWO_BODY;
+  const double dt = c->g.dtd;
+  p.wd = d->weight;
+  if (p.kind == BP_TWO_BODY) {
+    if (!(d->Zb > 0) || !(d->mc > d->Zb) || !d->omega_b || d->n_omega < 1 || !(d->lambda0_m > 0))
+      return fail(c, BP_ERR_ARG, "two-body species needs Zb > 0, mc > Zb, lambda0_m > 0, omega_b");
+    // species split (Sec. 2): q2 = -Zb e, m2 = Zb m_e, q1 = qc - q2, m1 = mc - m2
+    p.q2d = -d->Zb;
+    p.m2d = d->Zb;
+    p.q1d = d->qc - p.q2d;
+    p.m1d = d->mc - p.m2d;
+    const double kappa = R_E * 2.0 * M_PI / d->lambda0_m;
+    const double mr = p.m1d * p.m2d / (p.m1d + p.m2d);
+    std::vector<float> ac(d->n_omega);
+    for (int i = 0; i < d->n_omega; ++i) {
+      double w = d->omega_b[i];
+      if (!(w > 0)) return fail(c, BP_ERR_ARG, "omega_b must be positive");
+      // leapfrog stability of the internal oscillator
+      if (w * dt >= 2.0) return fail(c, BP_ERR_CFL, "omega_b dt = %g >= 2", w * dt);
+      // natural frequency (Sec. 3.1): w^2 = |q1 q2| kappa / (m_r ac^3)
+      ac[i] = (float)std::cbrt(std::fabs(p.q1d * p.q2d) * kappa / (mr * w * w));
+      s.omega.push_back(w);
+    }
+    p.kappa = (float)kappa;
+    p.nac = d->n_omega;
+    float *acd = (float *)dalloc(c, sizeof(float) * ac.size());
+    if (!acd) return fail(c, BP_ERR_OOM, "a_c table");
+    cudaMemcpyAsync(acd, ac.data(), sizeof(float) * ac.size(), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    p.ac = acd;
+  } else {
+    if (!(d->m > 0)) return fail(c, BP_ERR_ARG, "free species needs m > 0");
+    p.q1d = d->q;
+    p.m1d = d->m;
+    p.q2d = p.m2d = 0.0;
+  }
+  p.q1 = (float)p.q1d;
+  p.m1 = (float)p.m1d;
+  p.q2 = (float)p.q2d;
+  p.m2 = (float)p.m2d;
+  p.h1 = (float)(p.q1d * dt / (2.0 * p.m1d));
+  p.h2 = p.m2d > 0 ? (float)(p.q2d * dt / (2.0 * p.m2d)) : 0.0f;
+  p.qw1 = (float)(p.q1d * p.wd);
+  p.qw2 = (float)(p.q2d * p.wd);
+  c->sp.push_back(s);
+  update_jscale(c);
+  if (id) *id = (int)c->sp.size() - 1;
+  return BP_OK;
+}
+
+int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, const int32_t *pidx, int64_t n) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size() || n < 0 || (n > 0 && !x)) return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (s.loaded) return fail(c, BP_ERR_STATE, "species %d already loaded", sid);
+  if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
+  const GridP &g = c->g;
+  const int D = g.D;
+  const bool two = s.sp.kind == BP_TWO_BODY;
+  int rc = alloc_particles(c, s, n, pidx != nullptr);
+  if (rc) return rc;
+  s.has_pidx = pidx != nullptr;
+  const long long cap = s.p.cap;
+  std::vector<int> cell(cap, -1), id(cap, 0), pi(pidx ? cap : 0, 0);
+  std::vector<float> off((size_t)D * cap, 0.0f), u1(3 * cap, 0.0f), u2(two ? 3 * cap : 0, 0.0f);
+  const double q1 = s.sp.q1d, q2 = s.sp.q2d, m1 = s.sp.m1d, m2 = s.sp.m2d;
+  for (long long i = 0; i < n; ++i) {
+    int cc[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      float f;
+      to_cell(x[i * D + a], g.dxd[a], cc[a], f);
+      if (g.bc[a] == BP_PERIODIC) {
+        cc[a] = wrap_mod(cc[a], g.n[a]);
+      } else if (cc[a] < 0 || cc[a] >= g.n[a]) {
+        return fail(c, BP_ERR_DOMAIN, "particle %lld outside the grid", (long long)i);
+      }
+      off[(size_t)a * cap + i] = f;
+    }
+    cell[i] = cc[0] + g.n[0] * (cc[1] + g.n[1] * cc[2]);
+    id[i] = (int)i;
+    if (pidx) {
+      if (pidx[i] < 0 || (two && pidx[i] >= s.sp.nac)) return fail(c, BP_ERR_ARG, "param_idx out of range");
+      pi[i] = pidx[i];
+    }
+    for (int a = 0; a < 3; ++a) {
+      double uc = u ? u[3 * i + a] : 0.0;
+      if (!std::isfinite(uc)) return fail(c, BP_ERR_NONFINITE, "non-finite momentum of particle %lld", (long long)i);
+      if (!two) {
+        u1[a * cap + i] = (float)uc;
+      } else if (q1 + q2 == 0.0) {
+        // q1 v1 + q2 v2 = 0 with q1 = -q2 gives v1 = v2, so u1 = u2 = u_c
+        u1[a * cap + i] = (float)uc;
+        u2[a * cap + i] = (float)uc;
+      } else {
+        // p1 + p2 = p_c and q1 v1 + q2 v2 = 0, non-relativistic (u ~ v)
+        double a1 = (m1 + m2) * uc / (m1 - m2 * q1 / q2);
+        u1[a * cap + i] = (float)a1;
+        u2[a * cap + i] = (float)(-q1 * a1 / q2);
+      }
+    }
+  }
+  cudaStream_t st = c->stream;
+  cudaMemcpyAsync(s.p.cell, cell.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.p.off, off.data(), sizeof(float) * off.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.p.u1, u1.data(), sizeof(float) * u1.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.p.id, id.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
+  if (two) cudaMemcpyAsync(s.p.u2, u2.data(), sizeof(float) * u2.size(), cudaMemcpyHostToDevice, st);
+  if (pidx) cudaMemcpyAsync(s.p.pidx, pi.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
+  rc = initial_sort(c, s, n);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load");
+  if (rc) return rc;
+  s.n = n;
+  s.loaded = true;
+  return BP_OK;
+}
+
+int bp_set_medium(bp_ctx *c, int sid, const int64_t lo[3], const int64_t hi[3], int ppc, uint64_t seed,
+                  double sigma_u) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size() || !lo || !hi || ppc < 1) return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (s.loaded) return fail(c, BP_ERR_STATE, "species %d already loaded", sid);
+  const GridP &g = c->g;
+  int l[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  long long n = ppc;
+  for (int a = 0; a < g.D; ++a) {
+    if (lo[a] < 0 || hi[a] > g.n[a] || hi[a] <= lo[a]) return fail(c, BP_ERR_ARG, "bad medium box");
+    l[a] = (int)lo[a];
+    h[a] = (int)hi[a];
+    n *= (hi[a] - lo[a]);
+  }
+  if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
+  int rc = alloc_particles(c, s, n, false);
+  if (rc) return rc;
+  launch_gen_medium(g, s.sp, s.p, l, h, ppc, seed, sigma_u, 0, n, c->stream);
+  c->launches++;
+  if ((rc = check_launch(c, "medium generation"))) return rc;
+  rc = initial_sort(c, s, n);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "medium");
+  if (rc) return rc;
+  s.n = n;
+  s.loaded = true;
+  return BP_OK;
+}
+
+int bp_add_laser(bp_ctx *c, const bp_laser_desc *L) {
+  if (!c || !L) return BP_ERR_ARG;
+  if ((int)c->las.size() >= BP_MAX_LASER) return fail(c, BP_ERR_ARG, "too many lasers");
+  if ((L->comp != 1 && L->comp != 2) || L->ia < 0 || L->ia >= c->g.n[0])
+    return fail(c, BP_ERR_ARG, "laser comp must be 1 or 2 and ia inside the grid");
+  LaserP p;
+  p.comp = L->comp;
+  p.a0 = L->a0;
+  p.omega = L->omega;
+  p.theta = L->theta;
+  p.waist = L->waist;
+  p.fwhm = L->fwhm;
+  p.t0 = L->t0;
+  p.ramp = L->ramp;
+  p.phase = L->phase;
+  p.ia = (int)L->ia;
+  p.yc = L->yc;
+  p.zc = L->zc;
+  c->las.push_back(p);
+  return BP_OK;
+}
+
+int bp_add_probe(bp_ctx *c, int comp, const int64_t *nodes, int64_t npts, int64_t capacity, int *pid) {
+  if (!c || comp < 0 || comp > 8 || !nodes || npts < 1 || capacity < 1) return BP_ERR_ARG;
+  if ((int)c->pr.size() >= BP_MAX_PROBE) return fail(c, BP_ERR_ARG, "too many probes");
+  for (int64_t i = 0; i < npts; ++i)
+    if (nodes[i] < 0 || nodes[i] >= c->g.ncell) return fail(c, BP_ERR_ARG, "probe node out of range");
+  Probe p;
+  p.comp = comp;
+  p.npts = npts;
+  p.cap = capacity;
+  p.count = 0;
+  p.nodes = (long long *)dalloc(c, sizeof(long long) * npts);
+  p.buf = (float *)dalloc(c, sizeof(float) * npts * capacity);
+  if (!p.nodes || !p.buf) return fail(c, BP_ERR_OOM, "probe buffers");
+  cudaMemcpyAsync(p.nodes, nodes, sizeof(long long) * npts, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  c->pr.push_back(p);
+  if (pid) *pid = (int)c->pr.size() - 1;
+  return BP_OK;
+}
+
+int bp_step(bp_ctx *c, int64_t nsteps) {
+  if (!c || nsteps < 0) return BP_ERR_ARG;
+  const GridP &g = c->g;
+  cudaStream_t st = c->stream;
+  PushArgs A;
+  memset(&A, 0, sizeof A);
+  int nsp = 0;
+  for (auto &s : c->sp) {
+    if (!s.loaded) continue;
+    A.sp[nsp] = s.sp;
+    A.p[nsp] = s.p;
+    ++nsp;
+  }
+  A.nsp = nsp;
+  for (int k = 0; k < 3; ++k) {
+    A.E[k] = c->F[k];
+    A.B[k] = c->F[3 + k];
+  }
+  A.jbox = c->jbox;
+  A.occ = c->occ;
+  A.status = c->status;
+  A.jscale = c->jscale;
+  A.jinv = c->jinv;
+  float *E[3] = {c->F[0], c->F[1], c->F[2]}, *B[3] = {c->F[3], c->F[4], c->F[5]}, *J[3] = {c->F[6], c->F[7], c->F[8]};
+  const float *cE[3] = {E[0], E[1], E[2]}, *cB[3] = {B[0], B[1], B[2]}, *cJ[3] = {J[0], J[1], J[2]};
+  int nopen = 0;
+  for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
+  for (int64_t it = 0; it < nsteps; ++it) {
+    // re-sort when a particle left its tile margin in the previous step
+    if (nsp) {
+      for (auto &s : c->sp)
+        if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
+      launch_clear_sort_flag(c->status, st);
+      c->launches += nsp * sort_launches() + 1;
+    }
+    launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+    if (c->timing) {
+      if (c->ev_used + 2 > c->ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          cudaEventCreate(&e);
+          c->ev.push_back(e);
+        }
+      }
+      cudaEventRecord(c->ev[c->ev_used], st);
+    }
+    launch_push(g, A, st);
+    if (c->timing) {
+      cudaEventRecord(c->ev[c->ev_used + 1], st);
+      c->ev_used += 2;
+    }
+    launch_jsum(g, c->jbox, c->occ, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
+    launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+    launch_yee_e(g, E, cB, cJ, c->frame, st);
+    c->launches += 5 + (nopen ? 1 + nopen : 0);
+    c->step++;
+    for (auto &p : c->pr) {
+      if (p.count < p.cap) {
+        launch_probe(c->F[p.comp], p.nodes, p.npts, p.buf, p.count, st);
+        c->launches++;
+        p.count++;
+      }
+    }
+    int rc = check_launch(c, "step");
+    if (rc) return rc;
+  }
+  return BP_OK;
+}
+
+int bp_sync(bp_ctx *c) {
+  if (!c) return BP_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  if (c->timing && c->ev_used) {
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
+      c->push_ms += ms;
+      c->push_launches++;
+    }
+    c->ev_used = 0;
+  }
+  int st = 0;
+  e = cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status");
+  if (st & ST_NONFINITE) return fail(c, BP_ERR_NONFINITE, "non-finite momentum");
+  if (st & ST_DOMAIN) return fail(c, BP_ERR_DOMAIN, "a two-body ion left the region its tile handles or the grid");
+  if (st & ST_TIMEOUT) return fail(c, BP_ERR_TIMEOUT, "device wait timed out");
+  return BP_OK;
+}
+
+int bp_read_field(bp_ctx *c, int comp, float *dst, int on_device) {
+  if (!c || comp < 0 || comp > 8 || !dst) return BP_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(dst, c->F[comp], sizeof(float) * c->g.ncell,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "read field");
+}
+
+int bp_write_field(bp_ctx *c, int comp, const float *src, int on_device) {
+  if (!c || comp < 0 || comp > 8 || !src) return BP_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->F[comp], src, sizeof(float) * c->g.ncell,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "write field");
+}
+
+int bp_read_probe(bp_ctx *c, int pid, float *dst, int64_t cap, int64_t *n) {
+  if (!c || pid < 0 || pid >= (int)c->pr.size() || !dst) return BP_ERR_ARG;
+  Probe &p = c->pr[pid];
+  long long k = std::min<long long>(p.count, cap);
+  cudaError_t e = cudaMemcpyAsync(dst, p.buf, sizeof(float) * k * p.npts, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (n) *n = p.count;
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "read probe");
+}
+
+int bp_read_particles(bp_ctx *c, int sid, double *x1, double *x2, double *u1, double *u2, int64_t cap,
+                      int64_t *nout) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size()) return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (!s.loaded) return fail(c, BP_ERR_STATE, "species not loaded");
+  const GridP &g = c->g;
+  const int D = g.D;
+  const bool two = s.sp.kind == BP_TWO_BODY;
+  const long long pc = s.p.cap;
+  cudaStream_t st = c->stream;
+  cudaStreamSynchronize(st);
+  int cnt = 0;
+  cudaMemcpy(&cnt, s.p.tstart + g.ntiles, sizeof(int), cudaMemcpyDeviceToHost);
+  std::vector<int> cell(cnt), id(cnt);
+  std::vector<float> off((size_t)D * cnt), uu1(3 * (size_t)cnt), r(two ? 3 * (size_t)cnt : 0),
+      uu2(two ? 3 * (size_t)cnt : 0);
+  cudaMemcpy(cell.data(), s.p.cell, sizeof(int) * cnt, cudaMemcpyDeviceToHost);
+  cudaMemcpy(id.data(), s.p.id, sizeof(int) * cnt, cudaMemcpyDeviceToHost);
+  for (int a = 0; a < D; ++a)
+    cudaMemcpy(off.data() + (size_t)a * cnt, s.p.off + a * pc, sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+  for (int a = 0; a < 3; ++a) {
+    cudaMemcpy(uu1.data() + (size_t)a * cnt, s.p.u1 + a * pc, sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+    if (two) {
+      cudaMemcpy(r.data() + (size_t)a * cnt, s.p.r + a * pc, sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+      cudaMemcpy(uu2.data() + (size_t)a * cnt, s.p.u2 + a * pc, sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "read particles");
+  // alive particles, in load order
+  std::vector<std::pair<int, int>> order;
+  order.reserve(cnt);
+  for (int q = 0; q < cnt; ++q)
+    if (cell[q] >= 0) order.push_back({id[q], q});
+  std::sort(order.begin(), order.end());
+  long long k = 0;
+  for (auto &pr : order) {
+    if (k >= cap) break;
+    int q = pr.second;
+    int cc[3] = {cell[q] % g.n[0], (cell[q] / g.n[0]) % g.n[1], cell[q] / (g.n[0] * g.n[1])};
+    for (int a = 0; a < 3; ++a) {
+      double xa = a < D ? ((double)cc[a] + (double)off[(size_t)a * cnt + q]) * g.dxd[a] : 0.0;
+      if (x1) x1[3 * k + a] = xa;
+      if (two && x2) x2[3 * k + a] = xa - (double)r[(size_t)a * cnt + q];
+      if (u1) u1[3 * k + a] = uu1[(size_t)a * cnt + q];
+      if (two && u2) u2[3 * k + a] = uu2[(size_t)a * cnt + q];
+    }
+    ++k;
+  }
+  if (nout) *nout = (int64_t)order.size();
+  return BP_OK;
+}
+
+int bp_residual(bp_ctx *c, double *dst, int on_device) {
+  if (!c || !dst) return BP_ERR_ARG;
+  const GridP &g = c->g;
+  double *R = on_device ? dst : c->rho;
+  if (!R) {
+    c->rho = (double *)dalloc(c, sizeof(double) * g.ncell);
+    if (!c->rho) return fail(c, BP_ERR_OOM, "residual scratch");
+    R = c->rho;
+  }
+  cudaMemsetAsync(R, 0, sizeof(double) * g.ncell, c->stream);
+  for (auto &s : c->sp)
+    if (s.loaded) {
+      launch_rho(g, s.sp, s.p, R, c->stream);
+      c->launches++;
+    }
+  const float *E[3] = {c->F[0], c->F[1], c->F[2]};
+  launch_divE_minus(g, E, R, c->stream);
+  c->launches++;
+  int rc = check_launch(c, "residual");
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) e = cudaMemcpyAsync(dst, R, sizeof(double) * g.ncell, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "residual");
+}
+
+int64_t bp_kernel_launches(const bp_ctx *c) { return c ? c->launches : 0; }
+
+int bp_time_push(bp_ctx *c, int enable) {
+  if (!c) return BP_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  c->timing = enable != 0;
+  c->ev_used = 0;
+  c->push_ms = 0.0;
+  c->push_launches = 0;
+  return BP_OK;
+}
+
+int bp_push_time(bp_ctx *c, double *ms, int64_t *launches) {
+  if (!c) return BP_ERR_ARG;
+  if (ms) *ms = c->push_ms;
+  if (launches) *launches = c->push_launches;
+  return BP_OK;
+}
+
+}  // extern "C"

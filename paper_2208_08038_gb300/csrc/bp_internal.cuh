@@ -1,0 +1,163 @@
+// bp_internal.cuh -- internal types and device helpers of the GB300 two-body
+// PIC library.  The C ABI is include/bp.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bp.h"
+
+#define BP_MAX_SPECIES 8
+#define BP_MAX_LASER 4
+#define BP_MAX_PROBE 32
+
+// bits of the device status word
+enum { ST_NEED_SORT = 1, ST_DOMAIN = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+
+// Grid geometry as the kernels see it.  Axes >= D have n = 1, L = 1, box 1.
+struct GridP {
+  int D;
+  int n[3];
+  int bc[3];
+  float dx[3], idx[3];
+  float dt;
+  double dxd[3], dtd;
+  int L[3], nt[3];
+  int M;            // body 1 may sit up to M cells outside its tile
+  int og[3], gb[3]; // gather box: cells before the tile start, box extent
+  int oj[3], jb[3]; // current box
+  int gcells, jcells;
+  long long ncell;
+  int ntiles;
+  int cpt;          // cells per tile
+};
+
+struct SpecP {
+  int kind;                // BP_TWO_BODY / BP_FREE
+  float q1, m1, q2, m2;
+  float h1, h2;            // q dt / (2 m)
+  float qw1, qw2;          // q * weight
+  float kappa;             // r_e k0
+  const float *ac;         // softening a_c per parameter index
+  int nac;
+  double q1d, m1d, q2d, m2d, wd;
+};
+
+struct PartP {
+  int *cell;      // global linear cell of body 1 (-1: removed)
+  float *off;     // [D][cap] in-cell offset of body 1, [0, 1)
+  float *r;       // [3][cap] internal displacement r = x1 - x2 (two-body only)
+  float *u1;      // [3][cap]
+  float *u2;      // [3][cap] (two-body only)
+  int *pidx;      // parameter index (NULL: 0)
+  int *id;        // load order
+  int *tstart;    // [ntiles + 1] particle range of each tile
+  long long cap;
+};
+
+struct PushArgs {
+  int nsp;
+  SpecP sp[BP_MAX_SPECIES];
+  PartP p[BP_MAX_SPECIES];
+  const float *E[3];
+  const float *B[3];
+  float *jbox;             // [ntiles][3][jcells]
+  unsigned char *occ;      // [ntiles]
+  int *status;
+  float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
+};
+
+struct LaserP {
+  int comp;
+  double a0, omega, theta, waist, fwhm, t0, ramp, phase;
+  int ia;
+  double yc, zc;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+
+__host__ __device__ __forceinline__ int wrap_mod(int i, int n) {
+  int m = i % n;
+  return m < 0 ? m + n : m;
+}
+
+// quadratic B-spline weights for the three nodes around the nearest node,
+// xi = position - nearest node in [-1/2, 1/2)
+__device__ __forceinline__ void qweights(float xi, float w[3]) {
+  float a = 0.5f - xi, b = 0.5f + xi;
+  w[0] = 0.5f * a * a;
+  w[1] = 0.75f - xi * xi;
+  w[2] = 0.5f * b * b;
+}
+
+__device__ __forceinline__ float qshape(float x) {
+  float a = fabsf(x);
+  if (a <= 0.5f) return 0.75f - x * x;
+  if (a < 1.5f) {
+    float t = 1.5f - a;
+    return 0.5f * t * t;
+  }
+  return 0.0f;
+}
+
+// S(u + d) - S(u) for the quadratic B-spline.  When u and u + d fall on the
+// same polynomial piece the difference is formed from d directly (no
+// cancellation between two rounded shape values); otherwise directly.
+__device__ __forceinline__ float qshape_delta(float u, float d) {
+  float v = u + d;
+  float au = fabsf(u), av = fabsf(v);
+  if (au <= 0.5f && av <= 0.5f) return -d * (u + v);
+  if (u > 0.5f && v > 0.5f && u < 1.5f && v < 1.5f) return -0.5f * d * (3.0f - u - v);
+  if (u < -0.5f && v < -0.5f && u > -1.5f && v > -1.5f) return 0.5f * d * (3.0f + u + v);
+  if (au >= 1.5f && av >= 1.5f && (u > 0.0f) == (v > 0.0f)) return 0.0f;
+  return qshape(v) - qshape(u);
+}
+
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// key of stream `stream` of seed `seed`, and the counter-based draw k
+__host__ __device__ __forceinline__ uint64_t sm64_key(uint64_t seed, uint64_t stream) {
+  return sm64_mix(sm64_mix(seed) + stream * 0x9E3779B97F4A7C15ull);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint64_t k) {
+  return sm64_mix(key + (k + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+__host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t k) {
+  return (double)(sm64_draw(key, k) >> 11) * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers (host side), one translation unit each
+
+void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s);
+size_t push_smem_bytes(const GridP &g, int det);
+int push_prepare(const GridP &g, int det);
+
+void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);
+void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3],
+                  float *frame, cudaStream_t s);
+long long frame_floats(const GridP &g);
+void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, float *const J[3],
+                 const LaserP *las, int nlas, double t, cudaStream_t s);
+void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,
+                  cudaStream_t s);
+
+struct SortBufs {
+  int *hist;       // [ncell + 1]
+  int *bsum;       // scan block sums
+  int *tmp_cell;
+  float *tmp_f;    // enough floats for the largest species' float payload
+  int *tmp_i;      // pidx / id payload
+};
+void launch_sort(const GridP &g, const SpecP &sp, PartP &p, SortBufs &b, int *status, cudaStream_t s);
+void launch_clear_sort_flag(int *status, cudaStream_t s);
+void launch_set_sort_flag(int *status, cudaStream_t s);
+
+void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
+                       uint64_t seed, double sigma, long long first, long long count, cudaStream_t s);
+void launch_rho(const GridP &g, const SpecP &sp, const PartP &p, double *rho, cudaStream_t s);
+void launch_divE_minus(const GridP &g, const float *const E[3], double *R, cudaStream_t s);

@@ -1,0 +1,616 @@
+// k_push.cu -- the per-tile particle kernel: gather at both bodies, internal
+// modified-Coulomb field, relativistic Boris push of both bodies, drift and
+// Esirkepov (quadratic shape) current deposit into a shared-memory tile.
+//
+// Method: arXiv 2208.08038 Sec. 2 (two-body macro-ion, Boris equations,
+// modified Coulomb force, body currents q v / dV).  One CTA per tile:
+//   1. stage E and B of the tile plus halo in shared memory (FP32),
+//   2. push every particle of the tile (all species), accumulating the
+//      current of both bodies in a shared-memory box (tile + halo):
+//        BP_DEPOSIT_SORTED: 64-bit fixed point (integer adds are associative,
+//                           so the box is bit-identical whatever the order),
+//        BP_DEPOSIT_ATOMIC: FP32 shared atomics,
+//   3. write the box to the tile's slot of the global box array; the
+//      current-sum kernel adds the overlapping boxes of neighbouring tiles
+//      in a fixed order.
+#include <type_traits>
+
+#include "bp_internal.cuh"
+
+namespace {
+
+struct Loc {
+  int bn[3], bh[3];        // first box index of the node- / half-staggered stencil
+  float wn[3][3], wh[3][3];
+};
+
+template <int D>
+__device__ __forceinline__ void make_loc(const int d[3], const float f[3], const int og[3], Loc &L) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      int up = f[a] >= 0.5f ? 1 : 0;
+      L.bn[a] = d[a] + og[a] + up - 1;
+      qweights(f[a] - (float)up, L.wn[a]);
+      L.bh[a] = d[a] + og[a] - 1;
+      qweights(f[a] - 0.5f, L.wh[a]);
+    } else {
+      L.bn[a] = L.bh[a] = 0;
+      L.wn[a][0] = L.wh[a][0] = 1.0f;
+      L.wn[a][1] = L.wn[a][2] = L.wh[a][1] = L.wh[a][2] = 0.0f;
+    }
+  }
+}
+
+// one field component with stagger pattern PAT (bit a: half cell along a)
+// at two bodies; loads are shared when both stencils start at the same node
+template <int D, int PAT>
+__device__ __forceinline__ void gather_comp(const float *__restrict__ G, int gb0, int gb1, const Loc &A,
+                                            const Loc &Bo, float &oa, float &ob) {
+  int ba[3], bb[3];
+  const float *wa[3];
+  const float *wb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool half = (PAT >> a) & 1;
+    ba[a] = half ? A.bh[a] : A.bn[a];
+    bb[a] = half ? Bo.bh[a] : Bo.bn[a];
+    wa[a] = half ? A.wh[a] : A.wn[a];
+    wb[a] = half ? Bo.wh[a] : Bo.wn[a];
+  }
+  constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
+  const bool same = (ba[0] == bb[0]) && (D < 2 || ba[1] == bb[1]) && (D < 3 || ba[2] == bb[2]);
+  float sa = 0.0f, sb = 0.0f;
+  if (same) {
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const float *row = G + ba[0] + gb0 * ((ba[1] + j) + gb1 * (ba[2] + k));
+        float ra = 0.0f, rb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          float v = row[i];
+          ra = fmaf(wa[0][i], v, ra);
+          rb = fmaf(wb[0][i], v, rb);
+        }
+        sa = fmaf(wa[1][j] * wa[2][k], ra, sa);
+        sb = fmaf(wb[1][j] * wb[2][k], rb, sb);
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const float *ra_ = G + ba[0] + gb0 * ((ba[1] + j) + gb1 * (ba[2] + k));
+        const float *rb_ = G + bb[0] + gb0 * ((bb[1] + j) + gb1 * (bb[2] + k));
+        float ra = 0.0f, rb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          ra = fmaf(wa[0][i], ra_[i], ra);
+          rb = fmaf(wb[0][i], rb_[i], rb);
+        }
+        sa = fmaf(wa[1][j] * wa[2][k], ra, sa);
+        sb = fmaf(wb[1][j] * wb[2][k], rb, sb);
+      }
+  }
+  oa = sa;
+  ob = sb;
+}
+
+template <int D>
+__device__ __forceinline__ void gather_all(const float *G, int gcells, int gb0, int gb1, const Loc &A,
+                                           const Loc &Bo, float Ea[3], float Ba[3], float Eb[3], float Bb[3]) {
+  gather_comp<D, 1>(G + 0 * gcells, gb0, gb1, A, Bo, Ea[0], Eb[0]);
+  gather_comp<D, 2>(G + 1 * gcells, gb0, gb1, A, Bo, Ea[1], Eb[1]);
+  gather_comp<D, 4>(G + 2 * gcells, gb0, gb1, A, Bo, Ea[2], Eb[2]);
+  gather_comp<D, 6>(G + 3 * gcells, gb0, gb1, A, Bo, Ba[0], Bb[0]);
+  gather_comp<D, 5>(G + 4 * gcells, gb0, gb1, A, Bo, Ba[1], Bb[1]);
+  gather_comp<D, 3>(G + 5 * gcells, gb0, gb1, A, Bo, Ba[2], Bb[2]);
+}
+
+// relativistic Boris (Sec. 2): u- = u + hE; t = hB/gamma-; s = 2t/(1+t^2);
+// u+ = u- + (u- + u- x t) x s; u = u+ + hE
+__device__ __forceinline__ void boris(float h, const float E[3], const float B[3], float u[3]) {
+  float um0 = fmaf(h, E[0], u[0]), um1 = fmaf(h, E[1], u[1]), um2 = fmaf(h, E[2], u[2]);
+  float gi = 1.0f / sqrtf(1.0f + um0 * um0 + um1 * um1 + um2 * um2);
+  float t0 = h * B[0] * gi, t1 = h * B[1] * gi, t2 = h * B[2] * gi;
+  float sf = 2.0f / (1.0f + t0 * t0 + t1 * t1 + t2 * t2);
+  float s0 = t0 * sf, s1 = t1 * sf, s2 = t2 * sf;
+  float c0 = um0 + (um1 * t2 - um2 * t1);
+  float c1 = um1 + (um2 * t0 - um0 * t2);
+  float c2 = um2 + (um0 * t1 - um1 * t0);
+  float up0 = um0 + (c1 * s2 - c2 * s1);
+  float up1 = um1 + (c2 * s0 - c0 * s2);
+  float up2 = um2 + (c0 * s1 - c1 * s0);
+  u[0] = fmaf(h, E[0], up0);
+  u[1] = fmaf(h, E[1], up1);
+  u[2] = fmaf(h, E[2], up2);
+}
+
+// shape factors on the five-node window around the old nearest node:
+// S0[m] at the old position, DS[m] = S1[m] - S0[m], node n0 - 2 + m
+template <int D>
+__device__ __forceinline__ void window(const float f[3], const float de[3], float S0[3][5], float DS[3][5],
+                                       int n0[3], const int d[3], const int oj[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      int up = f[a] >= 0.5f ? 1 : 0;
+      float xi = f[a] - (float)up;
+      n0[a] = d[a] + oj[a] + up;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float u = xi - (float)(m - 2);
+        S0[a][m] = qshape(u);
+        DS[a][m] = qshape_delta(u, de[a]);
+      }
+    } else {
+      n0[a] = 2;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) { S0[a][m] = (m == 2) ? 1.0f : 0.0f; DS[a][m] = 0.0f; }
+    }
+  }
+}
+
+template <bool DET, typename JT>
+__device__ __forceinline__ void jadd(JT *p, float v, float scale) {
+  if (v == 0.0f) return;
+  if constexpr (DET) {
+    long long q = __float2ll_rn(v * scale);
+    if (q) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)q);
+  } else {
+    atomicAdd(p, v);
+  }
+}
+
+// Esirkepov density decomposition for NB bodies sharing one window:
+//   3D W_x = DSx (S0y S0z + (DSy S0z + S0y DSz)/2 + DSy DSz/3) (cyclic),
+//   2D W_x = DSx (S0y + DSy/2), J_z with S0x S0y + (DSx S0y + S0x DSy)/2 + DSx DSy/3,
+//   1D W_x = DSx, J_y/z with S0 + DS/2,
+// J_a on the face after node i = -qw dx_a/dt * sum_{i' <= i} W_a(i').
+template <int D, bool DET, int NB, typename JT>
+__device__ __forceinline__ void esirkepov(JT *__restrict__ J, int jcells, int jb0, int jb1, const int n0[3],
+                                          const float (*S0)[3][5], const float (*DS)[3][5], const float *qw,
+                                          const float (*v)[3], const float dxdt[3], float scale) {
+  JT *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
+  const int bx = n0[0] - 2, by = n0[1] - 2, bz = n0[2] - 2;
+  if constexpr (D == 1) {
+    float run[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        run[b] += DS[b][0][i];
+        jx += -qw[b] * dxdt[0] * run[b];
+        float sb = S0[b][0][i] + 0.5f * DS[b][0][i];
+        jy += qw[b] * v[b][1] * sb;
+        jz += qw[b] * v[b][2] * sb;
+      }
+      if (i < 4) jadd<DET>(Jx + bx + i, jx, scale);
+      jadd<DET>(Jy + bx + i, jy, scale);
+      jadd<DET>(Jz + bx + i, jz, scale);
+    }
+  } else if constexpr (D == 2) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      float fac[NB];
+      bool any = false;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        fac[b] = S0[b][1][j] + 0.5f * DS[b][1][j];
+        any |= fac[b] != 0.0f;
+      }
+      if (!any) continue;
+      float run[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float jx = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          run[b] += DS[b][0][i];
+          jx += -qw[b] * dxdt[0] * run[b] * fac[b];
+        }
+        jadd<DET>(Jx + (bx + i) + jb0 * (by + j), jx, scale);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float fac[NB];
+      bool any = false;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        fac[b] = S0[b][0][i] + 0.5f * DS[b][0][i];
+        any |= fac[b] != 0.0f;
+      }
+      if (!any) continue;
+      float run[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float jy = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          run[b] += DS[b][1][j];
+          jy += -qw[b] * dxdt[1] * run[b] * fac[b];
+        }
+        jadd<DET>(Jy + (bx + i) + jb0 * (by + j), jy, scale);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        float jz = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          float w = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
+                    (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
+          jz += qw[b] * v[b][2] * w;
+        }
+        jadd<DET>(Jz + (bx + i) + jb0 * (by + j), jz, scale);
+      }
+  } else {
+    // J_x
+#pragma unroll 1
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        float fac[NB];
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          fac[b] = S0[b][1][j] * S0[b][2][k] + 0.5f * (DS[b][1][j] * S0[b][2][k] + S0[b][1][j] * DS[b][2][k]) +
+                   (1.0f / 3.0f) * DS[b][1][j] * DS[b][2][k];
+          any |= fac[b] != 0.0f;
+        }
+        if (!any) continue;
+        float run[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float jx = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            run[b] += DS[b][0][i];
+            jx += -qw[b] * dxdt[0] * run[b] * fac[b];
+          }
+          jadd<DET>(Jx + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jx, scale);
+        }
+      }
+    // J_y
+#pragma unroll 1
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        float fac[NB];
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          fac[b] = S0[b][0][i] * S0[b][2][k] + 0.5f * (DS[b][0][i] * S0[b][2][k] + S0[b][0][i] * DS[b][2][k]) +
+                   (1.0f / 3.0f) * DS[b][0][i] * DS[b][2][k];
+          any |= fac[b] != 0.0f;
+        }
+        if (!any) continue;
+        float run[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float jy = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            run[b] += DS[b][1][j];
+            jy += -qw[b] * dxdt[1] * run[b] * fac[b];
+          }
+          jadd<DET>(Jy + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jy, scale);
+        }
+      }
+    // J_z
+#pragma unroll 1
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        float fac[NB];
+        bool any = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          fac[b] = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
+                   (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
+          any |= fac[b] != 0.0f;
+        }
+        if (!any) continue;
+        float run[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float jz = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            run[b] += DS[b][2][k];
+            jz += -qw[b] * dxdt[2] * run[b] * fac[b];
+          }
+          jadd<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jz, scale);
+        }
+      }
+  }
+}
+
+// tile-relative cell of a global cell coordinate (periodic: nearest image)
+__device__ __forceinline__ int rel_cell(const GridP &g, int a, int c, int T0) {
+  int d = c - T0;
+  if (g.bc[a] == BP_PERIODIC) {
+    if (d < -g.M) d += g.n[a];
+    else if (d >= g.L[a] + g.M) d -= g.n[a];
+  }
+  return d;
+}
+
+template <int D, bool DET, typename JT>
+__device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
+                              const float *Gsm, JT *Jsm, int *status, float scale) {
+  const long long cap = P.cap;
+  const bool two = sp.kind == BP_TWO_BODY;
+  int cell = P.cell[i];
+  if (cell < 0) return;
+  int c[3];
+  c[0] = cell % g.n[0];
+  c[1] = (cell / g.n[0]) % g.n[1];
+  c[2] = cell / (g.n[0] * g.n[1]);
+  float f[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f}, u1[3], u2[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int a = 0; a < D; ++a) f[a] = P.off[a * cap + i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u1[a] = P.u1[a * cap + i];
+  if (two) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = P.r[a * cap + i];
+      u2[a] = P.u2[a * cap + i];
+    }
+  }
+  int d[3] = {0, 0, 0}, d2[3] = {0, 0, 0};
+  float f2[3] = {0.0f, 0.0f, 0.0f};
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    d[a] = rel_cell(g, a, c[a], T0[a]);
+    bad |= (d[a] < -g.M) || (d[a] >= g.L[a] + g.M);
+    // body 2 sits at x1 - r
+    float rc = r[a] * g.idx[a];
+    bad |= !(fabsf(rc) < 1.0f);
+    float X = f[a] - rc;
+    float fl = floorf(X);
+    float fr = X - fl;
+    int di = (int)fl;
+    if (fr >= 1.0f) { fr = 0.0f; di += 1; }
+    d2[a] = d[a] + di;
+    f2[a] = fr;
+  }
+  if (bad) {
+    atomicOr(status, ST_DOMAIN);
+    return;
+  }
+  float E1[3], B1[3], E2[3], B2[3];
+  {
+    Loc L1, L2;
+    make_loc<D>(d, f, g.og, L1);
+    make_loc<D>(two ? d2 : d, two ? f2 : f, g.og, L2);
+    gather_all<D>(Gsm, g.gcells, g.gb[0], g.gb[1], L1, L2, E1, B1, E2, B2);
+  }
+  float v1[3], v2[3] = {0.0f, 0.0f, 0.0f};
+  if (two) {
+    // modified Coulomb field (Sec. 2): on the nucleus q2 kappa r / (r^2 + ac^2)^{3/2},
+    // on the bound electron -q1 kappa r / (...), r = x1 - x2
+    const int pi = P.pidx ? P.pidx[i] : 0;
+    const float ac = sp.ac[pi];
+    float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + ac * ac;
+    float s = sp.kappa / (rr * sqrtf(rr));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      E1[a] = fmaf(sp.q2 * s, r[a], E1[a]);
+      E2[a] = fmaf(-sp.q1 * s, r[a], E2[a]);
+    }
+    boris(sp.h2, E2, B2, u2);
+    float g2 = 1.0f / sqrtf(1.0f + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v2[a] = u2[a] * g2;
+  }
+  boris(sp.h1, E1, B1, u1);
+  {
+    float g1 = 1.0f / sqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v1[a] = u1[a] * g1;
+  }
+  // drift: body 1 moves in cells by dt v / dx; the internal displacement by
+  // dt (v1 - v2) on all three axes; the deposited moves are the ones the
+  // stored FP32 state actually makes
+  float fn[3] = {0.0f, 0.0f, 0.0f}, de1[3] = {0.0f, 0.0f, 0.0f}, de2[3] = {0.0f, 0.0f, 0.0f}, rn[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    fn[a] = f[a] + g.dt * v1[a] * g.idx[a];
+    de1[a] = fn[a] - f[a];
+  }
+  if (two) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      rn[a] = r[a] + g.dt * (v1[a] - v2[a]);
+      float dr = rn[a] - r[a];
+      if (a < D) de2[a] = de1[a] - dr * g.idx[a];
+    }
+  }
+  {
+    const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
+    float S0[2][3][5], DS[2][3][5];
+    float vv[2][3];
+    float qw[2] = {sp.qw1, sp.qw2};
+    int n1[3], n2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { vv[0][a] = v1[a]; vv[1][a] = v2[a]; }
+    window<D>(f, de1, S0[0], DS[0], n1, d, g.oj);
+    if (two) {
+      window<D>(f2, de2, S0[1], DS[1], n2, d2, g.oj);
+      const bool same = (n1[0] == n2[0]) && (D < 2 || n1[1] == n2[1]) && (D < 3 || n1[2] == n2[2]);
+      if (same) {
+        esirkepov<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+      } else {
+        esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+        esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
+      }
+    } else {
+      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+    }
+  }
+  // new cell of body 1.  On open axes a free particle whose cell leaves
+  // [2, n-2) is removed (after its last deposit); a two-body ion leaving the
+  // grid is a domain error.
+  bool need_sort = false, nonfinite = false, removed = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (fn[a] >= 1.0f) {
+      fn[a] -= 1.0f;
+      c[a] += 1;
+    } else if (fn[a] < 0.0f) {
+      fn[a] += 1.0f;
+      c[a] -= 1;
+      if (fn[a] >= 1.0f) { fn[a] = 0.0f; c[a] += 1; }
+    }
+    if (g.bc[a] == BP_PERIODIC) {
+      c[a] = wrap_mod(c[a], g.n[a]);
+    } else if (two) {
+      bad |= (c[a] < 0 || c[a] >= g.n[a]);
+    } else {
+      removed |= (c[a] < 2 || c[a] >= g.n[a] - 2);
+    }
+    int dn = rel_cell(g, a, c[a], T0[a]);
+    need_sort |= (dn < -g.M) || (dn >= g.L[a] + g.M);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nonfinite |= !isfinite(u1[a]) || !isfinite(u2[a]);
+  if (bad) atomicOr(status, ST_DOMAIN);
+  if (nonfinite) atomicOr(status, ST_NONFINITE);
+  if (bad || removed) {
+    P.cell[i] = -1;
+    return;
+  }
+  if (need_sort) atomicOr(status, ST_NEED_SORT);
+  P.cell[i] = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+#pragma unroll
+  for (int a = 0; a < D; ++a) P.off[a * cap + i] = fn[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) P.u1[a * cap + i] = u1[a];
+  if (two) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      P.r[a * cap + i] = rn[a];
+      P.u2[a * cap + i] = u2[a];
+    }
+  }
+}
+
+template <int D, bool DET>
+__global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A) {
+  using JT = typename std::conditional<DET, long long, float>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  JT *Jsm = reinterpret_cast<JT *>(smem);
+  float *Gsm = reinterpret_cast<float *>(smem + sizeof(JT) * 3 * (size_t)g.jcells);
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  int total = 0;
+  for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
+  if (total == 0) {
+    if (tid == 0) A.occ[t] = 0;
+    return;
+  }
+  int tc[3];
+  tc[0] = t % g.nt[0];
+  tc[1] = (t / g.nt[0]) % g.nt[1];
+  tc[2] = t / (g.nt[0] * g.nt[1]);
+  const int T0[3] = {tc[0] * g.L[0], tc[1] * g.L[1], tc[2] * g.L[2]};
+  for (int q = tid; q < 3 * g.jcells; q += bs) Jsm[q] = (JT)0;
+  // stage E, B of the tile plus halo (zero outside open faces)
+  for (int q = tid; q < g.gcells; q += bs) {
+    int b0 = q % g.gb[0], b1 = (q / g.gb[0]) % g.gb[1], b2 = q / (g.gb[0] * g.gb[1]);
+    int bidx[3] = {b0, b1, b2};
+    long long gi = 0, stride = 1;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int x = T0[a] - g.og[a] + bidx[a];
+      if (a < D) {
+        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        else ok &= (x >= 0 && x < g.n[a]);
+      }
+      gi += (long long)x * stride;
+      stride *= g.n[a];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      Gsm[cc * g.gcells + q] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
+      Gsm[(3 + cc) * g.gcells + q] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < A.nsp; ++s) {
+    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    for (long long i = beg + tid; i < end; i += bs)
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale);
+  }
+  __syncthreads();
+  float *out = A.jbox + (size_t)t * 3 * g.jcells;
+  for (int q = tid; q < 3 * g.jcells; q += bs) {
+    if constexpr (DET) out[q] = (float)((double)Jsm[q] * (double)A.jinv);
+    else out[q] = Jsm[q];
+  }
+  if (tid == 0) A.occ[t] = 1;
+}
+
+template <int D, bool DET>
+void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
+  size_t smem = push_smem_bytes(g, DET);
+  k_push<D, DET><<<g.ntiles, D == 3 ? 512 : 256, smem, s>>>(g, a);
+}
+
+template <int D, bool DET>
+int prepare_one(const GridP &g) {
+  size_t smem = push_smem_bytes(g, DET);
+  cudaError_t e = cudaFuncSetAttribute(k_push<D, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+size_t push_smem_bytes(const GridP &g, int det) {
+  return (det ? 8 : 4) * (size_t)3 * g.jcells + 4 * (size_t)6 * g.gcells;
+}
+
+int push_prepare(const GridP &g, int det) {
+  switch (g.D * 2 + (det ? 1 : 0)) {
+    case 2: return prepare_one<1, false>(g);
+    case 3: return prepare_one<1, true>(g);
+    case 4: return prepare_one<2, false>(g);
+    case 5: return prepare_one<2, true>(g);
+    case 6: return prepare_one<3, false>(g);
+    default: return prepare_one<3, true>(g);
+  }
+}
+
+void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s) {
+  const bool det = a.jscale != 0.0f;
+  switch (g.D * 2 + (det ? 1 : 0)) {
+    case 2: launch_one<1, false>(g, a, s); break;
+    case 3: launch_one<1, true>(g, a, s); break;
+    case 4: launch_one<2, false>(g, a, s); break;
+    case 5: launch_one<2, true>(g, a, s); break;
+    case 6: launch_one<3, false>(g, a, s); break;
+    default: launch_one<3, true>(g, a, s); break;
+  }
+}

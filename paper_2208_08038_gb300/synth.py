@@ -352,5 +352,5 @@ def cfg4_ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), ce
     las = [Laser(comp=1, a0=a0, fwhm=fwhm, t0=1.5 * fwhm, ia=8)]
     dt = 0.95 * dx / math.sqrt(2.0)
     return Workload("cfg4_ionized_crystal_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
-                    tile=(32, 32), free_bounds=((2.0, -1e300, -1e300), (nx - 3.0, 1e300, 1e300)),
+                    tile=(32, 32), free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
                     meta=dict(sites=st, lo=lo, hi=hi, sigma=sigma))

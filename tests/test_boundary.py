@@ -1,0 +1,51 @@
+"""The C-ABI library loads and exports every symbol include/bp.h declares
+(no compute calls: runs without a GPU)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_2208_08038_gb300 import binding, build_lib
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build_lib.build()
+
+
+def test_header_declares_the_api():
+    names = binding.header_functions()
+    for f in ["bp_create", "bp_destroy", "bp_add_species", "bp_load_particles", "bp_set_medium",
+              "bp_add_laser", "bp_add_probe", "bp_step", "bp_sync", "bp_read_field", "bp_write_field",
+              "bp_read_probe", "bp_read_particles", "bp_residual", "bp_last_error"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [f for f in binding.header_functions() if not hasattr(L, f)]
+    assert not missing, missing
+
+
+def test_library_is_sm103a_only(libpath):
+    """The fat binary carries sm_103a code (cuobjdump --list-elf lists only
+    the element names, it does not disassemble)."""
+    r = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in r.stdout
+
+
+def test_binding_signatures_cover_header():
+    assert set(binding.header_functions()) <= set(binding._SIGS)
+
+
+def test_oracle_not_imported_by_product():
+    """The product package never imports the oracle."""
+    pkg = os.path.dirname(binding.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(root, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "bp_oracle" not in txt, f
