@@ -130,18 +130,6 @@ void update_jscale(bp_ctx *c) {
   c->jinv = std::ldexp(1.0f, -k);
 }
 
-// FP64 position (normalised length) to (cell, FP32 offset in [0, 1))
-void to_cell(double x, double dx, int &cell, float &f) {
-  double X = x / dx;
-  double fl = std::floor(X);
-  f = (float)(X - fl);
-  cell = (int)fl;
-  if (f >= 1.0f) {
-    f = 0.0f;
-    cell += 1;
-  }
-}
-
 int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
   const int D = c->g.D;
   const bool two = s.sp.kind == BP_TWO_BODY;
@@ -376,59 +364,38 @@ int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, cons
   if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
   const GridP &g = c->g;
   const int D = g.D;
-  const bool two = s.sp.kind == BP_TWO_BODY;
   int rc = alloc_particles(c, s, n, pidx != nullptr);
   if (rc) return rc;
   s.has_pidx = pidx != nullptr;
-  const long long cap = s.p.cap;
-  std::vector<int> cell(cap, -1), id(cap, 0), pi(pidx ? cap : 0, 0);
-  std::vector<float> off((size_t)D * cap, 0.0f), u1(3 * cap, 0.0f), u2(two ? 3 * cap : 0, 0.0f);
-  const double q1 = s.sp.q1d, q2 = s.sp.q2d, m1 = s.sp.m1d, m2 = s.sp.m2d;
-  for (long long i = 0; i < n; ++i) {
-    int cc[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) {
-      float f;
-      to_cell(x[i * D + a], g.dxd[a], cc[a], f);
-      if (g.bc[a] == BP_PERIODIC) {
-        cc[a] = wrap_mod(cc[a], g.n[a]);
-      } else if (cc[a] < 0 || cc[a] >= g.n[a]) {
-        return fail(c, BP_ERR_DOMAIN, "particle %lld outside the grid", (long long)i);
-      }
-      off[(size_t)a * cap + i] = f;
-    }
-    cell[i] = cc[0] + g.n[0] * (cc[1] + g.n[1] * cc[2]);
-    id[i] = (int)i;
-    if (pidx) {
-      if (pidx[i] < 0 || (two && pidx[i] >= s.sp.nac)) return fail(c, BP_ERR_ARG, "param_idx out of range");
-      pi[i] = pidx[i];
-    }
-    for (int a = 0; a < 3; ++a) {
-      double uc = u ? u[3 * i + a] : 0.0;
-      if (!std::isfinite(uc)) return fail(c, BP_ERR_NONFINITE, "non-finite momentum of particle %lld", (long long)i);
-      if (!two) {
-        u1[a * cap + i] = (float)uc;
-      } else if (q1 + q2 == 0.0) {
-        // q1 v1 + q2 v2 = 0 with q1 = -q2 gives v1 = v2, so u1 = u2 = u_c
-        u1[a * cap + i] = (float)uc;
-        u2[a * cap + i] = (float)uc;
-      } else {
-        // p1 + p2 = p_c and q1 v1 + q2 v2 = 0, non-relativistic (u ~ v)
-        double a1 = (m1 + m2) * uc / (m1 - m2 * q1 / q2);
-        u1[a * cap + i] = (float)a1;
-        u2[a * cap + i] = (float)(-q1 * a1 / q2);
-      }
-    }
-  }
   cudaStream_t st = c->stream;
-  cudaMemcpyAsync(s.p.cell, cell.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(s.p.off, off.data(), sizeof(float) * off.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(s.p.u1, u1.data(), sizeof(float) * u1.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(s.p.id, id.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
-  if (two) cudaMemcpyAsync(s.p.u2, u2.data(), sizeof(float) * u2.size(), cudaMemcpyHostToDevice, st);
-  if (pidx) cudaMemcpyAsync(s.p.pidx, pi.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st);
-  rc = initial_sort(c, s, n);
+  // the caller's arrays are staged on the device in chunks and converted there
+  const long long chunk = std::min<long long>(std::max<long long>(n, 1), 1LL << 25);
+  char *stage = (char *)dalloc(c, (size_t)chunk * (sizeof(double) * (D + 3) + sizeof(int)));
+  if (!stage) return fail(c, BP_ERR_OOM, "load staging");
+  double *sx = (double *)stage;
+  double *su = sx + (size_t)chunk * D;
+  int *sp_ = (int *)(su + (size_t)chunk * 3);
+  int zero = 0;
+  cudaMemcpyAsync(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+  for (long long b = 0; b < n; b += chunk) {
+    long long k = std::min(chunk, n - b);
+    cudaMemcpyAsync(sx, x + b * D, sizeof(double) * k * D, cudaMemcpyHostToDevice, st);
+    if (u) cudaMemcpyAsync(su, u + b * 3, sizeof(double) * k * 3, cudaMemcpyHostToDevice, st);
+    if (pidx) cudaMemcpyAsync(sp_, pidx + b, sizeof(int) * k, cudaMemcpyHostToDevice, st);
+    launch_load_convert(g, s.sp, s.p, sx, u ? su : nullptr, pidx ? sp_ : nullptr, b, k, c->status, st);
+    c->launches++;
+  }
+  if ((rc = check_launch(c, "load conversion"))) return rc;
   cudaError_t e = cudaStreamSynchronize(st);
+  dfree(c, stage);
   if (e != cudaSuccess) return cuda_fail(c, e, "load");
+  int stw = 0;
+  cudaMemcpy(&stw, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (stw & ST_NONFINITE) return fail(c, BP_ERR_NONFINITE, "non-finite position or momentum in the load");
+  if (stw & ST_DOMAIN) return fail(c, BP_ERR_DOMAIN, "a particle lies outside the grid or has a bad param_idx");
+  rc = initial_sort(c, s, n);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load sort");
   if (rc) return rc;
   s.n = n;
   s.loaded = true;

@@ -159,5 +159,7 @@ void launch_set_sort_flag(int *status, cudaStream_t s);
 
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
                        uint64_t seed, double sigma, long long first, long long count, cudaStream_t s);
+void launch_load_convert(const GridP &g, const SpecP &sp, PartP &p, const double *x, const double *u, const int *pidx,
+                         long long first, long long count, int *status, cudaStream_t s);
 void launch_rho(const GridP &g, const SpecP &sp, const PartP &p, double *rho, cudaStream_t s);
 void launch_divE_minus(const GridP &g, const float *const E[3], double *R, cudaStream_t s);

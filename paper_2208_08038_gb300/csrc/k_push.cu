@@ -344,6 +344,151 @@ __device__ __forceinline__ void esirkepov(JT *__restrict__ J, int jcells, int jb
   }
 }
 
+
+// Fast path: all four positions (both bodies, before and after the move)
+// share one nearest node per axis, so the window is the three nodes around
+// it and S1 - S0 has a closed form in the move d (no cancellation):
+//   node n-1: -d (1 - 2 xi - d) / 2,  node n: -d (2 xi + d),  node n+1: d (1 + 2 xi + d) / 2
+// with xi = old position - n.  J along a simulated axis then lives on the two
+// faces inside the window.
+template <int D, bool DET, int NB, typename JT>
+__device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int jb0, int jb1, const int n[3],
+                                           const float (*xi)[3], const float (*de)[3], const float *qw,
+                                           const float (*v)[3], const float dxdt[3], float scale) {
+  float S0[NB][3][3], DS[NB][3][3], P[NB][3][2];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < D) {
+        const float x = xi[b][a], d = de[b][a];
+        qweights(x, S0[b][a]);
+        DS[b][a][0] = -0.5f * d * (1.0f - 2.0f * x - d);
+        DS[b][a][1] = -d * (2.0f * x + d);
+        DS[b][a][2] = 0.5f * d * (1.0f + 2.0f * x + d);
+        P[b][a][0] = DS[b][a][0];
+        P[b][a][1] = DS[b][a][0] + DS[b][a][1];
+      } else {
+        S0[b][a][0] = S0[b][a][2] = 0.0f;
+        S0[b][a][1] = 1.0f;
+        DS[b][a][0] = DS[b][a][1] = DS[b][a][2] = 0.0f;
+        P[b][a][0] = P[b][a][1] = 0.0f;
+      }
+    }
+  JT *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
+  const int bx = n[0] - 1, by = n[1] - 1, bz = n[2] - 1;
+  float cq[NB][3];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cq[b][a] = -qw[b] * dxdt[a];
+  if constexpr (D == 1) {
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      float jx = 0.0f;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0], P[b][0][f], jx);
+      jadd<DET>(Jx + bx + f, jx, scale);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float jy = 0.0f, jz = 0.0f;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        float sb = S0[b][0][i] + 0.5f * DS[b][0][i];
+        jy = fmaf(qw[b] * v[b][1], sb, jy);
+        jz = fmaf(qw[b] * v[b][2], sb, jz);
+      }
+      jadd<DET>(Jy + bx + i, jy, scale);
+      jadd<DET>(Jz + bx + i, jz, scale);
+    }
+  } else if constexpr (D == 2) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        float jx = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0] * P[b][0][f], S0[b][1][j] + 0.5f * DS[b][1][j], jx);
+        jadd<DET>(Jx + (bx + f) + jb0 * (by + j), jx, scale);
+      }
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float jy = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) jy = fmaf(cq[b][1] * P[b][1][g], S0[b][0][i] + 0.5f * DS[b][0][i], jy);
+        jadd<DET>(Jy + (bx + i) + jb0 * (by + g), jy, scale);
+      }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float jz = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          float w = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
+                    (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
+          jz = fmaf(qw[b] * v[b][2], w, jz);
+        }
+        jadd<DET>(Jz + (bx + i) + jb0 * (by + j), jz, scale);
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float F[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          F[b] = S0[b][1][j] * S0[b][2][k] + 0.5f * (DS[b][1][j] * S0[b][2][k] + S0[b][1][j] * DS[b][2][k]) +
+                 (1.0f / 3.0f) * DS[b][1][j] * DS[b][2][k];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          float jx = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0] * P[b][0][f], F[b], jx);
+          jadd<DET>(Jx + (bx + f) + jb0 * ((by + j) + jb1 * (bz + k)), jx, scale);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float F[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          F[b] = S0[b][0][i] * S0[b][2][k] + 0.5f * (DS[b][0][i] * S0[b][2][k] + S0[b][0][i] * DS[b][2][k]) +
+                 (1.0f / 3.0f) * DS[b][0][i] * DS[b][2][k];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          float jy = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) jy = fmaf(cq[b][1] * P[b][1][g], F[b], jy);
+          jadd<DET>(Jy + (bx + i) + jb0 * ((by + g) + jb1 * (bz + k)), jy, scale);
+        }
+      }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float F[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          F[b] = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
+                 (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float jz = 0.0f;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) jz = fmaf(cq[b][2] * P[b][2][h], F[b], jz);
+          jadd<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + h)), jz, scale);
+        }
+      }
+  }
+}
+
 // tile-relative cell of a global cell coordinate (periodic: nearest image)
 __device__ __forceinline__ int rel_cell(const GridP &g, int a, int c, int T0) {
   int d = c - T0;
@@ -354,9 +499,45 @@ __device__ __forceinline__ int rel_cell(const GridP &g, int a, int c, int T0) {
   return d;
 }
 
+
+// general case (a position changes nearest node, or the bodies straddle a
+// node boundary): five-node windows per body; kept out of line so the fast
+// path keeps its registers
+template <int D, bool DET, typename JT>
+__device__ __noinline__ void general_deposit(JT *Jsm, const GridP &g, const float *f, const float *de1, const int *d,
+                                             const float *f2, const float *de2, const int *d2, bool two, float qw1,
+                                             float qw2, const float *v1, const float *v2, float scale) {
+  const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
+  float S0[2][3][5], DS[2][3][5];
+  float vv[2][3];
+  float qw[2] = {qw1, qw2};
+  int n1[3], n2[3];
+  float fa[3], fb[3], da[3], db[3];
+  int ia[3], ib[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    vv[0][a] = v1[a];
+    vv[1][a] = v2[a];
+    fa[a] = f[a]; fb[a] = f2[a]; da[a] = de1[a]; db[a] = de2[a]; ia[a] = d[a]; ib[a] = d2[a];
+  }
+  window<D>(fa, da, S0[0], DS[0], n1, ia, g.oj);
+  if (two) {
+    window<D>(fb, db, S0[1], DS[1], n2, ib, g.oj);
+    const bool same = (n1[0] == n2[0]) && (D < 2 || n1[1] == n2[1]) && (D < 3 || n1[2] == n2[2]);
+    if (same) {
+      esirkepov<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+    } else {
+      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
+    }
+  } else {
+    esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+  }
+}
+
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
-                              const float *Gsm, JT *Jsm, int *status, float scale) {
+                              const float *Gsm, JT *Jsm, int *status, float scale, int *qbuf, int *qn, int qmax) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   int cell = P.cell[i];
@@ -447,27 +628,47 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       if (a < D) de2[a] = de1[a] - dr * g.idx[a];
     }
   }
-  {
-    const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
-    float S0[2][3][5], DS[2][3][5];
-    float vv[2][3];
-    float qw[2] = {sp.qw1, sp.qw2};
-    int n1[3], n2[3];
+  const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
+  // fast path when every position keeps one nearest node per axis
+  bool fast = true;
+  float xi[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+  int nn[3] = {2, 2, 2};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { vv[0][a] = v1[a]; vv[1][a] = v2[a]; }
-    window<D>(f, de1, S0[0], DS[0], n1, d, g.oj);
+  for (int a = 0; a < D; ++a) {
+    const float u1p = f[a] >= 0.5f ? 1.0f : 0.0f;
+    xi[0][a] = f[a] - u1p;
+    const float x1n = xi[0][a] + de1[a];
+    fast &= (x1n >= -0.5f) && (x1n < 0.5f);
+    nn[a] = d[a] + g.oj[a] + (int)u1p;
     if (two) {
-      window<D>(f2, de2, S0[1], DS[1], n2, d2, g.oj);
-      const bool same = (n1[0] == n2[0]) && (D < 2 || n1[1] == n2[1]) && (D < 3 || n1[2] == n2[2]);
-      if (same) {
-        esirkepov<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
-      } else {
-        esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
-        esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
-      }
-    } else {
-      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+      const float u2p = f2[a] >= 0.5f ? 1.0f : 0.0f;
+      xi[1][a] = f2[a] - u2p;
+      const float x2n = xi[1][a] + de2[a];
+      fast &= (d2[a] == d[a]) && (u2p == u1p) && (x2n >= -0.5f) && (x2n < 0.5f);
     }
+  }
+  if (!fast && qbuf) {
+    int slot = atomicAdd(qn, 1);
+    if (slot < qmax) {
+      qbuf[slot] = (int)i;  // redone by the whole block after the main pass
+      return;
+    }
+  }
+  if (fast) {
+    float qw[2] = {sp.qw1, sp.qw2};
+    float vv[2][3];
+    float dd[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vv[0][a] = v1[a];
+      vv[1][a] = v2[a];
+      dd[0][a] = de1[a];
+      dd[1][a] = de2[a];
+    }
+    if (two) esirkepov3<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], nn, xi, dd, qw, vv, dxdt, scale);
+    else esirkepov3<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], nn, xi, dd, qw, vv, dxdt, scale);
+  } else {
+    general_deposit<D, DET, JT>(Jsm, g, f, de1, d, f2, de2, d2, two, sp.qw1, sp.qw2, v1, v2, scale);
   }
   // new cell of body 1.  On open axes a free particle whose cell leaves
   // [2, n-2) is removed (after its last deposit); a two-body ion leaving the
@@ -559,12 +760,22 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
   }
   __syncthreads();
+  constexpr int QMAX = 512;
+  __shared__ int qbuf[QMAX];
+  __shared__ int qn;
   for (int s = 0; s < A.nsp; ++s) {
+    if (tid == 0) qn = 0;
+    __syncthreads();
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
     for (long long i = beg + tid; i < end; i += bs)
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale);
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qbuf, &qn, QMAX);
+    __syncthreads();
+    // particles leaving their node: general five-node window, compacted
+    const int nq = min(qn, QMAX);
+    for (int k = tid; k < nq; k += bs)
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], qbuf[k], T0, Gsm, Jsm, A.status, A.jscale, nullptr, nullptr, 0);
+    __syncthreads();
   }
-  __syncthreads();
   float *out = A.jbox + (size_t)t * 3 * g.jcells;
   for (int q = tid; q < 3 * g.jcells; q += bs) {
     if constexpr (DET) out[q] = (float)((double)Jsm[q] * (double)A.jinv);

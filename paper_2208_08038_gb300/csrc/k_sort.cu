@@ -307,6 +307,70 @@ __global__ void k_divE(GridP g, const float *Ex, const float *Ey, const float *E
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// load: FP64 ion positions / momenta (caller's layout, staged on the device)
+// to the particle arrays.  Initial conditions of Sec. 2: both bodies at the
+// ion position (r = 0); u1 = u2 = u_c for neutral ions, else the
+// non-relativistic solution of p1 + p2 = p_c, q1 v1 + q2 v2 = 0.
+
+__global__ void k_load_convert(GridP g, SpecP sp, PartP p, const double *x, const double *u, const int *pidx,
+                               long long first, long long count, int *status) {
+  const long long cap = p.cap;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long o = first + q;
+    int cell[3] = {0, 0, 0};
+    bool bad = false, nonfinite = false;
+    for (int a = 0; a < g.D; ++a) {
+      double xa = x[q * g.D + a];
+      nonfinite |= !isfinite(xa);
+      double X = xa / g.dxd[a];
+      double fl = floor(X);
+      float f = (float)(X - fl);
+      long long ci = (long long)fl;
+      if (f >= 1.0f) { f = 0.0f; ci += 1; }
+      if (g.bc[a] == BP_PERIODIC) {
+        long long m = ci % g.n[a];
+        ci = m < 0 ? m + g.n[a] : m;
+      } else if (ci < 0 || ci >= g.n[a]) {
+        bad = true;
+        ci = 0;
+      }
+      cell[a] = (int)ci;
+      p.off[a * cap + o] = f;
+    }
+    int pi = 0;
+    if (pidx) {
+      pi = pidx[q];
+      if (pi < 0 || (sp.kind == BP_TWO_BODY && pi >= sp.nac)) { bad = true; pi = 0; }
+      p.pidx[o] = pi;
+    }
+    for (int a = 0; a < 3; ++a) {
+      double uc = u ? u[q * 3 + a] : 0.0;
+      nonfinite |= !isfinite(uc);
+      if (sp.kind != BP_TWO_BODY) {
+        p.u1[a * cap + o] = (float)uc;
+      } else {
+        double u1, u2;
+        if (sp.q1d + sp.q2d == 0.0) {
+          u1 = u2 = uc;
+        } else {
+          u1 = (sp.m1d + sp.m2d) * uc / (sp.m1d - sp.m2d * sp.q1d / sp.q2d);
+          u2 = -sp.q1d * u1 / sp.q2d;
+        }
+        p.u1[a * cap + o] = (float)u1;
+        p.u2[a * cap + o] = (float)u2;
+        p.r[a * cap + o] = 0.0f;
+      }
+    }
+    p.cell[o] = (bad || nonfinite) ? -1 : cell[0] + g.n[0] * (cell[1] + g.n[1] * cell[2]);
+    p.id[o] = (int)o;
+    if (bad) atomicOr(status, ST_DOMAIN);
+    if (nonfinite) atomicOr(status, ST_NONFINITE);
+  }
+}
+
 }  // namespace
 
 void launch_sort(const GridP &g, const SpecP &sp, PartP &p, SortBufs &b, int *status, cudaStream_t s) {
@@ -344,4 +408,9 @@ void launch_rho(const GridP &g, const SpecP &sp, const PartP &p, double *rho, cu
 
 void launch_divE_minus(const GridP &g, const float *const E[3], double *R, cudaStream_t s) {
   k_divE<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, E[0], E[1], E[2], R);
+}
+
+void launch_load_convert(const GridP &g, const SpecP &sp, PartP &p, const double *x, const double *u, const int *pidx,
+                         long long first, long long count, int *status, cudaStream_t s) {
+  k_load_convert<<<blocks_for(count, 256), 256, 0, s>>>(g, sp, p, x, u, pidx, first, count, status);
 }
