@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "bp_oracle.c"), os.path.join(_HERE, "bp_oracle_adj.c")]
+_SRC = [os.path.join(_HERE, "bp_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -95,18 +95,20 @@ def _declare(L: C.CDLL) -> None:
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    if hasattr(L, "ora_create"):
-        _declare_adjoint(L)
-
-
-def _declare_adjoint(L: C.CDLL) -> None:
-    sig = {
+    adj = {
+        "or_dshape": (_d, [_d]),
+        "or_boris_adj": (None, [_d, _d, _d, _p, _p, _p, _p, _p, _p, _p]),
+        "or_internal_field_adj": (_d, [_d, _d, _d, _p, _p, _p]),
+        "or_gather_adj": (None, [_p, _p, _p, _p, _p, _p, _p]),
+        "or_deposit_adj": (None, [_p, _d, _p, _p, _p, _p, _p, _p, _p]),
+        "or_yee_b_adj": (None, [_p, _d, _p, _p]),
+        "or_yee_e_adj": (None, [_p, _p, _p, _p, _p]),
         "ora_create": (_p, [_p, _i]),
         "ora_destroy": (None, [_p]),
         "ora_forward": (_d, [_p, _i, _i, _p, _p, _i64]),
         "ora_backward": (None, [_p, _p, _p]),
     }
-    for name, (res, args) in sig.items():
+    for name, (res, args) in adj.items():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
@@ -296,3 +298,98 @@ class Sim:
         out = np.zeros(nx * ny * nz)
         self._L.or_residual(self._s, _ptr(out))
         return out.reshape(nz, ny, nx)
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+
+def _ptrs3(arrs):
+    """C array of three double* for a list of three float64 arrays."""
+    P = (C.c_void_p * 3)(*[a.ctypes.data for a in arrs])
+    return P
+
+
+def boris_adj(q, m, dt, E, B, u0, ubn):
+    E, B, u0, ubn = f64(E), f64(B), f64(u0), f64(ubn)
+    ub0, Eb, Bb = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().or_boris_adj(q, m, dt, _ptr(E), _ptr(B), _ptr(u0), _ptr(ubn), _ptr(ub0), _ptr(Eb), _ptr(Bb))
+    return ub0, Eb, Bb
+
+
+def internal_field_adj(q_other, kappa, ac, d, Eb):
+    d, Eb = f64(d), f64(Eb)
+    db = np.zeros(3)
+    acb = lib().or_internal_field_adj(q_other, kappa, ac, _ptr(d), _ptr(Eb), _ptr(db))
+    return db, acb
+
+
+def dshape(x: float) -> float:
+    return lib().or_dshape(float(x))
+
+
+class Adjoint:
+    """Forward run with stored states, then the discrete reverse pass."""
+
+    def __init__(self, sim: "Sim", sid: int):
+        self.sim = sim
+        self._o = lib().ora_create(sim._s, sid)
+
+    def forward(self, nsteps: int, pid: int, target: np.ndarray) -> tuple:
+        target = f64(target)
+        npts = target.shape[1]
+        out = np.zeros((nsteps, npts))
+        L = lib().ora_forward(self._o, nsteps, pid, _ptr(target), _ptr(out), npts)
+        return L, out
+
+    def backward(self, nac: int, n: int):
+        go = np.zeros(nac)
+        gx = np.zeros((n, 3))
+        lib().ora_backward(self._o, _ptr(go), _ptr(gx))
+        return go, gx
+
+    def close(self):
+        if self._o:
+            lib().ora_destroy(self._o)
+            self._o = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gather_adj(sim: "Sim", x, Eb, Bb, FEb=None, FBb=None):
+    x, Eb, Bb = f64(list(x) + [0.0] * (3 - len(x))), f64(Eb), f64(Bb)
+    xb = np.zeros(3)
+    pe = _ptrs3(FEb) if FEb is not None else None
+    pb = _ptrs3(FBb) if FBb is not None else None
+    lib().or_gather_adj(sim._s, _ptr(x), _ptr(Eb), _ptr(Bb), pe, pb, _ptr(xb))
+    return xb
+
+
+def deposit_adj(sim: "Sim", qw, X0, X1, v, lam):
+    X0 = f64(list(X0) + [0.0] * (3 - len(X0)))
+    X1 = f64(list(X1) + [0.0] * (3 - len(X1)))
+    v = f64(v)
+    lam = [f64(l).ravel() for l in lam]
+    X0b, X1b, vb = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().or_deposit_adj(sim._s, qw, _ptr(X0), _ptr(X1), _ptr(v), _ptrs3(lam), _ptr(X0b), _ptr(X1b), _ptr(vb))
+    return X0b, X1b, vb
+
+
+def yee_b_adj(sim: "Sim", h, Eb, Bb):
+    Eb = [f64(a).ravel().copy() for a in Eb]
+    Bb = [f64(a).ravel() for a in Bb]
+    lib().or_yee_b_adj(sim._s, h, _ptrs3(Eb), _ptrs3(Bb))
+    return Eb
+
+
+def yee_e_adj(sim: "Sim", G, Bb):
+    G = [f64(a).ravel().copy() for a in G]
+    Bb = [f64(a).ravel().copy() for a in Bb]
+    n = G[0].size
+    Hn = [np.zeros(n) for _ in range(3)]
+    Jb = [np.zeros(n) for _ in range(3)]
+    lib().or_yee_e_adj(sim._s, _ptrs3(G), _ptrs3(Hn), _ptrs3(Bb), _ptrs3(Jb))
+    return Hn, Bb, Jb

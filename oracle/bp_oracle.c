@@ -782,3 +782,511 @@ void or_residual(const or_sim *s, double *R) {
         R[id] = div - R[id];
       }
 }
+
+/* ======================================================================== */
+/* Discrete adjoint (reverse mode) of the step above, FP64.                 */
+/*                                                                          */
+/* Loss: L = sum over recorded probe samples of (p - target)^2.  The        */
+/* reverse pass runs the forward steps backwards, each operator replaced by */
+/* its transpose (linear operators) or its vector-Jacobian product          */
+/* (gather, internal force, Boris, drift, Esirkepov), from states stored    */
+/* during the forward run.  Parameters: the bound-electron frequency of     */
+/* every parameter index (through a_c of Sec. 3.1) and the initial ion      */
+/* positions (both bodies start at the ion position, Sec. 2).               */
+/* Restriction: one two-body species, no free particles.                   */
+/* ======================================================================== */
+
+/* derivative of the quadratic B-spline */
+double or_dshape(double x) {
+  double a = fabs(x);
+  if (a <= 0.5) return -2.0 * x;
+  if (a < 1.5) return (x > 0 ? -1.0 : 1.0) * (1.5 - a);
+  return 0.0;
+}
+
+/* reverse of or_boris: given ubar_new (adjoint of the pushed momentum),
+ * return ubar_old, Ebar, Bbar (adjoints of the inputs) */
+void or_boris_adj(double q, double m, double dt, const double E[3], const double B[3], const double u0[3],
+                  const double ubn[3], double ub0[3], double Eb[3], double Bb[3]) {
+  double h = q * dt / (2.0 * m);
+  double um[3], t[3], sv[3], c1[3];
+  for (int a = 0; a < 3; ++a) um[a] = u0[a] + h * E[a];
+  double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+  for (int a = 0; a < 3; ++a) t[a] = h * B[a] / gm;
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  for (int a = 0; a < 3; ++a) sv[a] = 2.0 * t[a] / (1.0 + t2);
+  c1[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+  c1[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+  c1[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+  double upb[3], umb[3], cb[3], sb[3], tb[3];
+  for (int a = 0; a < 3; ++a) { upb[a] = ubn[a]; Eb[a] = h * ubn[a]; }
+  /* up = um + c1 x s:  um += upb;  c1b = s x upb;  sb = upb x c1 */
+  for (int a = 0; a < 3; ++a) umb[a] = upb[a];
+  cb[0] = sv[1] * upb[2] - sv[2] * upb[1];
+  cb[1] = sv[2] * upb[0] - sv[0] * upb[2];
+  cb[2] = sv[0] * upb[1] - sv[1] * upb[0];
+  sb[0] = upb[1] * c1[2] - upb[2] * c1[1];
+  sb[1] = upb[2] * c1[0] - upb[0] * c1[2];
+  sb[2] = upb[0] * c1[1] - upb[1] * c1[0];
+  /* c1 = um + um x t:  umb += cb + t x cb;  tb = cb x um */
+  umb[0] += cb[0] + (t[1] * cb[2] - t[2] * cb[1]);
+  umb[1] += cb[1] + (t[2] * cb[0] - t[0] * cb[2]);
+  umb[2] += cb[2] + (t[0] * cb[1] - t[1] * cb[0]);
+  tb[0] = cb[1] * um[2] - cb[2] * um[1];
+  tb[1] = cb[2] * um[0] - cb[0] * um[2];
+  tb[2] = cb[0] * um[1] - cb[1] * um[0];
+  /* s = 2 t / (1 + t^2) */
+  double ts = t[0] * sb[0] + t[1] * sb[1] + t[2] * sb[2];
+  for (int a = 0; a < 3; ++a) tb[a] += 2.0 * sb[a] / (1.0 + t2) - 4.0 * t[a] * ts / ((1.0 + t2) * (1.0 + t2));
+  /* t = h B / gm */
+  double gmb = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    Bb[a] = h * tb[a] / gm;
+    gmb -= h * B[a] * tb[a] / (gm * gm);
+  }
+  /* gm = sqrt(1 + um^2) */
+  for (int a = 0; a < 3; ++a) umb[a] += um[a] * gmb / gm;
+  /* um = u0 + h E */
+  for (int a = 0; a < 3; ++a) {
+    ub0[a] = umb[a];
+    Eb[a] += h * umb[a];
+  }
+}
+
+/* reverse of the internal field: out = q_other kappa d / (|d|^2 + ac^2)^{3/2};
+ * given its adjoint Eb, add the adjoint of d to db and return the one of ac */
+double or_internal_field_adj(double q_other, double kappa, double ac, const double d[3], const double Eb[3],
+                             double db[3]) {
+  double rho = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + ac * ac;
+  double p32 = pow(rho, -1.5), p52 = pow(rho, -2.5);
+  double ed = Eb[0] * d[0] + Eb[1] * d[1] + Eb[2] * d[2];
+  for (int a = 0; a < 3; ++a) db[a] += q_other * kappa * (Eb[a] * p32 - 3.0 * ed * d[a] * p52);
+  return -3.0 * q_other * kappa * ed * ac * p52;
+}
+
+/* reverse of interp(): field adjoint Fb += weights * gb; returns dE/dX . gb
+ * per axis in Xb (cell units) */
+static void interp_adj(const or_sim *s, const double *F, double *Fb, const double st[3], const double X[3], double gb,
+                       double Xb[3]) {
+  long base[3];
+  int cnt[3];
+  double w[3][3], dw[3][3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < s->D) {
+      double Y = X[a] - st[a];
+      long nn = (long)floor(Y + 0.5);
+      double xi = Y - (double)nn;
+      base[a] = nn - 1;
+      cnt[a] = 3;
+      for (int m = 0; m < 3; ++m) {
+        w[a][m] = or_shape(xi - (double)(m - 1));
+        dw[a][m] = or_dshape(xi - (double)(m - 1));
+      }
+    } else {
+      base[a] = 0; cnt[a] = 1; w[a][0] = 1.0; dw[a][0] = 0.0;
+    }
+  }
+  for (int k = 0; k < cnt[2]; ++k)
+    for (int j = 0; j < cnt[1]; ++j)
+      for (int i = 0; i < cnt[0]; ++i) {
+        long id = lin(s, base[0] + i, base[1] + j, base[2] + k);
+        if (id < 0) continue;
+        if (Fb) Fb[id] += w[0][i] * w[1][j] * w[2][k] * gb;
+        double f = F[id] * gb;
+        Xb[0] += dw[0][i] * w[1][j] * w[2][k] * f;
+        if (s->D >= 2) Xb[1] += w[0][i] * dw[1][j] * w[2][k] * f;
+        if (s->D >= 3) Xb[2] += w[0][i] * w[1][j] * dw[2][k] * f;
+      }
+}
+
+/* reverse of gather(): Eb, Bb adjoints of the gathered fields at x;
+ * accumulates the field adjoints FEb, FBb (may be NULL) and xb */
+void or_gather_adj(const or_sim *s, const double x[3], const double Eb[3], const double Bb[3], double *const FEb[3],
+                   double *const FBb[3], double xb[3]) {
+  double X[3], Xb[3] = {0, 0, 0};
+  to_cell(s, x, X);
+  for (int c = 0; c < 3; ++c) {
+    interp_adj(s, s->F[c], FEb ? FEb[c] : NULL, STAG_E[c], X, Eb[c], Xb);
+    interp_adj(s, s->F[3 + c], FBb ? FBb[c] : NULL, STAG_B[c], X, Bb[c], Xb);
+  }
+  for (int a = 0; a < s->D; ++a) xb[a] += Xb[a] / s->dx[a];
+}
+
+/* reverse of or_deposit_one: with lam the adjoint of J (lam[0..2] arrays on
+ * the grid), adds d(sum lam . J)/dX0, /dX1 (cell units) and /dv */
+void or_deposit_adj(const or_sim *s, double qw, const double X0[3], const double X1[3], const double v[3],
+                    const double *const lam[3], double X0b[3], double X1b[3], double vb[3]) {
+  const int D = s->D;
+  long n0[3] = {2, 2, 2}; /* non-simulated axes: window entry 0 maps to index 0 */
+  double S0[3][5], DS[3][5], gS0[3][5], gDS[3][5];
+  for (int a = 0; a < 3; ++a)
+    for (int m = 0; m < 5; ++m) {
+      S0[a][m] = (a < D) ? 0.0 : (m == 2 ? 1.0 : 0.0);
+      DS[a][m] = 0.0; gS0[a][m] = 0.0; gDS[a][m] = 0.0;
+    }
+  for (int a = 0; a < D; ++a) {
+    n0[a] = (long)floor(X0[a] + 0.5);
+    for (int m = 0; m < 5; ++m) {
+      double node = (double)(n0[a] + m - 2);
+      double s0 = or_shape(X0[a] - node), s1 = or_shape(X1[a] - node);
+      S0[a][m] = s0;
+      DS[a][m] = s1 - s0;
+    }
+  }
+#define LAM(c, i, j, k) val(lam[c], lin(s, n0[0] + (i) - 2, n0[1] + (j) - 2, n0[2] + (k) - 2))
+  if (D == 1) {
+    double cx = -qw * s->dx[0] / s->dt;
+    for (int ip = 0; ip < 4; ++ip)
+      for (int i = ip; i < 4; ++i) gDS[0][ip] += cx * LAM(0, i, 0, 0);
+    for (int i = 0; i < 5; ++i) {
+      double ly = LAM(1, i, 0, 0), lz = LAM(2, i, 0, 0);
+      double sbar = S0[0][i] + 0.5 * DS[0][i];
+      gS0[0][i] += qw * (v[1] * ly + v[2] * lz);
+      gDS[0][i] += 0.5 * qw * (v[1] * ly + v[2] * lz);
+      vb[1] += qw * ly * sbar;
+      vb[2] += qw * lz * sbar;
+    }
+  } else if (D == 2) {
+    double cx = -qw * s->dx[0] / s->dt, cy = -qw * s->dx[1] / s->dt;
+    for (int j = 0; j < 5; ++j) {
+      double fac = S0[1][j] + 0.5 * DS[1][j], P = 0.0;
+      for (int i = 0; i < 4; ++i) {
+        P += DS[0][i];
+        double l = LAM(0, i, j, 0);
+        for (int ip = 0; ip <= i; ++ip) gDS[0][ip] += cx * l * fac;
+        gS0[1][j] += cx * l * P;
+        gDS[1][j] += 0.5 * cx * l * P;
+      }
+    }
+    for (int i = 0; i < 5; ++i) {
+      double fac = S0[0][i] + 0.5 * DS[0][i], P = 0.0;
+      for (int j = 0; j < 4; ++j) {
+        P += DS[1][j];
+        double l = LAM(1, i, j, 0);
+        for (int jp = 0; jp <= j; ++jp) gDS[1][jp] += cy * l * fac;
+        gS0[0][i] += cy * l * P;
+        gDS[0][i] += 0.5 * cy * l * P;
+      }
+    }
+    for (int j = 0; j < 5; ++j)
+      for (int i = 0; i < 5; ++i) {
+        double l = LAM(2, i, j, 0);
+        double wz = S0[0][i] * S0[1][j] + 0.5 * DS[0][i] * S0[1][j] + 0.5 * S0[0][i] * DS[1][j] +
+                    DS[0][i] * DS[1][j] / 3.0;
+        double c = qw * v[2] * l;
+        vb[2] += qw * l * wz;
+        gS0[0][i] += c * (S0[1][j] + 0.5 * DS[1][j]);
+        gDS[0][i] += c * (0.5 * S0[1][j] + DS[1][j] / 3.0);
+        gS0[1][j] += c * (S0[0][i] + 0.5 * DS[0][i]);
+        gDS[1][j] += c * (0.5 * S0[0][i] + DS[0][i] / 3.0);
+      }
+  } else {
+    /* the three components are the same formula with the axes permuted:
+     * component a runs along a with the factor of the other two (b, c) */
+    for (int a = 0; a < 3; ++a) {
+      int b = (a + 1) % 3, c = (a + 2) % 3;
+      double ca = -qw * s->dx[a] / s->dt;
+      for (int kb = 0; kb < 5; ++kb)
+        for (int kc = 0; kc < 5; ++kc) {
+          double fac = S0[b][kb] * S0[c][kc] + 0.5 * DS[b][kb] * S0[c][kc] + 0.5 * S0[b][kb] * DS[c][kc] +
+                       DS[b][kb] * DS[c][kc] / 3.0;
+          double P = 0.0;
+          for (int ka = 0; ka < 4; ++ka) {
+            P += DS[a][ka];
+            int idx[3];
+            idx[a] = ka; idx[b] = kb; idx[c] = kc;
+            double l = LAM(a, idx[0], idx[1], idx[2]);
+            if (l == 0.0) continue;
+            for (int kp = 0; kp <= ka; ++kp) gDS[a][kp] += ca * l * fac;
+            gS0[b][kb] += ca * l * P * (S0[c][kc] + 0.5 * DS[c][kc]);
+            gDS[b][kb] += ca * l * P * (0.5 * S0[c][kc] + DS[c][kc] / 3.0);
+            gS0[c][kc] += ca * l * P * (S0[b][kb] + 0.5 * DS[b][kb]);
+            gDS[c][kc] += ca * l * P * (0.5 * S0[b][kb] + DS[b][kb] / 3.0);
+          }
+        }
+    }
+  }
+#undef LAM
+  /* S0 = S(X0 - node), DS = S(X1 - node) - S(X0 - node) */
+  for (int a = 0; a < D; ++a)
+    for (int m = 0; m < 5; ++m) {
+      double node = (double)(n0[a] + m - 2);
+      X0b[a] += (gS0[a][m] - gDS[a][m]) * or_dshape(X0[a] - node);
+      X1b[a] += gDS[a][m] * or_dshape(X1[a] - node);
+    }
+}
+
+/* transpose of or_yee_b: E adjoint -= h curl^T (B adjoint); B adjoint unchanged */
+void or_yee_b_adj(const or_sim *s, double h, double *const Eb[3], const double *const Bb[3]) {
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long ijk[3] = {i, j, k};
+        long id = lin(s, i, j, k);
+        int f;
+        /* forward differences (F[idx + e_a] - F[idx]) / dx_a along simulated axes */
+        if (classify(s, STAG_B[0], ijk, &f) != CL_EXTERIOR) {
+          double g = h * Bb[0][id];
+          if (s->D >= 2) { double c = g / s->dx[1]; Eb[2][lin(s, i, j + 1, k)] -= c; Eb[2][id] += c; }
+          if (s->D >= 3) { double c = g / s->dx[2]; Eb[1][lin(s, i, j, k + 1)] += c; Eb[1][id] -= c; }
+        }
+        if (classify(s, STAG_B[1], ijk, &f) != CL_EXTERIOR) {
+          double g = h * Bb[1][id];
+          if (s->D >= 3) { double c = g / s->dx[2]; Eb[0][lin(s, i, j, k + 1)] -= c; Eb[0][id] += c; }
+          { double c = g / s->dx[0]; Eb[2][lin(s, i + 1, j, k)] += c; Eb[2][id] -= c; }
+        }
+        if (classify(s, STAG_B[2], ijk, &f) != CL_EXTERIOR) {
+          double g = h * Bb[2][id];
+          { double c = g / s->dx[0]; Eb[1][lin(s, i + 1, j, k)] -= c; Eb[1][id] += c; }
+          if (s->D >= 2) { double c = g / s->dx[1]; Eb[0][lin(s, i, j + 1, k)] += c; Eb[0][id] -= c; }
+        }
+      }
+}
+
+/* transpose of or_yee_e.  G: adjoint of E^{n+1} (destroyed); outputs the
+ * adjoint of E^n into Hn (overwritten), adds to the adjoint of B, and writes
+ * the adjoint of J (zero off the interior nodes) */
+void or_yee_e_adj(const or_sim *s, double *const G[3], double *const Hn[3], double *const Bb[3], double *const Jb[3]) {
+  const double dt = s->dt;
+  for (int c = 0; c < 3; ++c) {
+    memset(Hn[c], 0, sizeof(double) * (size_t)s->ncell);
+    memset(Jb[c], 0, sizeof(double) * (size_t)s->ncell);
+  }
+  /* Mur faces, last pass first */
+  for (int pass = 3; pass >= 1; --pass)
+    for (int c = 0; c < 3; ++c)
+      for (long k = 0; k < s->n[2]; ++k)
+        for (long j = 0; j < s->n[1]; ++j)
+          for (long i = 0; i < s->n[0]; ++i) {
+            long ijk[3] = {i, j, k};
+            int a;
+            if (classify(s, STAG_E[c], ijk, &a) != pass) continue;
+            long adj[3] = {i, j, k};
+            adj[a] += (ijk[a] == 0) ? 1 : -1;
+            long id = lin(s, i, j, k), ida = lin(s, adj[0], adj[1], adj[2]);
+            double km = (dt - s->dx[a]) / (dt + s->dx[a]);
+            double g = G[c][id];
+            Hn[c][ida] += g;
+            G[c][ida] += km * g;
+            Hn[c][id] -= km * g;
+            G[c][id] = 0.0;
+          }
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long ijk[3] = {i, j, k};
+        long id = lin(s, i, j, k);
+        int f;
+        for (int c = 0; c < 3; ++c) {
+          int cl = classify(s, STAG_E[c], ijk, &f);
+          if (cl == CL_EXTERIOR) { Hn[c][id] += G[c][id]; continue; }
+          if (cl != CL_INTERIOR) continue;
+          double g = G[c][id];
+          Hn[c][id] += g;
+          Jb[c][id] = -dt * g;
+          double e = dt * g;
+          /* backward differences (F[idx] - F[idx - e_a]) / dx_a */
+          if (c == 0) {
+            if (s->D >= 2) { double q = e / s->dx[1]; Bb[2][id] += q; Bb[2][lin(s, i, j - 1, k)] -= q; }
+            if (s->D >= 3) { double q = e / s->dx[2]; Bb[1][id] -= q; Bb[1][lin(s, i, j, k - 1)] += q; }
+          } else if (c == 1) {
+            if (s->D >= 3) { double q = e / s->dx[2]; Bb[0][id] += q; Bb[0][lin(s, i, j, k - 1)] -= q; }
+            { double q = e / s->dx[0]; Bb[2][id] -= q; Bb[2][lin(s, i - 1, j, k)] += q; }
+          } else {
+            { double q = e / s->dx[0]; Bb[1][id] += q; Bb[1][lin(s, i - 1, j, k)] -= q; }
+            if (s->D >= 2) { double q = e / s->dx[1]; Bb[0][id] -= q; Bb[0][lin(s, i, j - 1, k)] += q; }
+          }
+        }
+      }
+}
+
+/* ---------------------------------------------------------------------- */
+/* the whole run                                                           */
+
+typedef struct ora {
+  or_sim *s;
+  int sid, pid, nsteps;
+  int64_t n;
+  double *E, *B;           /* [nsteps][3][ncell] E^n and B^n (after the first half step) */
+  double *X1, *X2, *U1, *U2; /* [nsteps][n][3] particle state at step n (u at n - 1/2) */
+  double *target;          /* [nsteps][npts] */
+  double *probe;           /* [nsteps][npts] */
+} ora;
+
+ora *ora_create(or_sim *s, int sid) {
+  ora *o = (ora *)calloc(1, sizeof(ora));
+  o->s = s;
+  o->sid = sid;
+  return o;
+}
+
+void ora_destroy(ora *o) {
+  if (!o) return;
+  free(o->E); free(o->B); free(o->X1); free(o->X2); free(o->U1); free(o->U2);
+  free(o->target); free(o->probe);
+  free(o);
+}
+
+/* Runs nsteps forward steps storing every step's state, records probe pid
+ * into probe_out [nsteps][npts] and returns L = sum (probe - target)^2. */
+double ora_forward(ora *o, int nsteps, int pid, const double *target, double *probe_out, int64_t npts) {
+  or_sim *s = o->s;
+  or_species *p = &s->sp[o->sid];
+  const size_t nc = (size_t)s->ncell, np = (size_t)p->n;
+  o->nsteps = nsteps;
+  o->pid = pid;
+  o->n = p->n;
+  o->E = (double *)malloc(sizeof(double) * 3 * nc * (size_t)nsteps);
+  o->B = (double *)malloc(sizeof(double) * 3 * nc * (size_t)nsteps);
+  o->X1 = (double *)malloc(sizeof(double) * 3 * np * (size_t)nsteps + 8);
+  o->X2 = (double *)malloc(sizeof(double) * 3 * np * (size_t)nsteps + 8);
+  o->U1 = (double *)malloc(sizeof(double) * 3 * np * (size_t)nsteps + 8);
+  o->U2 = (double *)malloc(sizeof(double) * 3 * np * (size_t)nsteps + 8);
+  o->target = (double *)malloc(sizeof(double) * (size_t)(nsteps * npts));
+  memcpy(o->target, target, sizeof(double) * (size_t)(nsteps * npts));
+  or_probe *P = &s->pr[pid];
+  int64_t c0 = P->count;
+  for (int it = 0; it < nsteps; ++it) {
+    or_yee_b(s, 0.5 * s->dt);
+    for (int c = 0; c < 3; ++c) {
+      memcpy(o->E + ((size_t)it * 3 + c) * nc, s->F[c], sizeof(double) * nc);
+      memcpy(o->B + ((size_t)it * 3 + c) * nc, s->F[3 + c], sizeof(double) * nc);
+    }
+    memcpy(o->X1 + (size_t)it * 3 * np, p->x1, sizeof(double) * 3 * np);
+    memcpy(o->X2 + (size_t)it * 3 * np, p->x2, sizeof(double) * 3 * np);
+    memcpy(o->U1 + (size_t)it * 3 * np, p->u1, sizeof(double) * 3 * np);
+    memcpy(o->U2 + (size_t)it * 3 * np, p->u2, sizeof(double) * 3 * np);
+    for (int c = 6; c < 9; ++c) memset(s->F[c], 0, sizeof(double) * nc);
+    for (int i = 0; i < s->nsp; ++i) push_species(s, &s->sp[i]);
+    add_antennas(s, ((double)s->step + 0.5) * s->dt);
+    or_yee_b(s, 0.5 * s->dt);
+    or_yee_e(s);
+    s->step++;
+    record_probes(s);
+  }
+  double L = 0.0;
+  for (int it = 0; it < nsteps; ++it)
+    for (int64_t q = 0; q < npts; ++q) {
+      double v = P->data[(c0 + it) * P->npts + q];
+      if (probe_out) probe_out[it * npts + q] = v;
+      double d = v - target[it * npts + q];
+      L += d * d;
+    }
+  o->probe = (double *)malloc(sizeof(double) * (size_t)(nsteps * npts));
+  for (int it = 0; it < nsteps; ++it)
+    for (int64_t q = 0; q < npts; ++q) o->probe[it * npts + q] = P->data[(c0 + it) * P->npts + q];
+  return L;
+}
+
+/* Reverse pass.  grad_omega[nac]: dL/d omega_b per parameter index;
+ * grad_x0[n][3]: dL/d(initial ion position) (both bodies start there). */
+void ora_backward(ora *o, double *grad_omega, double *grad_x0) {
+  or_sim *s = o->s;
+  or_species *p = &s->sp[o->sid];
+  or_probe *P = &s->pr[o->pid];
+  const size_t nc = (size_t)s->ncell, np = (size_t)p->n;
+  const double dt = s->dt;
+  double *lamE[3], *lamB[3], *lamJ[3], *Hn[3], *Esave[3], *Bsave[3];
+  for (int c = 0; c < 3; ++c) {
+    lamE[c] = (double *)calloc(nc, sizeof(double));
+    lamB[c] = (double *)calloc(nc, sizeof(double));
+    lamJ[c] = (double *)calloc(nc, sizeof(double));
+    Hn[c] = (double *)calloc(nc, sizeof(double));
+    Esave[c] = s->F[c];
+    Bsave[c] = s->F[3 + c];
+  }
+  double *x1b = (double *)calloc(3 * np + 1, sizeof(double)), *x2b = (double *)calloc(3 * np + 1, sizeof(double));
+  double *u1b = (double *)calloc(3 * np + 1, sizeof(double)), *u2b = (double *)calloc(3 * np + 1, sizeof(double));
+  double *acb = (double *)calloc((size_t)p->nac, sizeof(double));
+  for (int it = o->nsteps - 1; it >= 0; --it) {
+    /* loss on the probe sample recorded after this step */
+    for (int64_t q = 0; q < P->npts; ++q)
+      lamE[P->comp][P->idx[q]] += 2.0 * (o->probe[it * P->npts + q] - o->target[it * P->npts + q]);
+    /* E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2}), Mur faces */
+    or_yee_e_adj(s, lamE, Hn, lamB, lamJ);
+    for (int c = 0; c < 3; ++c) { double *t = lamE[c]; lamE[c] = Hn[c]; Hn[c] = t; }
+    /* B^{n+1/2} = B^n - dt/2 curl E^n */
+    or_yee_b_adj(s, 0.5 * dt, lamE, (const double *const *)lamB);
+    /* particles: the fields of step n are the stored E^n, B^n */
+    for (int c = 0; c < 3; ++c) {
+      s->F[c] = o->E + ((size_t)it * 3 + c) * nc;
+      s->F[3 + c] = o->B + ((size_t)it * 3 + c) * nc;
+    }
+    const double *X1 = o->X1 + (size_t)it * 3 * np, *X2 = o->X2 + (size_t)it * 3 * np;
+    const double *U1 = o->U1 + (size_t)it * 3 * np, *U2 = o->U2 + (size_t)it * 3 * np;
+    for (int64_t q = 0; q < p->n; ++q) {
+      const double *x1 = X1 + 3 * q, *x2 = X2 + 3 * q, *u10 = U1 + 3 * q, *u20 = U2 + 3 * q;
+      double ac = p->ac[p->pidx[q]];
+      /* forward recompute */
+      double E1[3], B1[3], E2[3], B2[3], d12[3], d21[3], Ei1[3], Ei2[3];
+      gather(s, x1, E1, B1);
+      gather(s, x2, E2, B2);
+      for (int a = 0; a < 3; ++a) { d12[a] = x1[a] - x2[a]; d21[a] = -d12[a]; }
+      or_internal_field(p->q2, p->kappa, ac, d12, Ei1);
+      or_internal_field(p->q1, p->kappa, ac, d21, Ei2);
+      double Et1[3], Et2[3], u1[3], u2[3];
+      for (int a = 0; a < 3; ++a) {
+        Et1[a] = E1[a] + Ei1[a]; Et2[a] = E2[a] + Ei2[a];
+        u1[a] = u10[a]; u2[a] = u20[a];
+      }
+      or_boris(p->q1, p->m1, dt, Et1, B1, u1);
+      or_boris(p->q2, p->m2, dt, Et2, B2, u2);
+      double g1 = sqrt(1.0 + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+      double g2 = sqrt(1.0 + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+      double v1[3], v2[3], x1n[3], x2n[3], X10[3], X20[3], X11[3], X21[3];
+      for (int a = 0; a < 3; ++a) {
+        v1[a] = u1[a] / g1; v2[a] = u2[a] / g2;
+        x1n[a] = x1[a] + dt * v1[a]; x2n[a] = x2[a] + dt * v2[a];
+      }
+      to_cell(s, x1, X10); to_cell(s, x2, X20); to_cell(s, x1n, X11); to_cell(s, x2n, X21);
+      /* deposit */
+      double X10b[3] = {0, 0, 0}, X11b[3] = {0, 0, 0}, X20b[3] = {0, 0, 0}, X21b[3] = {0, 0, 0};
+      double v1b[3] = {0, 0, 0}, v2b[3] = {0, 0, 0};
+      or_deposit_adj(s, p->q1 * p->w, X10, X11, v1, (const double *const *)lamJ, X10b, X11b, v1b);
+      or_deposit_adj(s, p->q2 * p->w, X20, X21, v2, (const double *const *)lamJ, X20b, X21b, v2b);
+      double *xb1 = x1b + 3 * q, *xb2 = x2b + 3 * q, *ub1 = u1b + 3 * q, *ub2 = u2b + 3 * q;
+      /* adjoint of x^{n+1}: carried plus the deposit's */
+      for (int a = 0; a < s->D; ++a) { xb1[a] += X11b[a] / s->dx[a]; xb2[a] += X21b[a] / s->dx[a]; }
+      /* drift x^{n+1} = x^n + dt v(u^{n+1/2}): x^n gets the same adjoint */
+      for (int a = 0; a < 3; ++a) { v1b[a] += dt * xb1[a]; v2b[a] += dt * xb2[a]; }
+      /* v = u / gamma */
+      double uv1 = u1[0] * v1b[0] + u1[1] * v1b[1] + u1[2] * v1b[2];
+      double uv2 = u2[0] * v2b[0] + u2[1] * v2b[1] + u2[2] * v2b[2];
+      double un1b[3], un2b[3];
+      for (int a = 0; a < 3; ++a) {
+        un1b[a] = ub1[a] + v1b[a] / g1 - u1[a] * uv1 / (g1 * g1 * g1);
+        un2b[a] = ub2[a] + v2b[a] / g2 - u2[a] * uv2 / (g2 * g2 * g2);
+      }
+      /* Boris */
+      double Et1b[3], Et2b[3], B1b[3], B2b[3];
+      or_boris_adj(p->q1, p->m1, dt, Et1, B1, u10, un1b, ub1, Et1b, B1b);
+      or_boris_adj(p->q2, p->m2, dt, Et2, B2, u20, un2b, ub2, Et2b, B2b);
+      /* internal field */
+      double d12b[3] = {0, 0, 0}, d21b[3] = {0, 0, 0};
+      acb[p->pidx[q]] += or_internal_field_adj(p->q2, p->kappa, ac, d12, Et1b, d12b);
+      acb[p->pidx[q]] += or_internal_field_adj(p->q1, p->kappa, ac, d21, Et2b, d21b);
+      for (int a = 0; a < 3; ++a) {
+        xb1[a] += d12b[a] - d21b[a];
+        xb2[a] += d21b[a] - d12b[a];
+      }
+      /* gather: field adjoints of E^n and B^n, and the position gradients */
+      or_gather_adj(s, x1, Et1b, B1b, lamE, lamB, xb1);
+      or_gather_adj(s, x2, Et2b, B2b, lamE, lamB, xb2);
+      /* old positions through the deposit */
+      for (int a = 0; a < s->D; ++a) { xb1[a] += X10b[a] / s->dx[a]; xb2[a] += X20b[a] / s->dx[a]; }
+    }
+    /* B^n = B^{n-1/2} - dt/2 curl E^n */
+    or_yee_b_adj(s, 0.5 * dt, lamE, (const double *const *)lamB);
+  }
+  for (int c = 0; c < 3; ++c) { s->F[c] = Esave[c]; s->F[3 + c] = Bsave[c]; }
+  /* a_c(omega) = (|q1 q2| kappa / (m_r omega^2))^{1/3}: d a_c / d omega = -2 a_c / (3 omega) */
+  for (int i = 0; i < p->nac; ++i) {
+    double mr = p->m1 * p->m2 / (p->m1 + p->m2);
+    double om = sqrt(fabs(p->q1 * p->q2) * p->kappa / (mr * p->ac[i] * p->ac[i] * p->ac[i]));
+    grad_omega[i] = acb[i] * (-2.0 * p->ac[i] / (3.0 * om));
+  }
+  for (size_t q = 0; q < np; ++q)
+    for (int a = 0; a < 3; ++a) grad_x0[3 * q + a] = x1b[3 * q + a] + x2b[3 * q + a];
+  for (int c = 0; c < 3; ++c) { free(lamE[c]); free(lamB[c]); free(lamJ[c]); free(Hn[c]); }
+  free(x1b); free(x2b); free(u1b); free(u2b); free(acb);
+}
