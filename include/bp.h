@@ -71,7 +71,8 @@ typedef struct {
  * E_y at (i, j+1/2, k), E_z at (i, j, k+1/2), B_x at (i, j+1/2, k+1/2), B_y at
  * (i+1/2, j, k+1/2), B_z at (i+1/2, j+1/2, k); J with E.  Open axes use Mur
  * first-order absorbing faces on the tangential E; periodic axes wrap.
- * n[a] must be a multiple of tile[a]. */
+ * Tiles are 64 cells (1D), 32 x 32 (2D), 8 x 8 x 8 (3D); n[a] must be a
+ * multiple of the tile and the bit widths of n[0..2] may sum to at most 31. */
 typedef struct {
   int dims;           /* 1, 2 or 3 */
   int64_t n[3];       /* cells per axis (1 on unused axes) */
@@ -80,7 +81,7 @@ typedef struct {
   int boundary[3];    /* BP_PERIODIC or BP_OPEN per axis */
   int deposit_mode;   /* BP_DEPOSIT_ATOMIC (FP32 shared atomics) or
                          BP_DEPOSIT_SORTED (integer fixed point: bit-exact reruns) */
-  int tile[3];        /* cells per tile per axis; 0 picks 64 / 32x32 / 8x8x8 */
+  int tile[3];        /* 0, or the fixed tile size of the dimension */
 } bp_grid_desc;
 
 /* Species.  BP_TWO_BODY follows Sec. 2: q2 = -Zb, m2 = Zb, q1 = qc - q2,

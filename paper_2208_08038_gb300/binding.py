@@ -157,7 +157,7 @@ class Context:
             g.n[a] = int(n[a]) if a < dims else 1
             g.dx[a] = float(dx[a]) if a < dims else 1.0
             g.boundary[a] = int(boundary[a]) if a < dims else 0
-            g.tile[a] = int(tile[a]) if (tile is not None and a < dims) else 0
+            g.tile[a] = int(tile[a]) if (tile is not None and a < dims and tile[a]) else 0
         g.dt = float(dt)
         g.deposit_mode = deposit_mode
         self.dims = dims

@@ -201,8 +201,9 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
     return BP_ERR_ARG;
   }
   g.D = D;
-  static const int def_tile[4][3] = {{1, 1, 1}, {64, 1, 1}, {32, 32, 1}, {8, 8, 8}};
-  static const int def_margin[4] = {0, 8, 2, 1};
+  static const int def_tile[4][3] = {{1, 1, 1}, {Geo<1>::L0, 1, 1}, {Geo<2>::L0, Geo<2>::L1, 1},
+                                     {Geo<3>::L0, Geo<3>::L1, Geo<3>::L2}};
+  static const int def_margin[4] = {0, Geo<1>::M, Geo<2>::M, Geo<3>::M};
   g.M = def_margin[D];
   double inv2 = 0.0;
   long long ncell = 1;
@@ -215,8 +216,8 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
       g.n[a] = (int)gd->n[a];
       g.bc[a] = gd->boundary[a] == BP_OPEN ? BP_OPEN : BP_PERIODIC;
       g.dxd[a] = gd->dx[a];
-      g.L[a] = gd->tile[a] > 0 ? gd->tile[a] : def_tile[D][a];
-      if (g.n[a] % g.L[a] != 0 || g.L[a] < g.M + 3) {
+      g.L[a] = def_tile[D][a];
+      if (g.n[a] % g.L[a] != 0 || (gd->tile[a] > 0 && gd->tile[a] != g.L[a])) {
         delete c;
         return BP_ERR_ARG;
       }
@@ -245,6 +246,18 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
     return BP_ERR_CFL;
   }
   if (ncell >= (1LL << 31) - 1) {
+    delete c;
+    return BP_ERR_ARG;
+  }
+  int bits = 0;
+  for (int a = 0; a < 3; ++a) {
+    int b = 0;
+    while ((1 << b) < g.n[a]) ++b;
+    g.cb[a] = b;
+    g.cm[a] = (1 << b) - 1;
+    bits += b;
+  }
+  if (bits > 31) {
     delete c;
     return BP_ERR_ARG;
   }
@@ -629,7 +642,8 @@ int bp_read_particles(bp_ctx *c, int sid, double *x1, double *x2, double *u1, do
   for (auto &pr : order) {
     if (k >= cap) break;
     int q = pr.second;
-    int cc[3] = {cell[q] % g.n[0], (cell[q] / g.n[0]) % g.n[1], cell[q] / (g.n[0] * g.n[1])};
+    int cc[3];
+    unpack_cell(g, cell[q], cc);
     for (int a = 0; a < 3; ++a) {
       double xa = a < D ? ((double)cc[a] + (double)off[(size_t)a * cnt + q]) * g.dxd[a] : 0.0;
       if (x1) x1[3 * k + a] = xa;

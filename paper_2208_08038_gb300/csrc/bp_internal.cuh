@@ -29,7 +29,48 @@ struct GridP {
   long long ncell;
   int ntiles;
   int cpt;          // cells per tile
+  int cb[3], cm[3]; // particle cell index: bit width and mask of each axis
 };
+
+// Tile geometry per dimension (compile time): L cells per tile per simulated
+// axis; body 1 may sit up to M cells outside its tile; the field box staged
+// for the gather spans [T0 - M - 2, T0 + L + M + 2], the current box
+// [T0 - M - 3, T0 + L + M + 3] (body 2 within one cell of body 1, moves
+// shorter than one cell).
+template <int D>
+struct Geo;
+template <>
+struct Geo<1> {
+  static constexpr int L0 = 64, L1 = 1, L2 = 1, M = 8;
+};
+template <>
+struct Geo<2> {
+  static constexpr int L0 = 32, L1 = 32, L2 = 1, M = 2;
+};
+template <>
+struct Geo<3> {
+  static constexpr int L0 = 8, L1 = 8, L2 = 8, M = 1;
+};
+template <int D>
+struct Box {
+  static constexpr int M = Geo<D>::M;
+  static constexpr int G0 = Geo<D>::L0 + 2 * M + 5, G1 = D >= 2 ? Geo<D>::L1 + 2 * M + 5 : 1,
+                       G2 = D >= 3 ? Geo<D>::L2 + 2 * M + 5 : 1;
+  static constexpr int J0 = Geo<D>::L0 + 2 * M + 7, J1 = D >= 2 ? Geo<D>::L1 + 2 * M + 7 : 1,
+                       J2 = D >= 3 ? Geo<D>::L2 + 2 * M + 7 : 1;
+  static constexpr int OG = M + 2, OJ = M + 3;
+  static constexpr int GCELLS = G0 * G1 * G2, JCELLS = J0 * J1 * J2;
+};
+
+// particle cell index: the three cell coordinates packed in bit fields
+__host__ __device__ __forceinline__ int pack_cell(const GridP &g, int c0, int c1, int c2) {
+  return c0 | (c1 << g.cb[0]) | (c2 << (g.cb[0] + g.cb[1]));
+}
+__host__ __device__ __forceinline__ void unpack_cell(const GridP &g, int cell, int c[3]) {
+  c[0] = cell & g.cm[0];
+  c[1] = (cell >> g.cb[0]) & g.cm[1];
+  c[2] = cell >> (g.cb[0] + g.cb[1]);
+}
 
 struct SpecP {
   int kind;                // BP_TWO_BODY / BP_FREE

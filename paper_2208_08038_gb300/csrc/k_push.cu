@@ -25,14 +25,15 @@ struct Loc {
 };
 
 template <int D>
-__device__ __forceinline__ void make_loc(const int d[3], const float f[3], const int og[3], Loc &L) {
+__device__ __forceinline__ void make_loc(const int d[3], const float f[3], Loc &L) {
+  constexpr int og = Box<D>::OG;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a < D) {
       int up = f[a] >= 0.5f ? 1 : 0;
-      L.bn[a] = d[a] + og[a] + up - 1;
+      L.bn[a] = d[a] + og + up - 1;
       qweights(f[a] - (float)up, L.wn[a]);
-      L.bh[a] = d[a] + og[a] - 1;
+      L.bh[a] = d[a] + og - 1;
       qweights(f[a] - 0.5f, L.wh[a]);
     } else {
       L.bn[a] = L.bh[a] = 0;
@@ -45,8 +46,9 @@ __device__ __forceinline__ void make_loc(const int d[3], const float f[3], const
 // one field component with stagger pattern PAT (bit a: half cell along a)
 // at two bodies; loads are shared when both stencils start at the same node
 template <int D, int PAT>
-__device__ __forceinline__ void gather_comp(const float *__restrict__ G, int gb0, int gb1, const Loc &A,
-                                            const Loc &Bo, float &oa, float &ob) {
+__device__ __forceinline__ void gather_comp(const float *__restrict__ G, const Loc &A, const Loc &Bo, float &oa,
+                                            float &ob) {
+  constexpr int gb0 = Box<D>::G0, gb1 = Box<D>::G1;
   int ba[3], bb[3];
   const float *wa[3];
   const float *wb[3];
@@ -99,23 +101,24 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, int gb0
 }
 
 template <int D>
-__device__ __forceinline__ void gather_all(const float *G, int gcells, int gb0, int gb1, const Loc &A,
-                                           const Loc &Bo, float Ea[3], float Ba[3], float Eb[3], float Bb[3]) {
-  gather_comp<D, 1>(G + 0 * gcells, gb0, gb1, A, Bo, Ea[0], Eb[0]);
-  gather_comp<D, 2>(G + 1 * gcells, gb0, gb1, A, Bo, Ea[1], Eb[1]);
-  gather_comp<D, 4>(G + 2 * gcells, gb0, gb1, A, Bo, Ea[2], Eb[2]);
-  gather_comp<D, 6>(G + 3 * gcells, gb0, gb1, A, Bo, Ba[0], Bb[0]);
-  gather_comp<D, 5>(G + 4 * gcells, gb0, gb1, A, Bo, Ba[1], Bb[1]);
-  gather_comp<D, 3>(G + 5 * gcells, gb0, gb1, A, Bo, Ba[2], Bb[2]);
+__device__ __forceinline__ void gather_all(const float *G, const Loc &A, const Loc &Bo, float Ea[3], float Ba[3],
+                                           float Eb[3], float Bb[3]) {
+  constexpr int gc = Box<D>::GCELLS;
+  gather_comp<D, 1>(G + 0 * gc, A, Bo, Ea[0], Eb[0]);
+  gather_comp<D, 2>(G + 1 * gc, A, Bo, Ea[1], Eb[1]);
+  gather_comp<D, 4>(G + 2 * gc, A, Bo, Ea[2], Eb[2]);
+  gather_comp<D, 6>(G + 3 * gc, A, Bo, Ba[0], Bb[0]);
+  gather_comp<D, 5>(G + 4 * gc, A, Bo, Ba[1], Bb[1]);
+  gather_comp<D, 3>(G + 5 * gc, A, Bo, Ba[2], Bb[2]);
 }
 
 // relativistic Boris (Sec. 2): u- = u + hE; t = hB/gamma-; s = 2t/(1+t^2);
 // u+ = u- + (u- + u- x t) x s; u = u+ + hE
 __device__ __forceinline__ void boris(float h, const float E[3], const float B[3], float u[3]) {
   float um0 = fmaf(h, E[0], u[0]), um1 = fmaf(h, E[1], u[1]), um2 = fmaf(h, E[2], u[2]);
-  float gi = 1.0f / sqrtf(1.0f + um0 * um0 + um1 * um1 + um2 * um2);
+  float gi = rsqrtf(1.0f + um0 * um0 + um1 * um1 + um2 * um2);
   float t0 = h * B[0] * gi, t1 = h * B[1] * gi, t2 = h * B[2] * gi;
-  float sf = 2.0f / (1.0f + t0 * t0 + t1 * t1 + t2 * t2);
+  float sf = __fdividef(2.0f, 1.0f + t0 * t0 + t1 * t1 + t2 * t2);
   float s0 = t0 * sf, s1 = t1 * sf, s2 = t2 * sf;
   float c0 = um0 + (um1 * t2 - um2 * t1);
   float c1 = um1 + (um2 * t0 - um0 * t2);
@@ -132,13 +135,13 @@ __device__ __forceinline__ void boris(float h, const float E[3], const float B[3
 // S0[m] at the old position, DS[m] = S1[m] - S0[m], node n0 - 2 + m
 template <int D>
 __device__ __forceinline__ void window(const float f[3], const float de[3], float S0[3][5], float DS[3][5],
-                                       int n0[3], const int d[3], const int oj[3]) {
+                                       int n0[3], const int d[3]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a < D) {
       int up = f[a] >= 0.5f ? 1 : 0;
       float xi = f[a] - (float)up;
-      n0[a] = d[a] + oj[a] + up;
+      n0[a] = d[a] + Box<D>::OJ + up;
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
         float u = xi - (float)(m - 2);
@@ -170,9 +173,10 @@ __device__ __forceinline__ void jadd(JT *p, float v, float scale) {
 //   1D W_x = DSx, J_y/z with S0 + DS/2,
 // J_a on the face after node i = -qw dx_a/dt * sum_{i' <= i} W_a(i').
 template <int D, bool DET, int NB, typename JT>
-__device__ __forceinline__ void esirkepov(JT *__restrict__ J, int jcells, int jb0, int jb1, const int n0[3],
-                                          const float (*S0)[3][5], const float (*DS)[3][5], const float *qw,
-                                          const float (*v)[3], const float dxdt[3], float scale) {
+__device__ __forceinline__ void esirkepov(JT *__restrict__ J, const int n0[3], const float (*S0)[3][5],
+                                          const float (*DS)[3][5], const float *qw, const float (*v)[3],
+                                          const float dxdt[3], float scale) {
+  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
   JT *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
   const int bx = n0[0] - 2, by = n0[1] - 2, bz = n0[2] - 2;
   if constexpr (D == 1) {
@@ -352,9 +356,10 @@ __device__ __forceinline__ void esirkepov(JT *__restrict__ J, int jcells, int jb
 // with xi = old position - n.  J along a simulated axis then lives on the two
 // faces inside the window.
 template <int D, bool DET, int NB, typename JT>
-__device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int jb0, int jb1, const int n[3],
-                                           const float (*xi)[3], const float (*de)[3], const float *qw,
-                                           const float (*v)[3], const float dxdt[3], float scale) {
+__device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], const float (*xi)[3],
+                                           const float (*de)[3], const float *qw, const float (*v)[3],
+                                           const float dxdt[3], float scale) {
+  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
   float S0[NB][3][3], DS[NB][3][3], P[NB][3][2];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
@@ -387,7 +392,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
     for (int f = 0; f < 2; ++f) {
       float jx = 0.0f;
 #pragma unroll
-      for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0], P[b][0][f], jx);
+      for (int b = 0; b < NB; ++b) jx = __fadd_rn(jx, __fmul_rn(cq[b][0], P[b][0][f]));
       jadd<DET>(Jx + bx + f, jx, scale);
     }
 #pragma unroll
@@ -396,8 +401,8 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         float sb = S0[b][0][i] + 0.5f * DS[b][0][i];
-        jy = fmaf(qw[b] * v[b][1], sb, jy);
-        jz = fmaf(qw[b] * v[b][2], sb, jz);
+        jy = __fadd_rn(jy, __fmul_rn(qw[b] * v[b][1], sb));
+        jz = __fadd_rn(jz, __fmul_rn(qw[b] * v[b][2], sb));
       }
       jadd<DET>(Jy + bx + i, jy, scale);
       jadd<DET>(Jz + bx + i, jz, scale);
@@ -409,7 +414,8 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
       for (int f = 0; f < 2; ++f) {
         float jx = 0.0f;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0] * P[b][0][f], S0[b][1][j] + 0.5f * DS[b][1][j], jx);
+        for (int b = 0; b < NB; ++b)
+          jx = __fadd_rn(jx, __fmul_rn(cq[b][0] * P[b][0][f], S0[b][1][j] + 0.5f * DS[b][1][j]));
         jadd<DET>(Jx + (bx + f) + jb0 * (by + j), jx, scale);
       }
 #pragma unroll
@@ -418,7 +424,8 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
       for (int i = 0; i < 3; ++i) {
         float jy = 0.0f;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) jy = fmaf(cq[b][1] * P[b][1][g], S0[b][0][i] + 0.5f * DS[b][0][i], jy);
+        for (int b = 0; b < NB; ++b)
+          jy = __fadd_rn(jy, __fmul_rn(cq[b][1] * P[b][1][g], S0[b][0][i] + 0.5f * DS[b][0][i]));
         jadd<DET>(Jy + (bx + i) + jb0 * (by + g), jy, scale);
       }
 #pragma unroll
@@ -430,7 +437,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
         for (int b = 0; b < NB; ++b) {
           float w = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
                     (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
-          jz = fmaf(qw[b] * v[b][2], w, jz);
+          jz = __fadd_rn(jz, __fmul_rn(qw[b] * v[b][2], w));
         }
         jadd<DET>(Jz + (bx + i) + jb0 * (by + j), jz, scale);
       }
@@ -448,7 +455,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
         for (int f = 0; f < 2; ++f) {
           float jx = 0.0f;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) jx = fmaf(cq[b][0] * P[b][0][f], F[b], jx);
+          for (int b = 0; b < NB; ++b) jx = __fadd_rn(jx, __fmul_rn(cq[b][0] * P[b][0][f], F[b]));
           jadd<DET>(Jx + (bx + f) + jb0 * ((by + j) + jb1 * (bz + k)), jx, scale);
         }
       }
@@ -465,7 +472,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
         for (int g = 0; g < 2; ++g) {
           float jy = 0.0f;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) jy = fmaf(cq[b][1] * P[b][1][g], F[b], jy);
+          for (int b = 0; b < NB; ++b) jy = __fadd_rn(jy, __fmul_rn(cq[b][1] * P[b][1][g], F[b]));
           jadd<DET>(Jy + (bx + i) + jb0 * ((by + g) + jb1 * (bz + k)), jy, scale);
         }
       }
@@ -482,7 +489,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
         for (int h = 0; h < 2; ++h) {
           float jz = 0.0f;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) jz = fmaf(cq[b][2] * P[b][2][h], F[b], jz);
+          for (int b = 0; b < NB; ++b) jz = __fadd_rn(jz, __fmul_rn(cq[b][2] * P[b][2][h], F[b]));
           jadd<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + h)), jz, scale);
         }
       }
@@ -490,13 +497,23 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, int jcells, int j
 }
 
 // tile-relative cell of a global cell coordinate (periodic: nearest image)
+template <int D>
 __device__ __forceinline__ int rel_cell(const GridP &g, int a, int c, int T0) {
+  constexpr int M = Geo<D>::M;
+  const int L = a == 0 ? Geo<D>::L0 : (a == 1 ? Geo<D>::L1 : Geo<D>::L2);
   int d = c - T0;
   if (g.bc[a] == BP_PERIODIC) {
-    if (d < -g.M) d += g.n[a];
-    else if (d >= g.L[a] + g.M) d -= g.n[a];
+    if (d < -M) d += g.n[a];
+    else if (d >= L + M) d -= g.n[a];
   }
   return d;
+}
+
+template <int D>
+__device__ __forceinline__ bool outside_margin(int a, int d) {
+  constexpr int M = Geo<D>::M;
+  const int L = a == 0 ? Geo<D>::L0 : (a == 1 ? Geo<D>::L1 : Geo<D>::L2);
+  return d < -M || d >= L + M;
 }
 
 
@@ -520,18 +537,18 @@ __device__ __noinline__ void general_deposit(JT *Jsm, const GridP &g, const floa
     vv[1][a] = v2[a];
     fa[a] = f[a]; fb[a] = f2[a]; da[a] = de1[a]; db[a] = de2[a]; ia[a] = d[a]; ib[a] = d2[a];
   }
-  window<D>(fa, da, S0[0], DS[0], n1, ia, g.oj);
+  window<D>(fa, da, S0[0], DS[0], n1, ia);
   if (two) {
-    window<D>(fb, db, S0[1], DS[1], n2, ib, g.oj);
+    window<D>(fb, db, S0[1], DS[1], n2, ib);
     const bool same = (n1[0] == n2[0]) && (D < 2 || n1[1] == n2[1]) && (D < 3 || n1[2] == n2[2]);
     if (same) {
-      esirkepov<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+      esirkepov<D, DET, 2>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
     } else {
-      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
-      esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
+      esirkepov<D, DET, 1>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
+      esirkepov<D, DET, 1>(Jsm, n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
     }
   } else {
-    esirkepov<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], n1, S0, DS, qw, vv, dxdt, scale);
+    esirkepov<D, DET, 1>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
   }
 }
 
@@ -543,9 +560,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   int cell = P.cell[i];
   if (cell < 0) return;
   int c[3];
-  c[0] = cell % g.n[0];
-  c[1] = (cell / g.n[0]) % g.n[1];
-  c[2] = cell / (g.n[0] * g.n[1]);
+  unpack_cell(g, cell, c);
   float f[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f}, u1[3], u2[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int a = 0; a < D; ++a) f[a] = P.off[a * cap + i];
@@ -563,8 +578,8 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    d[a] = rel_cell(g, a, c[a], T0[a]);
-    bad |= (d[a] < -g.M) || (d[a] >= g.L[a] + g.M);
+    d[a] = rel_cell<D>(g, a, c[a], T0[a]);
+    bad |= outside_margin<D>(a, d[a]);
     // body 2 sits at x1 - r
     float rc = r[a] * g.idx[a];
     bad |= !(fabsf(rc) < 1.0f);
@@ -583,9 +598,9 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   float E1[3], B1[3], E2[3], B2[3];
   {
     Loc L1, L2;
-    make_loc<D>(d, f, g.og, L1);
-    make_loc<D>(two ? d2 : d, two ? f2 : f, g.og, L2);
-    gather_all<D>(Gsm, g.gcells, g.gb[0], g.gb[1], L1, L2, E1, B1, E2, B2);
+    make_loc<D>(d, f, L1);
+    make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
+    gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
   }
   float v1[3], v2[3] = {0.0f, 0.0f, 0.0f};
   if (two) {
@@ -594,20 +609,21 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     const int pi = P.pidx ? P.pidx[i] : 0;
     const float ac = sp.ac[pi];
     float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + ac * ac;
-    float s = sp.kappa / (rr * sqrtf(rr));
+    float rs = rsqrtf(rr);
+    float s = sp.kappa * rs * rs * rs;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       E1[a] = fmaf(sp.q2 * s, r[a], E1[a]);
       E2[a] = fmaf(-sp.q1 * s, r[a], E2[a]);
     }
     boris(sp.h2, E2, B2, u2);
-    float g2 = 1.0f / sqrtf(1.0f + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+    float g2 = rsqrtf(1.0f + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) v2[a] = u2[a] * g2;
   }
   boris(sp.h1, E1, B1, u1);
   {
-    float g1 = 1.0f / sqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    float g1 = rsqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) v1[a] = u1[a] * g1;
   }
@@ -639,7 +655,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     xi[0][a] = f[a] - u1p;
     const float x1n = xi[0][a] + de1[a];
     fast &= (x1n >= -0.5f) && (x1n < 0.5f);
-    nn[a] = d[a] + g.oj[a] + (int)u1p;
+    nn[a] = d[a] + Box<D>::OJ + (int)u1p;
     if (two) {
       const float u2p = f2[a] >= 0.5f ? 1.0f : 0.0f;
       xi[1][a] = f2[a] - u2p;
@@ -665,8 +681,8 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       dd[0][a] = de1[a];
       dd[1][a] = de2[a];
     }
-    if (two) esirkepov3<D, DET, 2>(Jsm, g.jcells, g.jb[0], g.jb[1], nn, xi, dd, qw, vv, dxdt, scale);
-    else esirkepov3<D, DET, 1>(Jsm, g.jcells, g.jb[0], g.jb[1], nn, xi, dd, qw, vv, dxdt, scale);
+    if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+    else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
   } else {
     general_deposit<D, DET, JT>(Jsm, g, f, de1, d, f2, de2, d2, two, sp.qw1, sp.qw2, v1, v2, scale);
   }
@@ -691,8 +707,8 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     } else {
       removed |= (c[a] < 2 || c[a] >= g.n[a] - 2);
     }
-    int dn = rel_cell(g, a, c[a], T0[a]);
-    need_sort |= (dn < -g.M) || (dn >= g.L[a] + g.M);
+    int dn = rel_cell<D>(g, a, c[a], T0[a]);
+    need_sort |= outside_margin<D>(a, dn);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) nonfinite |= !isfinite(u1[a]) || !isfinite(u2[a]);
@@ -703,7 +719,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     return;
   }
   if (need_sort) atomicOr(status, ST_NEED_SORT);
-  P.cell[i] = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+  P.cell[i] = pack_cell(g, c[0], c[1], c[2]);
 #pragma unroll
   for (int a = 0; a < D; ++a) P.off[a * cap + i] = fn[a];
 #pragma unroll
@@ -721,8 +737,10 @@ template <int D, bool DET>
 __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A) {
   using JT = typename std::conditional<DET, long long, float>::type;
   extern __shared__ __align__(16) unsigned char smem[];
+  using BX = Box<D>;
+  constexpr int JC = BX::JCELLS, GC = BX::GCELLS;
   JT *Jsm = reinterpret_cast<JT *>(smem);
-  float *Gsm = reinterpret_cast<float *>(smem + sizeof(JT) * 3 * (size_t)g.jcells);
+  float *Gsm = reinterpret_cast<float *>(smem + sizeof(JT) * 3 * (size_t)JC);
   const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
   int total = 0;
@@ -735,17 +753,17 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   tc[0] = t % g.nt[0];
   tc[1] = (t / g.nt[0]) % g.nt[1];
   tc[2] = t / (g.nt[0] * g.nt[1]);
-  const int T0[3] = {tc[0] * g.L[0], tc[1] * g.L[1], tc[2] * g.L[2]};
-  for (int q = tid; q < 3 * g.jcells; q += bs) Jsm[q] = (JT)0;
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  for (int q = tid; q < 3 * JC; q += bs) Jsm[q] = (JT)0;
   // stage E, B of the tile plus halo (zero outside open faces)
-  for (int q = tid; q < g.gcells; q += bs) {
-    int b0 = q % g.gb[0], b1 = (q / g.gb[0]) % g.gb[1], b2 = q / (g.gb[0] * g.gb[1]);
+  for (int q = tid; q < GC; q += bs) {
+    int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     int bidx[3] = {b0, b1, b2};
     long long gi = 0, stride = 1;
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      int x = T0[a] - g.og[a] + bidx[a];
+      int x = T0[a] - (a < D ? BX::OG : 0) + bidx[a];
       if (a < D) {
         if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
         else ok &= (x >= 0 && x < g.n[a]);
@@ -755,8 +773,8 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      Gsm[cc * g.gcells + q] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
-      Gsm[(3 + cc) * g.gcells + q] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
+      Gsm[cc * GC + q] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
+      Gsm[(3 + cc) * GC + q] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
     }
   }
   __syncthreads();
@@ -776,8 +794,8 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], qbuf[k], T0, Gsm, Jsm, A.status, A.jscale, nullptr, nullptr, 0);
     __syncthreads();
   }
-  float *out = A.jbox + (size_t)t * 3 * g.jcells;
-  for (int q = tid; q < 3 * g.jcells; q += bs) {
+  float *out = A.jbox + (size_t)t * 3 * JC;
+  for (int q = tid; q < 3 * JC; q += bs) {
     if constexpr (DET) out[q] = (float)((double)Jsm[q] * (double)A.jinv);
     else out[q] = Jsm[q];
   }
@@ -800,7 +818,11 @@ int prepare_one(const GridP &g) {
 }  // namespace
 
 size_t push_smem_bytes(const GridP &g, int det) {
-  return (det ? 8 : 4) * (size_t)3 * g.jcells + 4 * (size_t)6 * g.gcells;
+  int jc = 0, gc = 0;
+  if (g.D == 1) { jc = Box<1>::JCELLS; gc = Box<1>::GCELLS; }
+  if (g.D == 2) { jc = Box<2>::JCELLS; gc = Box<2>::GCELLS; }
+  if (g.D == 3) { jc = Box<3>::JCELLS; gc = Box<3>::GCELLS; }
+  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc;
 }
 
 int push_prepare(const GridP &g, int det) {

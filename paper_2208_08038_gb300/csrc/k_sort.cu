@@ -18,9 +18,9 @@ int blocks_for(long long n, int bs, long long cap = 152LL * 16) {
 __device__ __forceinline__ bool sorting(const int *status) { return (*(volatile const int *)status) & ST_NEED_SORT; }
 
 __device__ __forceinline__ int sort_key(const GridP &g, int cell) {
-  int c0 = cell % g.n[0];
-  int c1 = (cell / g.n[0]) % g.n[1];
-  int c2 = cell / (g.n[0] * g.n[1]);
+  int cc[3];
+  unpack_cell(g, cell, cc);
+  const int c0 = cc[0], c1 = cc[1], c2 = cc[2];
   int t = c0 / g.L[0] + g.nt[0] * (c1 / g.L[1] + g.nt[1] * (c2 / g.L[2]));
   int l = c0 % g.L[0] + g.L[0] * (c1 % g.L[1] + g.L[1] * (c2 % g.L[2]));
   return t * g.cpt + l;
@@ -215,7 +215,7 @@ __global__ void k_gen_medium(GridP g, SpecP sp, PartP p, int lo0, int lo1, int l
       }
     }
     long long o = out0 + q;
-    p.cell[o] = cell[0] + g.n[0] * (cell[1] + g.n[1] * cell[2]);
+    p.cell[o] = pack_cell(g, cell[0], cell[1], cell[2]);
     for (int a = 0; a < g.D; ++a) p.off[a * cap + o] = off[a];
     if (sp.kind == BP_TWO_BODY) {
       double qc = sp.q1d + sp.q2d;
@@ -249,7 +249,8 @@ __global__ void k_rho(GridP g, SpecP sp, PartP p, double *rho) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     int cell = p.cell[q];
     if (cell < 0) continue;
-    int c[3] = {cell % g.n[0], (cell / g.n[0]) % g.n[1], cell / (g.n[0] * g.n[1])};
+    int c[3];
+    unpack_cell(g, cell, c);
     const int nb = sp.kind == BP_TWO_BODY ? 2 : 1;
     for (int b = 0; b < nb; ++b) {
       double qw = (b == 0 ? sp.q1d : sp.q2d) * sp.wd;
@@ -364,7 +365,7 @@ __global__ void k_load_convert(GridP g, SpecP sp, PartP p, const double *x, cons
         p.r[a * cap + o] = 0.0f;
       }
     }
-    p.cell[o] = (bad || nonfinite) ? -1 : cell[0] + g.n[0] * (cell[1] + g.n[1] * cell[2]);
+    p.cell[o] = (bad || nonfinite) ? -1 : pack_cell(g, cell[0], cell[1], cell[2]);
     p.id[o] = (int)o;
     if (bad) atomicOr(status, ST_DOMAIN);
     if (nonfinite) atomicOr(status, ST_NONFINITE);

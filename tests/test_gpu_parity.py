@@ -45,8 +45,7 @@ def test_vacuum_yee_parity(D):
     dx = [0.2, 0.25, 0.3][:D]
     dt = 0.9 / math.sqrt(sum(1 / d ** 2 for d in dx))
     bc = [1] + [0] * (D - 1)
-    wl = synth.Workload("vac", D, tuple(n), tuple(dx), dt, tuple(bc), 40, [], [], tile=tuple([8] * D) if D == 3 else
-                        (tuple([32] * D) if D == 2 else (16,)))
+    wl = synth.Workload("vac", D, tuple(n), tuple(dx), dt, tuple(bc), 40, [], [], tile=(0, 0, 0)[:D])
     ora, _, _ = oracle_from_workload(wl)
     gpu, _, _ = gpu_from_workload(wl)
     rng = np.random.default_rng(D)
@@ -206,7 +205,10 @@ def test_errors_are_status_codes():
     with pytest.raises(B.BPError) as e:
         B.Context(2, (60, 64), (0.1, 0.1), 0.05, (1, 0))  # 60 is not a multiple of the 32-cell tile
     assert e.value.code == B.BP_ERR_ARG
-    ctx = B.Context(1, (64,), (0.1,), 0.09, (1,), tile=(16,))
+    with pytest.raises(B.BPError) as e:
+        B.Context(1, (64,), (0.1,), 0.09, (1,), tile=(16,))  # tiles are fixed per dimension
+    assert e.value.code == B.BP_ERR_ARG
+    ctx = B.Context(1, (64,), (0.1,), 0.09, (1,))
     with pytest.raises(B.BPError) as e:
         ctx.add_two_body(1.0, 0.0, synth.M_AU, 0.01, 12.4e-9, [30.0])  # omega_b dt >= 2
     assert e.value.code == B.BP_ERR_CFL
