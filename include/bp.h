@@ -179,6 +179,25 @@ int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, doubl
  * shape).  dst holds nz*ny*nx doubles (device pointer if on_device). */
 int bp_residual(bp_ctx *ctx, double *dst, int on_device);
 
+/* bp_residual for callers that cannot have the library allocate device
+ * memory during the call.  (The paper has no counterpart: this is an
+ * interface for such callers.)  bp_residual obtains an FP64 scratch grid
+ * through the context's allocator when dst is host memory; a thread that
+ * does not own that allocator, or a run whose device memory is fully
+ * committed, cannot allow that.  This entry point keeps the scratch in a
+ * fixed array of the library's static device memory (32 MiB, present on
+ * every GPU that loads the library until the process exits) and calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ *   dst   host pointer to nz*ny*nx doubles, written with div E - rho.
+ *   Grids of more than 4,194,304 nodes are rejected with BP_ERR_ARG.
+ *   The context's device must be current (else BP_ERR_STATE).  The first
+ *   call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array, which keeps the previous call's values
+ *   (each call clears it first); calls that overlap on the GPU, from any
+ *   contexts of the process, race on it.  Synchronous. */
+int bp_residual_noalloc(bp_ctx *ctx, double *dst);
+
 /* Number of own-kernel launches issued since creation (for accounting). */
 int64_t bp_kernel_launches(const bp_ctx *ctx);
 

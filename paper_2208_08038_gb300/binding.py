@@ -81,6 +81,7 @@ _SIGS = {
     "bp_read_probe": (_i, [_p, _i, _p, _i64, C.POINTER(_i64)]),
     "bp_read_particles": (_i, [_p, _i, _p, _p, _p, _p, _i64, C.POINTER(_i64)]),
     "bp_residual": (_i, [_p, _p, _i]),
+    "bp_residual_noalloc": (_i, [_p, _p]),
     "bp_kernel_launches": (_i64, [_p]),
     "bp_time_push": (_i, [_p, _i]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
@@ -285,6 +286,14 @@ class Context:
         nx, ny, nz = self.n
         out = np.empty(nx * ny * nz, dtype=np.float64)
         self._check(self._L.bp_residual(self._h, _ptr(out), 0), "bp_residual")
+        return out.reshape(nz, ny, nx)
+
+    def residual_noalloc(self) -> np.ndarray:
+        """bp_residual_noalloc: the residual through the library's static
+        scratch (no device allocation during the call)."""
+        nx, ny, nz = self.n
+        out = np.empty(nx * ny * nz, dtype=np.float64)
+        self._check(self._L.bp_residual_noalloc(self._h, _ptr(out)), "bp_residual_noalloc")
         return out.reshape(nz, ny, nx)
 
     def kernel_launches(self) -> int:
