@@ -198,6 +198,42 @@ int bp_residual(bp_ctx *ctx, double *dst, int on_device);
  *   contexts of the process, race on it.  Synchronous. */
 int bp_residual_noalloc(bp_ctx *ctx, double *dst);
 
+/* --- discrete adjoint -------------------------------------------------- */
+
+/* Zero the fields, the step counter and the probe records, and unload the
+ * particles (species and lasers stay; particle arrays are reused by the next
+ * bp_load_particles). */
+int bp_reset(bp_ctx *ctx);
+
+/* Replace the bound-electron frequencies omega_b[n] of a two-body species
+ * (n = its n_omega); a_c follows from w_c^2 = |q1 q2| kappa / (m_r a_c^3). */
+int bp_set_omega(bp_ctx *ctx, int species_id, const double *omega_b, int n);
+
+/* Run n_steps steps like bp_step (probes recorded), keeping the state before
+ * every K-th step (E, B, particles, status) for the reverse pass.  Needs
+ * BP_DEPOSIT_SORTED, whose bit-reproducible steps make the recomputation
+ * exact. */
+int bp_forward_ckpt(bp_ctx *ctx, int64_t n_steps, int K);
+
+/* Reverse pass of the run of the last bp_forward_ckpt: for each segment,
+ * newest first, restore its checkpoint, recompute its K steps storing every
+ * step's state, then apply the transposed step K times (transposed Yee with
+ * Mur faces, Esirkepov deposit transposed as a gather of the current adjoint,
+ * reversed drift, Boris and modified-Coulomb force, gather transposed as a
+ * deposit).  The loss gradient enters as dl_dprobe [n_steps][npts] (host,
+ * FP32): dL/d(sample s of probe probe_id recorded by that run); the probe
+ * must record an E component.  Outputs (host, FP64, reduced on the device in
+ * a fixed order; either may be NULL):
+ *   grad_omega [n_omega]        dL/d omega_b per parameter index of species_id
+ *   grad_group [n_groups][dims] sum over the ions i of group g of dL/dx_i at
+ *                               load time (both bodies start at x_i), with
+ *                               group[n] the caller's group of each ion in
+ *                               load order (e.g. its lattice site).
+ * Afterwards the context holds an intermediate state: call bp_reset before
+ * the next run. */
+int bp_backward(bp_ctx *ctx, int probe_id, const float *dl_dprobe, int species_id, double *grad_omega,
+                const int32_t *group, int64_t n_groups, double *grad_group);
+
 /* Number of own-kernel launches issued since creation (for accounting). */
 int64_t bp_kernel_launches(const bp_ctx *ctx);
 

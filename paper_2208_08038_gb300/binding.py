@@ -82,6 +82,10 @@ _SIGS = {
     "bp_read_particles": (_i, [_p, _i, _p, _p, _p, _p, _i64, C.POINTER(_i64)]),
     "bp_residual": (_i, [_p, _p, _i]),
     "bp_residual_noalloc": (_i, [_p, _p]),
+    "bp_reset": (_i, [_p]),
+    "bp_set_omega": (_i, [_p, _i, _p, _i]),
+    "bp_forward_ckpt": (_i, [_p, _i64, _i]),
+    "bp_backward": (_i, [_p, _i, _p, _i, _p, _p, _i64, _p]),
     "bp_kernel_launches": (_i64, [_p]),
     "bp_time_push": (_i, [_p, _i]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
@@ -295,6 +299,25 @@ class Context:
         out = np.empty(nx * ny * nz, dtype=np.float64)
         self._check(self._L.bp_residual_noalloc(self._h, _ptr(out)), "bp_residual_noalloc")
         return out.reshape(nz, ny, nx)
+
+    def reset(self):
+        self._check(self._L.bp_reset(self._h), "bp_reset")
+
+    def set_omega(self, sid: int, omega_b):
+        om = np.ascontiguousarray(np.atleast_1d(omega_b), dtype=np.float64)
+        self._check(self._L.bp_set_omega(self._h, sid, _ptr(om), len(om)), "bp_set_omega")
+
+    def forward_ckpt(self, nsteps: int, K: int):
+        self._check(self._L.bp_forward_ckpt(self._h, int(nsteps), int(K)), "bp_forward_ckpt")
+
+    def backward(self, pid: int, dl_dprobe, sid: int, n_omega: int, group=None, n_groups: int = 0):
+        dl = np.ascontiguousarray(dl_dprobe, dtype=np.float32)
+        go = np.zeros(n_omega)
+        gg = np.zeros((max(n_groups, 1), self.dims))
+        grp = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+        self._check(self._L.bp_backward(self._h, pid, _ptr(dl), sid, _ptr(go), _ptr(grp), int(n_groups),
+                                        _ptr(gg) if group is not None else None), "bp_backward")
+        return go, gg[:n_groups]
 
     def kernel_launches(self) -> int:
         return int(self._L.bp_kernel_launches(self._h))

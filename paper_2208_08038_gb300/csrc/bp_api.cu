@@ -92,6 +92,16 @@ int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
   const bool two = s.sp.kind == BP_TWO_BODY;
   long long cap = std::max(1LL, n);
   PartP &p = s.p;
+  if (p.cell && p.cap >= cap) {
+    // reload after bp_reset: keep the arrays
+    if (pidx && !p.pidx) p.pidx = (int *)dalloc(c, sizeof(int) * p.cap);
+    if (!pidx) p.pidx = nullptr;
+    return (pidx && !p.pidx) ? fail(c, BP_ERR_OOM, "param index array") : BP_OK;
+  }
+  if (p.cell) {
+    void *old[] = {p.cell, p.off, p.u1, p.id, p.tstart, p.r, p.u2, p.pidx};
+    for (void *q : old) dfree(c, q);
+  }
   p.cap = cap;
   p.cell = (int *)dalloc(c, sizeof(int) * cap);
   p.off = (float *)dalloc(c, sizeof(float) * D * cap);
@@ -307,6 +317,7 @@ int bp_add_species(bp_ctx *c, const bp_species_desc *d, int *id) {
     cudaMemcpyAsync(acd, ac.data(), sizeof(float) * ac.size(), cudaMemcpyHostToDevice, c->stream);
     cudaStreamSynchronize(c->stream);
     p.ac = acd;
+    s.ac_dev = acd;
   } else {
     if (!(d->m > 0)) return fail(c, BP_ERR_ARG, "free species needs m > 0");
     p.q1d = d->q;
@@ -337,6 +348,8 @@ int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, cons
   int rc = alloc_particles(c, s, n, pidx != nullptr);
   if (rc) return rc;
   s.has_pidx = pidx != nullptr;
+  if (pidx) s.pidx_host.assign(pidx, pidx + n);
+  else s.pidx_host.assign((size_t)n, 0);
   cudaStream_t st = c->stream;
   // the caller's arrays are staged on the device in chunks and converted there
   const long long chunk = std::min<long long>(std::max<long long>(n, 1), 1LL << 25);
@@ -389,6 +402,7 @@ int bp_set_medium(bp_ctx *c, int sid, const int64_t lo[3], const int64_t hi[3], 
   if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
   int rc = alloc_particles(c, s, n, false);
   if (rc) return rc;
+  s.pidx_host.assign((size_t)n, 0);
   launch_gen_medium(g, s.sp, s.p, l, h, ppc, seed, sigma_u, 0, n, c->stream);
   c->launches++;
   if ((rc = check_launch(c, "medium generation"))) return rc;
@@ -443,10 +457,11 @@ int bp_add_probe(bp_ctx *c, int comp, const int64_t *nodes, int64_t npts, int64_
   return BP_OK;
 }
 
-int bp_step(bp_ctx *c, int64_t nsteps) {
-  if (!c || nsteps < 0) return BP_ERR_ARG;
-  const GridP &g = c->g;
-  cudaStream_t st = c->stream;
+}  // extern "C"
+
+namespace {
+
+PushArgs push_args(bp_ctx *c, int *nsp_out) {
   PushArgs A;
   memset(&A, 0, sizeof A);
   int nsp = 0;
@@ -466,39 +481,89 @@ int bp_step(bp_ctx *c, int64_t nsteps) {
   A.status = c->status;
   A.jscale = c->jscale;
   A.jinv = c->jinv;
+  *nsp_out = nsp;
+  return A;
+}
+
+// copy of the particle arrays of one species (same capacity)
+int copy_alloc(bp_ctx *c, const PartP &src, int D, bool two, PartP &dst) {
+  dst = src;
+  long long cap = src.cap;
+  dst.cell = (int *)dalloc(c, sizeof(int) * cap);
+  dst.off = (float *)dalloc(c, sizeof(float) * D * cap);
+  dst.u1 = (float *)dalloc(c, sizeof(float) * 3 * cap);
+  dst.id = (int *)dalloc(c, sizeof(int) * cap);
+  dst.tstart = (int *)dalloc(c, sizeof(int) * (c->g.ntiles + 1));
+  dst.r = two ? (float *)dalloc(c, sizeof(float) * 3 * cap) : nullptr;
+  dst.u2 = two ? (float *)dalloc(c, sizeof(float) * 3 * cap) : nullptr;
+  dst.pidx = src.pidx ? (int *)dalloc(c, sizeof(int) * cap) : nullptr;
+  if (!dst.cell || !dst.off || !dst.u1 || !dst.id || !dst.tstart || (two && (!dst.r || !dst.u2)) ||
+      (src.pidx && !dst.pidx))
+    return BP_ERR_OOM;
+  return BP_OK;
+}
+
+void copy_parts(bp_ctx *c, const PartP &src, PartP &dst, int D, bool two) {
+  cudaStream_t st = c->stream;
+  long long cap = src.cap;
+  cudaMemcpyAsync(dst.cell, src.cell, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst.off, src.off, sizeof(float) * D * cap, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst.u1, src.u1, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst.id, src.id, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst.tstart, src.tstart, sizeof(int) * (c->g.ntiles + 1), cudaMemcpyDeviceToDevice, st);
+  if (two) {
+    cudaMemcpyAsync(dst.r, src.r, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dst.u2, src.u2, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
+  }
+  if (src.pidx) cudaMemcpyAsync(dst.pidx, src.pidx, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
+}
+
+// one leapfrog step; when snap_fields is given, E^n and B^n (after the first
+// half step) and the particle state before the push are copied there
+int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fields,
+             std::vector<bp_part_copy> *snap_parts) {
+  const GridP &g = c->g;
+  cudaStream_t st = c->stream;
   float *E[3] = {c->F[0], c->F[1], c->F[2]}, *B[3] = {c->F[3], c->F[4], c->F[5]}, *J[3] = {c->F[6], c->F[7], c->F[8]};
   const float *cE[3] = {E[0], E[1], E[2]}, *cB[3] = {B[0], B[1], B[2]}, *cJ[3] = {J[0], J[1], J[2]};
   int nopen = 0;
   for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
-  for (int64_t it = 0; it < nsteps; ++it) {
-    // re-sort when a particle left its tile margin in the previous step
-    if (nsp) {
-      for (auto &s : c->sp)
-        if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
-      launch_clear_sort_flag(c->status, st);
-      c->launches += nsp * sort_launches() + 1;
-    }
-    launch_yee_b(g, B, cE, 0.5f * g.dt, st);
-    if (c->timing) {
-      if (c->ev_used + 2 > c->ev.size()) {
-        for (int k = 0; k < 64; ++k) {
-          cudaEvent_t e;
-          cudaEventCreate(&e);
-          c->ev.push_back(e);
-        }
+  // re-sort when a particle left its tile margin in the previous step
+  if (nsp) {
+    for (auto &s : c->sp)
+      if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
+    launch_clear_sort_flag(c->status, st);
+    c->launches += nsp * sort_launches() + 1;
+  }
+  launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+  if (snap_fields) {
+    for (int k = 0; k < 6; ++k)
+      cudaMemcpyAsync(snap_fields + (size_t)k * g.ncell, c->F[k], sizeof(float) * g.ncell, cudaMemcpyDeviceToDevice, st);
+    int q = 0;
+    for (auto &s : c->sp)
+      if (s.loaded) copy_parts(c, s.p, (*snap_parts)[q++].p, g.D, s.sp.kind == BP_TWO_BODY);
+  }
+  if (c->timing) {
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev.push_back(e);
       }
-      cudaEventRecord(c->ev[c->ev_used], st);
     }
-    launch_push(g, A, st);
-    if (c->timing) {
-      cudaEventRecord(c->ev[c->ev_used + 1], st);
-      c->ev_used += 2;
-    }
-    launch_jsum(g, c->jbox, c->occ, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
-    launch_yee_b(g, B, cE, 0.5f * g.dt, st);
-    launch_yee_e(g, E, cB, cJ, c->frame, st);
-    c->launches += 5 + (nopen ? 1 + nopen : 0);
-    c->step++;
+    cudaEventRecord(c->ev[c->ev_used], st);
+  }
+  launch_push(g, A, st);
+  if (c->timing) {
+    cudaEventRecord(c->ev[c->ev_used + 1], st);
+    c->ev_used += 2;
+  }
+  launch_jsum(g, c->jbox, c->occ, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
+  launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+  launch_yee_e(g, E, cB, cJ, c->frame, st);
+  c->launches += 5 + (nopen ? 1 + nopen : 0);
+  c->step++;
+  if (probes) {
     for (auto &p : c->pr) {
       if (p.count < p.cap) {
         launch_probe(c->F[p.comp], p.nodes, p.npts, p.buf, p.count, st);
@@ -506,7 +571,20 @@ int bp_step(bp_ctx *c, int64_t nsteps) {
         p.count++;
       }
     }
-    int rc = check_launch(c, "step");
+  }
+  return check_launch(c, "step");
+}
+
+}  // namespace
+
+extern "C" {
+
+int bp_step(bp_ctx *c, int64_t nsteps) {
+  if (!c || nsteps < 0) return BP_ERR_ARG;
+  int nsp = 0;
+  PushArgs A = push_args(c, &nsp);
+  for (int64_t it = 0; it < nsteps; ++it) {
+    int rc = one_step(c, A, nsp, true, nullptr, nullptr);
     if (rc) return rc;
   }
   return BP_OK;
@@ -656,6 +734,297 @@ int bp_push_time(bp_ctx *c, double *ms, int64_t *launches) {
   if (!c) return BP_ERR_ARG;
   if (ms) *ms = c->push_ms;
   if (launches) *launches = c->push_launches;
+  return BP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// reset, parameters, checkpointed forward and the discrete adjoint
+
+extern "C" {
+
+int bp_reset(bp_ctx *c) {
+  if (!c) return BP_ERR_ARG;
+  cudaStream_t st = c->stream;
+  for (int k = 0; k < 9; ++k) cudaMemsetAsync(c->F[k], 0, sizeof(float) * c->g.ncell, st);
+  cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st);
+  c->step = 0;
+  for (auto &p : c->pr) p.count = 0;
+  for (auto &s : c->sp) s.loaded = false;
+  c->adj.ready = false;
+  cudaError_t e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "reset");
+}
+
+int bp_set_omega(bp_ctx *c, int sid, const double *omega_b, int n) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size() || !omega_b) return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (s.sp.kind != BP_TWO_BODY || n != s.sp.nac) return fail(c, BP_ERR_ARG, "bp_set_omega: %d values for %d", n, s.sp.nac);
+  const double mr = s.sp.m1d * s.sp.m2d / (s.sp.m1d + s.sp.m2d);
+  std::vector<float> ac(n);
+  for (int i = 0; i < n; ++i) {
+    double w = omega_b[i];
+    if (!(w > 0)) return fail(c, BP_ERR_ARG, "omega_b must be positive");
+    if (w * c->g.dtd >= 2.0) return fail(c, BP_ERR_CFL, "omega_b dt = %g >= 2", w * c->g.dtd);
+    ac[i] = (float)std::cbrt(std::fabs(s.sp.q1d * s.sp.q2d) * (double)s.sp.kappa / (mr * w * w));
+    s.omega[i] = w;
+  }
+  cudaMemcpyAsync(s.ac_dev, ac.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "set omega");
+}
+
+int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
+  if (!c || nsteps < 1 || K < 1) return BP_ERR_ARG;
+  if (!c->det) return fail(c, BP_ERR_STATE, "the adjoint needs the sorted (bit-reproducible) deposit");
+  const GridP &g = c->g;
+  bp_adjoint &ad = c->adj;
+  const int nseg = (int)((nsteps + K - 1) / K);
+  // checkpoint storage (reused when it is large enough)
+  bool caps_ok = !ad.ck_parts.empty() && ad.ck_parts[0].size() == c->sp.size();
+  for (size_t q = 0; caps_ok && q < c->sp.size(); ++q)
+    caps_ok = ad.ck_parts[0][q].p.cap == c->sp[q].p.cap && (ad.ck_parts[0][q].p.pidx != nullptr) == (c->sp[q].p.pidx != nullptr);
+  if (ad.K != K || ad.nseg < nseg || !caps_ok) {
+    for (float *p : ad.ck_fields) dfree(c, p);
+    for (float *p : ad.st_fields) dfree(c, p);
+    for (auto &v : ad.ck_parts)
+      for (auto &q : v) {
+        void *a[] = {q.p.cell, q.p.off, q.p.u1, q.p.id, q.p.tstart, q.p.r, q.p.u2, q.p.pidx};
+        for (void *x : a) dfree(c, x);
+      }
+    for (auto &v : ad.st_parts)
+      for (auto &q : v) {
+        void *a[] = {q.p.cell, q.p.off, q.p.u1, q.p.id, q.p.tstart, q.p.r, q.p.u2, q.p.pidx};
+        for (void *x : a) dfree(c, x);
+      }
+    ad.ck_fields.assign(nseg, nullptr);
+    ad.ck_parts.assign(nseg, std::vector<bp_part_copy>(c->sp.size()));
+    ad.st_fields.assign(K, nullptr);
+    ad.st_parts.assign(K, std::vector<bp_part_copy>(c->sp.size()));
+    for (int k = 0; k < nseg; ++k) {
+      ad.ck_fields[k] = (float *)dalloc(c, sizeof(float) * 6 * g.ncell);
+      if (!ad.ck_fields[k]) return fail(c, BP_ERR_OOM, "checkpoint fields");
+      for (size_t q = 0; q < c->sp.size(); ++q)
+        if (copy_alloc(c, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY, ad.ck_parts[k][q].p))
+          return fail(c, BP_ERR_OOM, "checkpoint particles");
+    }
+    for (int k = 0; k < K; ++k) {
+      ad.st_fields[k] = (float *)dalloc(c, sizeof(float) * 6 * g.ncell);
+      if (!ad.st_fields[k]) return fail(c, BP_ERR_OOM, "step store fields");
+      for (size_t q = 0; q < c->sp.size(); ++q)
+        if (copy_alloc(c, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY, ad.st_parts[k][q].p))
+          return fail(c, BP_ERR_OOM, "step store particles");
+    }
+    dfree(c, ad.ck_status);
+    ad.ck_status = (int *)dalloc(c, sizeof(int) * 4 * nseg);
+    if (!ad.ck_status) return fail(c, BP_ERR_OOM, "checkpoint status");
+    ad.K = K;
+    ad.nseg = nseg;
+  }
+  for (auto &s : c->sp)
+    if (!s.loaded) return fail(c, BP_ERR_STATE, "every species must be loaded before bp_forward_ckpt");
+  ad.start = c->step;
+  ad.nsteps = nsteps;
+  ad.probe_c0.clear();
+  for (auto &p : c->pr) ad.probe_c0.push_back(p.count);
+  int nsp = 0;
+  PushArgs A = push_args(c, &nsp);
+  cudaStream_t st = c->stream;
+  for (int k = 0; k < nseg; ++k) {
+    // the state before step start + k K: E, B^{n-1/2}, particles
+    for (int f = 0; f < 6; ++f)
+      cudaMemcpyAsync(ad.ck_fields[k] + (size_t)f * g.ncell, c->F[f], sizeof(float) * g.ncell,
+                      cudaMemcpyDeviceToDevice, st);
+    for (size_t q = 0; q < c->sp.size(); ++q)
+      copy_parts(c, c->sp[q].p, ad.ck_parts[k][q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
+    cudaMemcpyAsync(ad.ck_status + 4 * k, c->status, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st);
+    long long len = std::min<long long>(K, nsteps - (long long)k * K);
+    for (long long j = 0; j < len; ++j) {
+      int rc = one_step(c, A, nsp, true, nullptr, nullptr);
+      if (rc) return rc;
+    }
+  }
+  ad.ready = true;
+  return BP_OK;
+}
+
+int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double *grad_omega, const int32_t *group,
+                int64_t n_groups, double *grad_group) {
+  if (!c || probe_id < 0 || probe_id >= (int)c->pr.size() || !dl_dprobe || sid < 0 || sid >= (int)c->sp.size())
+    return BP_ERR_ARG;
+  bp_adjoint &ad = c->adj;
+  if (!ad.ready) return fail(c, BP_ERR_STATE, "bp_backward needs a preceding bp_forward_ckpt");
+  const GridP &g = c->g;
+  cudaStream_t st = c->stream;
+  Probe &P = c->pr[probe_id];
+  if (P.comp > 2) return fail(c, BP_ERR_ARG, "bp_backward: the loss probe must record an E component");
+  const long long c0 = ad.probe_c0[probe_id];
+  const long long nrec = std::min<long long>(ad.nsteps, P.cap - c0);
+  if (adj_prepare(g.D)) return fail(c, BP_ERR_CUDA, "adjoint kernel set-up");
+  // buffers
+  if (!ad.lamE[0]) {
+    for (int k = 0; k < 3; ++k) {
+      ad.lamE[k] = (float *)dalloc(c, sizeof(float) * g.ncell);
+      ad.lamB[k] = (float *)dalloc(c, sizeof(float) * g.ncell);
+      ad.lamJ[k] = (float *)dalloc(c, sizeof(float) * g.ncell);
+      ad.H[k] = (float *)dalloc(c, sizeof(float) * g.ncell);
+      if (!ad.lamE[k] || !ad.lamB[k] || !ad.lamJ[k] || !ad.H[k]) return fail(c, BP_ERR_OOM, "adjoint fields");
+    }
+    ad.box = (float *)dalloc(c, sizeof(float) * 6 * (size_t)g.gcells * g.ntiles);
+    ad.occ = (unsigned char *)dalloc(c, g.ntiles);
+    if (!ad.box || !ad.occ) return fail(c, BP_ERR_OOM, "adjoint boxes");
+  }
+  bool xb_ok = ad.xb.size() == c->sp.size() && ad.xb_cap.size() == c->sp.size();
+  for (size_t q = 0; xb_ok && q < c->sp.size(); ++q) xb_ok = ad.xb_cap[q] == c->sp[q].p.cap;
+  if (!xb_ok) {
+    for (auto p : ad.xb) dfree(c, p);
+    for (auto p : ad.acb) dfree(c, p);
+    ad.xb.assign(c->sp.size(), nullptr);
+    ad.acb.assign(c->sp.size(), nullptr);
+    ad.xb_cap.assign(c->sp.size(), 0);
+    for (size_t q = 0; q < c->sp.size(); ++q) {
+      ad.xb[q] = (float *)dalloc(c, sizeof(float) * 12 * c->sp[q].p.cap);
+      ad.acb[q] = (double *)dalloc(c, sizeof(double) * c->sp[q].p.cap);
+      if (!ad.xb[q] || !ad.acb[q]) return fail(c, BP_ERR_OOM, "particle adjoints");
+      ad.xb_cap[q] = c->sp[q].p.cap;
+    }
+  }
+  long long need = std::max<long long>(1, nrec * P.npts);
+  if (ad.dl_len < need) {
+    dfree(c, ad.dl);
+    ad.dl = (float *)dalloc(c, sizeof(float) * need);
+    if (!ad.dl) return fail(c, BP_ERR_OOM, "probe gradient");
+    ad.dl_len = need;
+  }
+  if (nrec > 0) cudaMemcpyAsync(ad.dl, dl_dprobe, sizeof(float) * nrec * P.npts, cudaMemcpyHostToDevice, st);
+  for (int k = 0; k < 3; ++k) {
+    cudaMemsetAsync(ad.lamE[k], 0, sizeof(float) * g.ncell, st);
+    cudaMemsetAsync(ad.lamB[k], 0, sizeof(float) * g.ncell, st);
+  }
+  for (size_t q = 0; q < c->sp.size(); ++q) {
+    cudaMemsetAsync(ad.xb[q], 0, sizeof(float) * 12 * c->sp[q].p.cap, st);
+    cudaMemsetAsync(ad.acb[q], 0, sizeof(double) * c->sp[q].p.cap, st);
+  }
+  int nsp = 0;
+  PushArgs A = push_args(c, &nsp);
+  std::vector<SpecP> sps;
+  std::vector<float *> xbs;
+  std::vector<double *> acbs;
+  std::vector<long long> caps;
+  for (size_t q = 0; q < c->sp.size(); ++q) {
+    sps.push_back(c->sp[q].sp);
+    xbs.push_back(ad.xb[q]);
+    acbs.push_back(ad.acb[q]);
+    caps.push_back(c->sp[q].p.cap);
+  }
+  for (int seg = ad.nseg - 1; seg >= 0; --seg) {
+    // restore the checkpoint and recompute the segment, storing each step
+    for (int f = 0; f < 6; ++f)
+      cudaMemcpyAsync(c->F[f], ad.ck_fields[seg] + (size_t)f * g.ncell, sizeof(float) * g.ncell,
+                      cudaMemcpyDeviceToDevice, st);
+    for (size_t q = 0; q < c->sp.size(); ++q)
+      copy_parts(c, ad.ck_parts[seg][q].p, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
+    cudaMemcpyAsync(c->status, ad.ck_status + 4 * seg, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st);
+    const long long base = (long long)seg * ad.K;
+    const long long len = std::min<long long>(ad.K, ad.nsteps - base);
+    c->step = ad.start + base;
+    for (long long j = 0; j < len; ++j) {
+      int rc = one_step(c, A, nsp, false, ad.st_fields[j], &ad.st_parts[j]);
+      if (rc) return rc;
+    }
+    for (long long j = len - 1; j >= 0; --j) {
+      const long long n = base + j;  // step n maps state n to n + 1
+      // loss on the probe sample recorded after step n
+      if (n < nrec) {
+        launch_adj_inject(ad.lamE[P.comp], P.nodes, P.npts, ad.dl + n * P.npts, st);
+        c->launches++;
+      }
+      // E update with Mur faces, transposed
+      for (int k = 0; k < 3; ++k) cudaMemsetAsync(ad.H[k], 0, sizeof(float) * g.ncell, st);
+      launch_adj_e(g, ad.lamE, ad.H, ad.lamB, ad.lamJ, st);
+      for (int k = 0; k < 3; ++k) std::swap(ad.lamE[k], ad.H[k]);
+      // B^{n+1/2} = B^n - dt/2 curl E^n
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, st);
+      // particles, with E^n, B^n and the particle state stored for step n
+      const float *En[3], *Bn[3], *lJ[3] = {ad.lamJ[0], ad.lamJ[1], ad.lamJ[2]};
+      for (int k = 0; k < 3; ++k) {
+        En[k] = ad.st_fields[j] + (size_t)k * g.ncell;
+        Bn[k] = ad.st_fields[j] + (size_t)(3 + k) * g.ncell;
+      }
+      std::vector<PartP> pp;
+      for (size_t q = 0; q < c->sp.size(); ++q) pp.push_back(ad.st_parts[j][q].p);
+      launch_adj_push(g, (int)c->sp.size(), sps.data(), pp.data(), xbs.data(), acbs.data(), caps.data(), En, Bn, lJ,
+                      ad.box, ad.occ, ad.lamE, ad.lamB, st);
+      // B^n = B^{n-1/2} - dt/2 curl E^n
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, st);
+      c->launches += 6;
+      int rc = check_launch(c, "backward step");
+      if (rc) return rc;
+    }
+  }
+  // FP64 reductions in a fixed order: parameters and groups (CSR over load order)
+  Species &S = c->sp[sid];
+  const long long n = S.n;
+  std::vector<int> ptr, ids;
+  auto build_csr = [&](const int32_t *key, long long nrows) {
+    ptr.assign(nrows + 1, 0);
+    for (long long i = 0; i < n; ++i) ptr[key[i] + 1]++;
+    for (long long r = 0; r < nrows; ++r) ptr[r + 1] += ptr[r];
+    ids.assign(n, 0);
+    std::vector<int> cur(ptr.begin(), ptr.end() - 1);
+    for (long long i = 0; i < n; ++i) ids[cur[key[i]]++] = (int)i;
+  };
+  int *dptr = nullptr, *dids = nullptr;
+  double *dout = nullptr, *dscale = nullptr;
+  const long long nrow_max = std::max<long long>(S.sp.nac, n_groups) + 1;
+  dptr = (int *)dalloc(c, sizeof(int) * (nrow_max + 1));
+  dids = (int *)dalloc(c, sizeof(int) * std::max<long long>(1, n));
+  dout = (double *)dalloc(c, sizeof(double) * nrow_max * 3);
+  dscale = (double *)dalloc(c, sizeof(double) * nrow_max);
+  if (!dptr || !dids || !dout || !dscale) return fail(c, BP_ERR_OOM, "reduction buffers");
+  int rc = BP_OK;
+  if (grad_omega && S.sp.kind == BP_TWO_BODY) {
+    for (long long i = 0; i < n; ++i)
+      if (S.pidx_host[i] < 0 || S.pidx_host[i] >= S.sp.nac) rc = BP_ERR_STATE;
+    if (!rc) {
+      build_csr(S.pidx_host.data(), S.sp.nac);
+      // a_c = (|q1 q2| kappa / (m_r w^2))^{1/3}: d a_c / d w = -2 a_c / (3 w)
+      std::vector<double> scale(S.sp.nac);
+      const double mr = S.sp.m1d * S.sp.m2d / (S.sp.m1d + S.sp.m2d);
+      for (int p = 0; p < S.sp.nac; ++p) {
+        double w = S.omega[p];
+        double ac = std::cbrt(std::fabs(S.sp.q1d * S.sp.q2d) * (double)S.sp.kappa / (mr * w * w));
+        scale[p] = -2.0 * ac / (3.0 * w);
+      }
+      cudaMemcpyAsync(dptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(dids, ids.data(), sizeof(int) * std::max<long long>(1, n), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * scale.size(), cudaMemcpyHostToDevice, st);
+      launch_csr_sum(dptr, dids, S.sp.nac, ad.xb[sid], S.p.cap, 1, ad.acb[sid], dscale, dout, st);
+      cudaMemcpyAsync(grad_omega, dout, sizeof(double) * S.sp.nac, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+    }
+  }
+  if (!rc && grad_group && group && n_groups > 0) {
+    for (long long i = 0; i < n; ++i)
+      if (group[i] < 0 || group[i] >= n_groups) rc = BP_ERR_ARG;
+    if (!rc) {
+      build_csr(group, n_groups);
+      cudaMemcpyAsync(dptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(dids, ids.data(), sizeof(int) * std::max<long long>(1, n), cudaMemcpyHostToDevice, st);
+      launch_csr_sum(dptr, dids, (int)n_groups, ad.xb[sid], S.p.cap, g.D, nullptr, nullptr, dout, st);
+      cudaMemcpyAsync(grad_group, dout, sizeof(double) * n_groups * g.D, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  dfree(c, dptr);
+  dfree(c, dids);
+  dfree(c, dout);
+  dfree(c, dscale);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward");
+  if (rc) return fail(c, rc, "bp_backward: bad parameter or group index");
+  c->launches += 2;
   return BP_OK;
 }
 

@@ -6,12 +6,39 @@
 #include "bp_internal.cuh"
 
 struct bp_species_state {
-  SpecP sp;
-  PartP p;
+  SpecP sp{};
+  PartP p{};  // null until the first load (alloc_particles tests p.cell)
   long long n = 0;       // particles loaded (before any removal)
   bool loaded = false;
   bool has_pidx = false;
   std::vector<double> omega;
+  std::vector<int> pidx_host;  // parameter index per particle, load order
+  float *ac_dev = nullptr;
+};
+
+// particle arrays copied aside (checkpoints, per-step stores of the adjoint)
+struct bp_part_copy {
+  PartP p{};
+};
+
+struct bp_adjoint {
+  bool ready = false;
+  int K = 0, nseg = 0;
+  long long start = 0, nsteps = 0;
+  std::vector<long long> probe_c0;
+  std::vector<float *> ck_fields;                   // [nseg] E, B (6 ncell)
+  int *ck_status = nullptr;                         // [nseg][4] device status words
+  std::vector<std::vector<bp_part_copy>> ck_parts;  // [nseg][species]
+  std::vector<float *> st_fields;                   // [K] E^n, B^n
+  std::vector<std::vector<bp_part_copy>> st_parts;  // [K][species]
+  float *lamE[3] = {}, *lamB[3] = {}, *lamJ[3] = {}, *H[3] = {};
+  float *box = nullptr;
+  unsigned char *occ = nullptr;
+  std::vector<float *> xb;     // per species [12][cap]
+  std::vector<double *> acb;   // per species [cap]
+  std::vector<long long> xb_cap;
+  float *dl = nullptr;         // probe-loss gradient on the device
+  long long dl_len = 0;
 };
 
 struct bp_probe_state {
@@ -49,4 +76,5 @@ struct bp_ctx {
   std::vector<void *> owned;
   std::string err;
   float jscale = 0.0f, jinv = 0.0f;
+  bp_adjoint adj;
 };

@@ -204,3 +204,16 @@ void launch_load_convert(const GridP &g, const SpecP &sp, PartP &p, const double
                          long long first, long long count, int *status, cudaStream_t s);
 void launch_rho(const GridP &g, const SpecP &sp, const PartP &p, double *rho, cudaStream_t s);
 void launch_divE_minus(const GridP &g, const float *const E[3], double *R, cudaStream_t s);
+
+// adjoint
+void launch_adj_inject(float *lam, const long long *nodes, long long npts, const float *dl, cudaStream_t s);
+void launch_adj_e(const GridP &g, float *G[3], float *H[3], float *lamB[3], float *lamJ[3], cudaStream_t s);
+void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, cudaStream_t s);
+size_t adj_push_smem(int D);
+int adj_prepare(int D);
+void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
+                     const long long *cap, const float *const E[3], const float *const B[3],
+                     const float *const lamJ[3], float *box, unsigned char *occ, float *lamE[3], float *lamB[3],
+                     cudaStream_t s);
+void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
+                    const double *acb, const double *scale, double *out, cudaStream_t s);

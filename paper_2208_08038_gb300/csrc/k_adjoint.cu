@@ -1,0 +1,839 @@
+// k_adjoint.cu -- discrete adjoint of the PIC step (reverse mode), FP32 with
+// FP64 parameter-gradient reductions.
+//
+// Each forward operator is replaced by its transpose or vector-Jacobian
+// product, applied in reverse order:
+//   E^{n+1} = E^n + dt (curl B^{n+1/2} - J) with Mur faces  ->  k_adj_mur (last
+//       pass first) + k_adj_e (gathers curl^T of the interior adjoint, J adjoint)
+//   B^{n+1/2} = B^n - dt/2 curl E^n                          ->  k_adj_b
+//   per particle: Esirkepov deposit, drift, Boris, internal modified-Coulomb
+//       field (arXiv 2208.08038 Sec. 2), gather              ->  k_adj_push
+//       (the deposit's transpose reads the current adjoint like a gather; the
+//       gather's transpose scatters like a deposit, into a shared-memory box)
+//   B^n = B^{n-1/2} - dt/2 curl E^n                          ->  k_adj_b
+// The particle adjoints are indexed by load order, so re-sorting between
+// steps does not disturb them.
+#include "bp_internal.cuh"
+#include "bp_particle.cuh"
+
+namespace {
+
+int blocks_for(long long n, int bs) {
+  long long b = (n + bs - 1) / bs;
+  long long cap = 152LL * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+__device__ __forceinline__ void coords(const GridP &g, long long q, int c[3]) {
+  c[0] = (int)(q % g.n[0]);
+  long long r = q / g.n[0];
+  c[1] = (int)(r % g.n[1]);
+  c[2] = (int)(r / g.n[1]);
+}
+
+
+
+__device__ __forceinline__ bool ext(const GridP &g, int pat, const int c[3]) {
+  bool e = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.D && g.bc[a] == BP_OPEN && ((pat >> a) & 1)) e |= c[a] == g.n[a] - 1;
+  return e;
+}
+__device__ __forceinline__ int nbnd(const GridP &g, int pat, const int c[3], int *first) {
+  int k = 0;
+  *first = -1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < g.D && g.bc[a] == BP_OPEN && !((pat >> a) & 1) && (c[a] == 0 || c[a] == g.n[a] - 1)) {
+      if (*first < 0) *first = a;
+      ++k;
+    }
+  return k;
+}
+// E component comp updated by the interior formula at c
+__device__ __forceinline__ bool e_interior(const GridP &g, int comp, const int c[3]) {
+  int f;
+  return !ext(g, 1 << comp, c) && nbnd(g, 1 << comp, c, &f) == 0;
+}
+// value of G masked to interior E nodes (0 off the grid)
+__device__ __forceinline__ float gint(const GridP &g, const float *G, int comp, const int c[3], int a, int o) {
+  int x[3] = {c[0], c[1], c[2]};
+  if (o) {
+    x[a] += o;
+    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_mod(x[a], g.n[a]);
+    if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
+  }
+  if (!e_interior(g, comp, x)) return 0.0f;
+  return G[x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2])];
+}
+// B adjoint masked to non-exterior B nodes
+__device__ __forceinline__ float bnx(const GridP &g, const float *Bb, int comp, const int c[3], int a, int o) {
+  static constexpr int pat[3] = {6, 5, 3};
+  int x[3] = {c[0], c[1], c[2]};
+  if (o) {
+    x[a] += o;
+    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_mod(x[a], g.n[a]);
+    if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
+  }
+  if (ext(g, pat[comp], x)) return 0.0f;
+  return Bb[x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2])];
+}
+
+__global__ void k_adj_inject(float *lam, const long long *nodes, long long npts, const float *dl) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
+    atomicAdd(lam + nodes[q], dl[q]);
+}
+
+// Mur faces, one (pass, axis) per launch: E_b(n+1) = E_a(n) + k (E_a(n+1) - E_b(n))
+__global__ void k_adj_mur(GridP g, float *G0, float *G1, float *G2, float *H0, float *H1, float *H2, int axis,
+                          int pass) {
+  float *G[3] = {G0, G1, G2}, *H[3] = {H0, H1, H2};
+  const int a = axis;
+  const long long F = g.ncell / g.n[a];
+  const long long total = 4 * F;  // 2 sides x 2 tangential components
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long pos = q % F;
+    int t = (int)(q / F);
+    int ci = t & 1, side = t >> 1;
+    int comp = ci == 0 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2);
+    int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+    int lo = o1 < o2 ? o1 : o2, hi = o1 < o2 ? o2 : o1;
+    int c[3];
+    c[lo] = (int)(pos % g.n[lo]);
+    c[hi] = (int)(pos / g.n[lo]);
+    c[a] = side == 0 ? 0 : g.n[a] - 1;
+    int first;
+    if (ext(g, 1 << comp, c)) continue;
+    if (nbnd(g, 1 << comp, c, &first) != pass || first != a) continue;
+    int ca[3] = {c[0], c[1], c[2]};
+    ca[a] += side == 0 ? 1 : -1;
+    long long id = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+    long long ida = ca[0] + (long long)g.n[0] * (ca[1] + (long long)g.n[1] * ca[2]);
+    float km = (g.dt - g.dx[a]) / (g.dt + g.dx[a]);
+    float v = G[comp][id];
+    H[comp][ida] += v;
+    G[comp][ida] += km * v;
+    H[comp][id] -= km * v;
+    G[comp][id] = 0.0f;
+  }
+}
+
+// interior E update transposed: H += G (interior and exterior nodes),
+// lamJ = -dt G (interior), lamB += dt curl_B^T (G on interior nodes)
+__global__ void k_adj_e(GridP g, const float *G0, const float *G1, const float *G2, float *H0, float *H1, float *H2,
+                        float *B0, float *B1, float *B2, float *J0, float *J1, float *J2) {
+  const float *G[3] = {G0, G1, G2};
+  float *H[3] = {H0, H1, H2}, *J[3] = {J0, J1, J2};
+  const bool y = g.D >= 2, z = g.D >= 3;
+  const float dt = g.dt;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords(g, q, c);
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const bool ex = ext(g, 1 << comp, c);
+      const bool in = e_interior(g, comp, c);
+      const float v = G[comp][q];
+      if (in || ex) H[comp][q] += v;
+      J[comp][q] = in ? -dt * v : 0.0f;
+    }
+    // B_x: +dt (g_y[q] - g_y[q+z])/dz - dt (g_z[q] - g_z[q+y])/dy
+    float bx = 0.0f, by = 0.0f, bz = 0.0f;
+    if (z) bx += (gint(g, G[1], 1, c, 2, 0) - gint(g, G[1], 1, c, 2, 1)) * g.idx[2];
+    if (y) bx -= (gint(g, G[2], 2, c, 1, 0) - gint(g, G[2], 2, c, 1, 1)) * g.idx[1];
+    // B_y: -dt (g_x[q] - g_x[q+z])/dz + dt (g_z[q] - g_z[q+x])/dx
+    if (z) by -= (gint(g, G[0], 0, c, 2, 0) - gint(g, G[0], 0, c, 2, 1)) * g.idx[2];
+    by += (gint(g, G[2], 2, c, 0, 0) - gint(g, G[2], 2, c, 0, 1)) * g.idx[0];
+    // B_z: +dt (g_x[q] - g_x[q+y])/dy - dt (g_y[q] - g_y[q+x])/dx
+    if (y) bz += (gint(g, G[0], 0, c, 1, 0) - gint(g, G[0], 0, c, 1, 1)) * g.idx[1];
+    bz -= (gint(g, G[1], 1, c, 0, 0) - gint(g, G[1], 1, c, 0, 1)) * g.idx[0];
+    B0[q] += dt * bx;
+    B1[q] += dt * by;
+    B2[q] += dt * bz;
+  }
+}
+
+// B <- B - h curl E transposed: E adjoint -= h curl_E^T (B adjoint on
+// non-exterior B nodes); the B adjoint itself passes through
+__global__ void k_adj_b(GridP g, float *E0, float *E1, float *E2, const float *B0, const float *B1, const float *B2,
+                        float h) {
+  const float *Bb[3] = {B0, B1, B2};
+  const bool y = g.D >= 2, z = g.D >= 3;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords(g, q, c);
+    // (curl_E^T b) at the E locations, b the B adjoint on non-exterior nodes
+    float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+    if (z) ex += (bnx(g, Bb[1], 1, c, 2, -1) - bnx(g, Bb[1], 1, c, 2, 0)) * g.idx[2];
+    if (y) ex -= (bnx(g, Bb[2], 2, c, 1, -1) - bnx(g, Bb[2], 2, c, 1, 0)) * g.idx[1];
+    if (z) ey -= (bnx(g, Bb[0], 0, c, 2, -1) - bnx(g, Bb[0], 0, c, 2, 0)) * g.idx[2];
+    ey += (bnx(g, Bb[2], 2, c, 0, -1) - bnx(g, Bb[2], 2, c, 0, 0)) * g.idx[0];
+    if (y) ez += (bnx(g, Bb[0], 0, c, 1, -1) - bnx(g, Bb[0], 0, c, 1, 0)) * g.idx[1];
+    ez -= (bnx(g, Bb[1], 1, c, 0, -1) - bnx(g, Bb[1], 1, c, 0, 0)) * g.idx[0];
+    E0[q] -= h * ex;
+    E1[q] -= h * ey;
+    E2[q] -= h * ez;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// particles
+
+__device__ __forceinline__ float dqshape(float x) {
+  float a = fabsf(x);
+  if (a <= 0.5f) return -2.0f * x;
+  if (a < 1.5f) return (x > 0.0f ? -1.0f : 1.0f) * (1.5f - a);
+  return 0.0f;
+}
+
+// reverse of boris(): given the adjoint of the pushed momentum, the adjoints
+// of the old momentum, E and B
+__device__ void boris_adj(float h, const float E[3], const float B[3], const float u0[3], const float ubn[3],
+                          float ub0[3], float Eb[3], float Bb[3]) {
+  float um[3], t[3], sv[3], c1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) um[a] = u0[a] + h * E[a];
+  float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) t[a] = h * B[a] / gm;
+  float t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) sv[a] = 2.0f * t[a] / (1.0f + t2);
+  c1[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+  c1[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+  c1[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+  float umb[3], cb[3], sb[3], tb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Eb[a] = h * ubn[a];
+    umb[a] = ubn[a];
+  }
+  cb[0] = sv[1] * ubn[2] - sv[2] * ubn[1];
+  cb[1] = sv[2] * ubn[0] - sv[0] * ubn[2];
+  cb[2] = sv[0] * ubn[1] - sv[1] * ubn[0];
+  sb[0] = ubn[1] * c1[2] - ubn[2] * c1[1];
+  sb[1] = ubn[2] * c1[0] - ubn[0] * c1[2];
+  sb[2] = ubn[0] * c1[1] - ubn[1] * c1[0];
+  umb[0] += cb[0] + (t[1] * cb[2] - t[2] * cb[1]);
+  umb[1] += cb[1] + (t[2] * cb[0] - t[0] * cb[2]);
+  umb[2] += cb[2] + (t[0] * cb[1] - t[1] * cb[0]);
+  tb[0] = cb[1] * um[2] - cb[2] * um[1];
+  tb[1] = cb[2] * um[0] - cb[0] * um[2];
+  tb[2] = cb[0] * um[1] - cb[1] * um[0];
+  float ts = t[0] * sb[0] + t[1] * sb[1] + t[2] * sb[2];
+  float i1 = 1.0f / (1.0f + t2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) tb[a] += 2.0f * sb[a] * i1 - 4.0f * t[a] * ts * i1 * i1;
+  float gmb = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Bb[a] = h * tb[a] / gm;
+    gmb -= h * B[a] * tb[a] / (gm * gm);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    umb[a] += um[a] * gmb / gm;
+    ub0[a] = umb[a];
+    Eb[a] += h * umb[a];
+  }
+}
+
+// gather transposed for one component of stagger PAT at one body: scatter
+// e * weights into the accumulator box, add e * d(interpolated field)/dX
+template <int D, int PAT>
+__device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, float *Acc, const int d[3],
+                                                const float f[3], float e, float Xb[3]) {
+  constexpr int gb0 = Box<D>::G0, gb1 = Box<D>::G1;
+  int b[3];
+  float w[3][3], dw[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      const bool half = (PAT >> a) & 1;
+      float xi;
+      if (half) {
+        b[a] = d[a] + Box<D>::OG - 1;
+        xi = f[a] - 0.5f;
+      } else {
+        int up = f[a] >= 0.5f ? 1 : 0;
+        b[a] = d[a] + Box<D>::OG + up - 1;
+        xi = f[a] - (float)up;
+      }
+      qweights(xi, w[a]);
+      dw[a][0] = -(0.5f - xi);
+      dw[a][1] = -2.0f * xi;
+      dw[a][2] = 0.5f + xi;
+    } else {
+      b[a] = 0;
+      w[a][0] = 1.0f; w[a][1] = w[a][2] = 0.0f;
+      dw[a][0] = dw[a][1] = dw[a][2] = 0.0f;
+    }
+  }
+  constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
+#pragma unroll
+  for (int k = 0; k < NK; ++k)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int idx = (b[0] + i) + gb0 * ((b[1] + j) + gb1 * (b[2] + k));
+        const float F = G[idx] * e;
+        atomicAdd(Acc + idx, w[0][i] * w[1][j] * w[2][k] * e);
+        Xb[0] += dw[0][i] * w[1][j] * w[2][k] * F;
+        if (D >= 2) Xb[1] += w[0][i] * dw[1][j] * w[2][k] * F;
+        if (D >= 3) Xb[2] += w[0][i] * w[1][j] * dw[2][k] * F;
+      }
+}
+
+template <int D>
+__device__ __forceinline__ void gather_adj_all(const float *G, float *Acc, const int d[3], const float f[3],
+                                               const float Eb[3], const float Bb[3], float Xb[3]) {
+  constexpr int gc = Box<D>::GCELLS;
+  gather_adj_comp<D, 1>(G + 0 * gc, Acc + 0 * gc, d, f, Eb[0], Xb);
+  gather_adj_comp<D, 2>(G + 1 * gc, Acc + 1 * gc, d, f, Eb[1], Xb);
+  gather_adj_comp<D, 4>(G + 2 * gc, Acc + 2 * gc, d, f, Eb[2], Xb);
+  gather_adj_comp<D, 6>(G + 3 * gc, Acc + 3 * gc, d, f, Bb[0], Xb);
+  gather_adj_comp<D, 5>(G + 4 * gc, Acc + 4 * gc, d, f, Bb[1], Xb);
+  gather_adj_comp<D, 3>(G + 5 * gc, Acc + 5 * gc, d, f, Bb[2], Xb);
+}
+
+// Esirkepov transposed for one body: reads the current adjoint lam on the
+// five-node window (like a gather) and returns d(lam . J)/dX0, /dX1 (cells)
+// and /dv
+template <int D>
+__device__ void deposit_adj(const float *__restrict__ Jl, const int d[3], const float f[3], const float de[3],
+                            float qw, const float v[3], const float dxdt[3], float X0b[3], float X1b[3],
+                            float vb[3]) {
+  constexpr int jc = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  float S0[3][5], DS[3][5], gS0[3][5], gDS[3][5], dS0[3][5], dS1[3][5];
+  int n0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      int up = f[a] >= 0.5f ? 1 : 0;
+      float xi = f[a] - (float)up;
+      n0[a] = d[a] + Box<D>::OJ + up;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float u = xi - (float)(m - 2);
+        S0[a][m] = qshape(u);
+        DS[a][m] = qshape(u + de[a]) - S0[a][m];
+        dS0[a][m] = dqshape(u);
+        dS1[a][m] = dqshape(u + de[a]);
+      }
+    } else {
+      n0[a] = 2;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        S0[a][m] = m == 2 ? 1.0f : 0.0f;
+        DS[a][m] = dS0[a][m] = dS1[a][m] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) gS0[a][m] = gDS[a][m] = 0.0f;
+  }
+  const int bx = n0[0] - 2, by = n0[1] - 2, bz = n0[2] - 2;
+  auto L = [&](int comp, int i, int j, int k) -> float {
+    return Jl[comp * jc + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k))];
+  };
+  if constexpr (D == 1) {
+    const float cx = -qw * dxdt[0];
+    float suf = 0.0f;
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      suf += L(0, i, 0, 0);
+      gDS[0][i] += cx * suf;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float ly = L(1, i, 0, 0), lz = L(2, i, 0, 0);
+      float sbar = S0[0][i] + 0.5f * DS[0][i];
+      float t = qw * (v[1] * ly + v[2] * lz);
+      gS0[0][i] += t;
+      gDS[0][i] += 0.5f * t;
+      vb[1] += qw * ly * sbar;
+      vb[2] += qw * lz * sbar;
+    }
+  } else if constexpr (D == 2) {
+    const float cx = -qw * dxdt[0], cy = -qw * dxdt[1];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const float fac = S0[1][j] + 0.5f * DS[1][j];
+      float P = 0.0f, sumLP = 0.0f;
+      float suf = 0.0f;
+#pragma unroll
+      for (int i = 3; i >= 0; --i) {
+        suf += L(0, i, j, 0);
+        gDS[0][i] += cx * suf * fac;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        P += DS[0][i];
+        sumLP += L(0, i, j, 0) * P;
+      }
+      gS0[1][j] += cx * sumLP;
+      gDS[1][j] += 0.5f * cx * sumLP;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float fac = S0[0][i] + 0.5f * DS[0][i];
+      float P = 0.0f, sumLP = 0.0f;
+      float suf = 0.0f;
+#pragma unroll
+      for (int j = 3; j >= 0; --j) {
+        suf += L(1, i, j, 0);
+        gDS[1][j] += cy * suf * fac;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        P += DS[1][j];
+        sumLP += L(1, i, j, 0) * P;
+      }
+      gS0[0][i] += cy * sumLP;
+      gDS[0][i] += 0.5f * cy * sumLP;
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const float l = L(2, i, j, 0);
+        const float wz = S0[0][i] * S0[1][j] + 0.5f * (DS[0][i] * S0[1][j] + S0[0][i] * DS[1][j]) +
+                         (1.0f / 3.0f) * DS[0][i] * DS[1][j];
+        const float c = qw * v[2] * l;
+        vb[2] += qw * l * wz;
+        gS0[0][i] += c * (S0[1][j] + 0.5f * DS[1][j]);
+        gDS[0][i] += c * (0.5f * S0[1][j] + (1.0f / 3.0f) * DS[1][j]);
+        gS0[1][j] += c * (S0[0][i] + 0.5f * DS[0][i]);
+        gDS[1][j] += c * (0.5f * S0[0][i] + (1.0f / 3.0f) * DS[0][i]);
+      }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      const float ca = -qw * dxdt[a];
+#pragma unroll 1
+      for (int kb = 0; kb < 5; ++kb)
+#pragma unroll 1
+        for (int kc = 0; kc < 5; ++kc) {
+          const float fac = S0[b][kb] * S0[c][kc] + 0.5f * (DS[b][kb] * S0[c][kc] + S0[b][kb] * DS[c][kc]) +
+                            (1.0f / 3.0f) * DS[b][kb] * DS[c][kc];
+          float lv[4];
+#pragma unroll
+          for (int ka = 0; ka < 4; ++ka) {
+            int idx[3];
+            idx[a] = ka;
+            idx[b] = kb;
+            idx[c] = kc;
+            lv[ka] = L(a, idx[0], idx[1], idx[2]);
+          }
+          float suf = 0.0f, P = 0.0f, sumLP = 0.0f;
+#pragma unroll
+          for (int ka = 3; ka >= 0; --ka) {
+            suf += lv[ka];
+            gDS[a][ka] += ca * suf * fac;
+          }
+#pragma unroll
+          for (int ka = 0; ka < 4; ++ka) {
+            P += DS[a][ka];
+            sumLP += lv[ka] * P;
+          }
+          gS0[b][kb] += ca * sumLP * (S0[c][kc] + 0.5f * DS[c][kc]);
+          gDS[b][kb] += ca * sumLP * (0.5f * S0[c][kc] + (1.0f / 3.0f) * DS[c][kc]);
+          gS0[c][kc] += ca * sumLP * (S0[b][kb] + 0.5f * DS[b][kb]);
+          gDS[c][kc] += ca * sumLP * (0.5f * S0[b][kb] + (1.0f / 3.0f) * DS[b][kb]);
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float x0 = 0.0f, x1 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      x0 += (gS0[a][m] - gDS[a][m]) * dS0[a][m];
+      x1 += gDS[a][m] * dS1[a][m];
+    }
+    X0b[a] += x0;
+    X1b[a] += x1;
+  }
+}
+
+struct AdjState {
+  float *xb;      // [12][cap] by load id: x1b(3) x2b(3) u1b(3) u2b(3)
+  double *acb;    // [cap] adjoint of a_c, accumulated over steps
+  long long cap;
+};
+
+struct AdjArgs {
+  int nsp;
+  SpecP sp[BP_MAX_SPECIES];
+  PartP p[BP_MAX_SPECIES];       // particle state of step n
+  AdjState st[BP_MAX_SPECIES];
+  const float *E[3], *B[3];      // E^n, B^n
+  const float *lamJ[3];
+  float *box;                    // [ntiles][6][gcells]
+  unsigned char *occ;
+};
+
+template <int D>
+__device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, AdjState &S, long long i,
+                             const int T0[3], const float *Gsm, const float *Jl, float *Acc) {
+  const long long cap = P.cap;
+  const bool two = sp.kind == BP_TWO_BODY;
+  const int cell = P.cell[i];
+  if (cell < 0) return;
+  const int id = P.id[i];
+  int c[3];
+  unpack_cell(g, cell, c);
+  float f[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f}, u1[3], u2[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int a = 0; a < D; ++a) f[a] = P.off[a * cap + i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u1[a] = P.u1[a * cap + i];
+  if (two) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = P.r[a * cap + i];
+      u2[a] = P.u2[a * cap + i];
+    }
+  }
+  int d[3] = {0, 0, 0}, d2[3] = {0, 0, 0};
+  float f2[3] = {0.0f, 0.0f, 0.0f};
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    d[a] = rel_cell<D>(g, a, c[a], T0[a]);
+    bad |= outside_margin<D>(a, d[a]) || !(fabsf(r[a] * g.idx[a]) < 1.0f);
+    float X = f[a] - r[a] * g.idx[a];
+    float fl = floorf(X);
+    float fr = X - fl;
+    int di = (int)fl;
+    if (fr >= 1.0f) { fr = 0.0f; di += 1; }
+    d2[a] = d[a] + di;
+    f2[a] = fr;
+  }
+  if (bad) return;  // the forward push skipped it too (domain error)
+  // forward recompute
+  float E1[3], B1[3], E2[3], B2[3];
+  {
+    Loc L1, L2;
+    make_loc<D>(d, f, L1);
+    make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
+    gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
+  }
+  float ac = 0.0f, rr = 1.0f, s3 = 0.0f;
+  if (two) {
+    const int pi = P.pidx ? P.pidx[i] : 0;
+    ac = sp.ac[pi];
+    rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + ac * ac;
+    float rs = rsqrtf(rr);
+    s3 = sp.kappa * rs * rs * rs;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      E1[a] = fmaf(sp.q2 * s3, r[a], E1[a]);
+      E2[a] = fmaf(-sp.q1 * s3, r[a], E2[a]);
+    }
+  }
+  float un1[3] = {u1[0], u1[1], u1[2]}, un2[3] = {u2[0], u2[1], u2[2]};
+  boris(sp.h1, E1, B1, un1);
+  if (two) boris(sp.h2, E2, B2, un2);
+  float gi1 = rsqrtf(1.0f + un1[0] * un1[0] + un1[1] * un1[1] + un1[2] * un1[2]);
+  float gi2 = rsqrtf(1.0f + un2[0] * un2[0] + un2[1] * un2[1] + un2[2] * un2[2]);
+  float v1[3], v2[3], de1[3] = {0.0f, 0.0f, 0.0f}, de2[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v1[a] = un1[a] * gi1;
+    v2[a] = un2[a] * gi2;
+    if (a < D) {
+      de1[a] = g.dt * v1[a] * g.idx[a];
+      de2[a] = g.dt * v2[a] * g.idx[a];
+    }
+  }
+  const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
+  // deposit transposed
+  float X10b[3] = {0, 0, 0}, X11b[3] = {0, 0, 0}, X20b[3] = {0, 0, 0}, X21b[3] = {0, 0, 0};
+  float v1b[3] = {0, 0, 0}, v2b[3] = {0, 0, 0};
+  deposit_adj<D>(Jl, d, f, de1, sp.qw1, v1, dxdt, X10b, X11b, v1b);
+  if (two) deposit_adj<D>(Jl, d2, f2, de2, sp.qw2, v2, dxdt, X20b, X21b, v2b);
+  // carried adjoints of x^{n+1}, u^{n+1/2}
+  const long long sc = S.cap;
+  float xb1[3], xb2[3], ub1[3], ub2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xb1[a] = S.xb[(0 + a) * sc + id];
+    xb2[a] = S.xb[(3 + a) * sc + id];
+    ub1[a] = S.xb[(6 + a) * sc + id];
+    ub2[a] = S.xb[(9 + a) * sc + id];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    xb1[a] += X11b[a] * g.idx[a];
+    xb2[a] += X21b[a] * g.idx[a];
+  }
+  // drift x^{n+1} = x^n + dt v: v adjoint; v = u / gamma
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v1b[a] += g.dt * xb1[a];
+    v2b[a] += g.dt * xb2[a];
+  }
+  float uv1 = un1[0] * v1b[0] + un1[1] * v1b[1] + un1[2] * v1b[2];
+  float uv2 = un2[0] * v2b[0] + un2[1] * v2b[1] + un2[2] * v2b[2];
+  float g31 = gi1 * gi1 * gi1, g32 = gi2 * gi2 * gi2;
+  float unb1[3], unb2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    unb1[a] = ub1[a] + v1b[a] * gi1 - un1[a] * uv1 * g31;
+    unb2[a] = ub2[a] + v2b[a] * gi2 - un2[a] * uv2 * g32;
+  }
+  // Boris transposed
+  float Eb1[3], Bb1[3], Eb2[3] = {0, 0, 0}, Bb2[3] = {0, 0, 0};
+  boris_adj(sp.h1, E1, B1, u1, unb1, ub1, Eb1, Bb1);
+  if (two) boris_adj(sp.h2, E2, B2, u2, unb2, ub2, Eb2, Bb2);
+  // internal field transposed: w = q2 Eb1 - q1 Eb2 against kappa r rho^{-3/2}
+  if (two) {
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w[a] = sp.q2 * Eb1[a] - sp.q1 * Eb2[a];
+    float wr = w[0] * r[0] + w[1] * r[1] + w[2] * r[2];
+    float p52 = s3 / (sp.kappa * rr);  // rho^{-5/2}
+    float p32 = s3 / sp.kappa;         // rho^{-3/2}
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float rb = sp.kappa * (w[a] * p32 - 3.0f * wr * r[a] * p52);
+      xb1[a] += rb;
+      xb2[a] -= rb;
+    }
+    S.acb[id] += (double)(-3.0f * sp.kappa * wr * ac * p52);
+  }
+  // gather transposed; old positions through the deposit
+  float Xg1[3] = {0, 0, 0}, Xg2[3] = {0, 0, 0};
+  gather_adj_all<D>(Gsm, Acc, d, f, Eb1, Bb1, Xg1);
+  if (two) gather_adj_all<D>(Gsm, Acc, d2, f2, Eb2, Bb2, Xg2);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    xb1[a] += (Xg1[a] + X10b[a]) * g.idx[a];
+    xb2[a] += (Xg2[a] + X20b[a]) * g.idx[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S.xb[(0 + a) * sc + id] = xb1[a];
+    S.xb[(3 + a) * sc + id] = two ? xb2[a] : 0.0f;
+    S.xb[(6 + a) * sc + id] = ub1[a];
+    S.xb[(9 + a) * sc + id] = two ? ub2[a] : 0.0f;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_push(GridP g, AdjArgs A) {
+  using BX = Box<D>;
+  constexpr int GC = BX::GCELLS, JC = BX::JCELLS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *Gsm = reinterpret_cast<float *>(smem);  // E^n, B^n
+  float *Acc = Gsm + 6 * GC;                     // adjoints of E^n, B^n
+  float *Jl = Acc + 6 * GC;                      // adjoint of J
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  int total = 0;
+  for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
+  if (total == 0) {
+    if (tid == 0) A.occ[t] = 0;
+    return;
+  }
+  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  for (int q = tid; q < GC; q += bs) {
+    int bidx[3] = {q % BX::G0, (q / BX::G0) % BX::G1, q / (BX::G0 * BX::G1)};
+    long long gi = 0, stride = 1;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int x = T0[a] - (a < D ? BX::OG : 0) + bidx[a];
+      if (a < D) {
+        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        else ok &= (x >= 0 && x < g.n[a]);
+      }
+      gi += (long long)x * stride;
+      stride *= g.n[a];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      Gsm[cc * GC + q] = ok ? A.E[cc][gi] : 0.0f;
+      Gsm[(3 + cc) * GC + q] = ok ? A.B[cc][gi] : 0.0f;
+    }
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) Acc[cc * GC + q] = 0.0f;
+  }
+  for (int q = tid; q < JC; q += bs) {
+    int bidx[3] = {q % BX::J0, (q / BX::J0) % BX::J1, q / (BX::J0 * BX::J1)};
+    long long gi = 0, stride = 1;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int x = T0[a] - (a < D ? BX::OJ : 0) + bidx[a];
+      if (a < D) {
+        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        else ok &= (x >= 0 && x < g.n[a]);
+      }
+      gi += (long long)x * stride;
+      stride *= g.n[a];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + q] = ok ? A.lamJ[cc][gi] : 0.0f;
+  }
+  __syncthreads();
+  for (int s = 0; s < A.nsp; ++s) {
+    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    for (long long i = beg + tid; i < end; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, Acc);
+  }
+  __syncthreads();
+  float *out = A.box + (size_t)t * 6 * GC;
+  for (int q = tid; q < 6 * GC; q += bs) out[q] = Acc[q];
+  if (tid == 0) A.occ[t] = 1;
+}
+
+// adds the per-tile gather-adjoint boxes to the field adjoints, in a fixed
+// order of the covering tiles
+__global__ void k_adj_boxsum(GridP g, const float *box, const unsigned char *occ, float *E0, float *E1, float *E2,
+                             float *B0, float *B1, float *B2) {
+  float *out[6] = {E0, E1, E2, B0, B1, B2};
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords(g, q, c);
+    int tw[3][3], loc[3][3], nc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      nc[a] = 0;
+      if (a >= g.D) {
+        tw[a][0] = 0;
+        loc[a][0] = 0;
+        nc[a] = 1;
+        continue;
+      }
+      int tb = c[a] / g.L[a];
+      for (int dt = -1; dt <= 1; ++dt) {
+        int tu = tb + dt;
+        int l = c[a] - (tu * g.L[a] - g.og[a]);
+        if (l < 0 || l >= g.gb[a]) continue;
+        int tt = tu;
+        if (g.bc[a] == BP_PERIODIC) tt = wrap_mod(tu, g.nt[a]);
+        else if (tu < 0 || tu >= g.nt[a]) continue;
+        tw[a][nc[a]] = tt;
+        loc[a][nc[a]] = l;
+        ++nc[a];
+      }
+    }
+    float acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < nc[2]; ++k)
+      for (int j = 0; j < nc[1]; ++j)
+        for (int i = 0; i < nc[0]; ++i) {
+          int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
+          if (!occ[tile]) continue;
+          long long l = loc[0][i] + (long long)g.gb[0] * (loc[1][j] + (long long)g.gb[1] * loc[2][k]);
+          const float *b = box + (size_t)tile * 6 * g.gcells;
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) acc[cc] += b[(size_t)cc * g.gcells + l];
+        }
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) out[cc][q] += acc[cc];
+  }
+}
+
+// deterministic FP64 row sums: out[r * ncomp + k] = scale[r] * sum over the
+// ids of row r (CSR, fixed order) of val(id, k)
+__global__ void k_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
+                          const double *acb, const double *scale, double *out) {
+  __shared__ double sh[256];
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    for (int k = 0; k < ncomp; ++k) {
+      double s = 0.0;
+      for (int j = ptr[r] + threadIdx.x; j < ptr[r + 1]; j += blockDim.x) {
+        const int id = ids[j];
+        // positions: adjoint of the ion position = x1b + x2b (both bodies start there)
+        s += acb ? acb[id] : (double)xb[(size_t)k * cap + id] + (double)xb[(size_t)(3 + k) * cap + id];
+      }
+      sh[threadIdx.x] = s;
+      __syncthreads();
+      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) out[(size_t)r * ncomp + k] = sh[0] * (scale ? scale[r] : 1.0);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+void launch_adj_inject(float *lam, const long long *nodes, long long npts, const float *dl, cudaStream_t s) {
+  k_adj_inject<<<blocks_for(npts, 256), 256, 0, s>>>(lam, nodes, npts, dl);
+}
+
+void launch_adj_e(const GridP &g, float *G[3], float *H[3], float *lamB[3], float *lamJ[3], cudaStream_t s) {
+  int nopen = 0;
+  for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
+  for (int p = nopen; p >= 1; --p)
+    for (int a = 0; a < g.D; ++a)
+      if (g.bc[a] == BP_OPEN)
+        k_adj_mur<<<blocks_for(4 * (g.ncell / g.n[a]), 256), 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], a, p);
+  k_adj_e<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2],
+                                                    lamJ[0], lamJ[1], lamJ[2]);
+}
+
+void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, cudaStream_t s) {
+  k_adj_b<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h);
+}
+
+size_t adj_push_smem(int D) {
+  if (D == 1) return sizeof(float) * (12 * Box<1>::GCELLS + 3 * Box<1>::JCELLS);
+  if (D == 2) return sizeof(float) * (12 * Box<2>::GCELLS + 3 * Box<2>::JCELLS);
+  return sizeof(float) * (12 * Box<3>::GCELLS + 3 * Box<3>::JCELLS);
+}
+
+int adj_prepare(int D) {
+  cudaError_t e = cudaSuccess;
+  if (D == 1) e = cudaFuncSetAttribute(k_adj_push<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(1));
+  if (D == 2) e = cudaFuncSetAttribute(k_adj_push<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(2));
+  if (D == 3) e = cudaFuncSetAttribute(k_adj_push<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(3));
+  return e == cudaSuccess ? 0 : -1;
+}
+
+// the particle adjoint of one step, then the sum of its boxes
+void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
+                     const long long *cap, const float *const E[3], const float *const B[3],
+                     const float *const lamJ[3], float *box, unsigned char *occ, float *lamE[3], float *lamB[3],
+                     cudaStream_t s) {
+  AdjArgs A;
+  memset(&A, 0, sizeof A);
+  A.nsp = nsp;
+  for (int k = 0; k < nsp; ++k) {
+    A.sp[k] = sp[k];
+    A.p[k] = p[k];
+    A.st[k].xb = xb[k];
+    A.st[k].acb = acb[k];
+    A.st[k].cap = cap[k];
+  }
+  for (int c = 0; c < 3; ++c) {
+    A.E[c] = E[c];
+    A.B[c] = B[c];
+    A.lamJ[c] = lamJ[c];
+  }
+  A.box = box;
+  A.occ = occ;
+  size_t smem = adj_push_smem(g.D);
+  if (g.D == 1) k_adj_push<1><<<g.ntiles, 256, smem, s>>>(g, A);
+  if (g.D == 2) k_adj_push<2><<<g.ntiles, 256, smem, s>>>(g, A);
+  if (g.D == 3) k_adj_push<3><<<g.ntiles, 256, smem, s>>>(g, A);
+  k_adj_boxsum<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, box, occ, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1],
+                                                         lamB[2]);
+}
+
+void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
+                    const double *acb, const double *scale, double *out, cudaStream_t s) {
+  int nb = nrows < 4096 ? (nrows < 1 ? 1 : nrows) : 4096;
+  k_csr_sum<<<nb, 256, 0, s>>>(ptr, ids, nrows, xb, cap, ncomp, acb, scale, out);
+}

@@ -1,0 +1,104 @@
+"""GPU discrete adjoint against the oracle's FP64 adjoint (itself pinned by
+finite differences in test_oracle_adjoint.py), on the same small problems:
+gradients of a probe loss with respect to per-group omega_b and rigid
+group ('site') positions.  Both adjoints get the same loss gradient dL/dp
+(from the oracle's probe), so the comparison measures the reverse pass, not
+the FP32 forward's effect on a small residual p - target.  Tolerance 1e-4
+relative to the largest component (FP32 forward and adjoint, FP64
+reductions).  The gather transpose scatters with FP32 shared atomics, so
+reruns agree to rounding, not bit for bit."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2208_08038_gb300 import synth
+from _common import gpu_from_workload
+from test_oracle_adjoint import build_oracle, fd_problem, run_loss
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+
+
+def oracle_gradients(D):
+    wl, steps, groups = fd_problem(D)
+    sp = wl.species[0]
+    npts = len(wl.probe_nodes)
+    om_true = synth.uniform_params(33, groups, 2.5, 3.5)
+    _, target = run_loss(wl, steps, om_true, np.zeros((steps, npts)))
+    s, sid, pid = build_oracle(wl, sp.omega_b)
+    a = O.Adjoint(s, sid)
+    L0, probe = a.forward(steps, pid, target)
+    g_om, g_x = a.backward(groups, len(sp.x))
+    a.close()
+    s.close()
+    g_site = np.stack([g_x[sp.pidx == k, :D].sum(axis=0) for k in range(groups)])
+    return wl, steps, groups, target, probe, g_om, g_site
+
+
+def gpu_problem(wl, steps, K):
+    from paper_2208_08038_gb300.adjoint import SiteProblem
+    sp = wl.species[0]
+    ctx, sids, pid = gpu_from_workload(wl, deposit_mode=1, probe_cap=steps)
+    prob = SiteProblem(ctx, sids[0], pid, sp.pidx, sp.x, sp.pidx, steps, K)
+    return prob
+
+
+@pytest.fixture(scope="module", params=[1, 2])
+def case(request):
+    return oracle_gradients(request.param)
+
+
+def test_gpu_adjoint_matches_oracle(case):
+    wl, steps, groups, target, probe_o, g_om, g_site = case
+    D = wl.D
+    prob = gpu_problem(wl, steps, K=20)
+    sites0 = np.zeros((groups, D))
+    probe = prob.run(wl.species[0].omega_b, sites0)
+    assert np.abs(probe - probe_o).max() <= 1e-5 * np.abs(probe_o).max()
+    go, gs = prob.gradients(2.0 * (probe_o - target), groups)
+    assert np.abs(go - g_om).max() <= 1e-4 * np.abs(g_om).max(), (go, g_om)
+    assert np.abs(gs - g_site).max() <= 1e-4 * np.abs(g_site).max(), (gs, g_site)
+
+
+def test_checkpoint_interval_does_not_change_gradients(case):
+    wl, steps, groups, target, probe_o, *_ = case
+    out = []
+    for K in (1, 7, steps):
+        prob = gpu_problem(wl, steps, K=K)
+        prob.run(wl.species[0].omega_b, np.zeros((groups, wl.D)))
+        out.append(prob.gradients(2.0 * (probe_o - target), groups))
+        prob.ctx.close()
+    for go, gs in out[1:]:
+        assert np.abs(go - out[0][0]).max() <= 1e-4 * np.abs(out[0][0]).max()
+        assert np.abs(gs - out[0][1]).max() <= 1e-4 * np.abs(out[0][1]).max()
+
+
+def test_autograd_function(case):
+    """loss = sum probe^2 through torch.autograd (the residual is the probe
+    itself, large against FP32 forward errors) against the oracle's adjoint
+    of the same loss."""
+    import torch
+    from paper_2208_08038_gb300.adjoint import PICProbe
+    wl, steps, groups, *_ = case
+    sp = wl.species[0]
+    npts = len(wl.probe_nodes)
+    s, sid, pid = build_oracle(wl, sp.omega_b)
+    a = O.Adjoint(s, sid)
+    a.forward(steps, pid, np.zeros((steps, npts)))
+    g_om, g_x = a.backward(groups, len(sp.x))
+    a.close()
+    s.close()
+    g_site = np.stack([g_x[sp.pidx == k, :wl.D].sum(axis=0) for k in range(groups)])
+    prob = gpu_problem(wl, steps, K=16)
+    om = torch.tensor(sp.omega_b, dtype=torch.float64, requires_grad=True)
+    sites = torch.zeros((groups, wl.D), dtype=torch.float64, requires_grad=True)
+    probe = PICProbe.apply(om, sites, prob)
+    loss = (probe ** 2).sum()
+    loss.backward()
+    assert np.abs(om.grad.numpy() - g_om).max() <= 1e-4 * np.abs(g_om).max()
+    assert np.abs(sites.grad.numpy() - g_site).max() <= 1e-4 * np.abs(g_site).max()
