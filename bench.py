@@ -162,17 +162,95 @@ def run_e2e(wl, n_ion, mode, steps, rank, world):
                     "E_y read back every step; context creation included"}
 
 
+def run_adjoint_ratio(steps=400, K=20):
+    """Adjoint cost on the 2D adjoint workload (1024^2 cells, dx = lambda/32,
+    524,288 ions in the bound slab on 4096 sites, per-column omega_b, 400
+    steps, checkpoints every 20): (checkpointed forward + backward) / plain
+    forward, each timed with CUDA events on the context stream."""
+    import numpy as np
+    import torch
+    from paper_2208_08038_gb300 import binding as B
+    from paper_2208_08038_gb300 import synth
+    from paper_2208_08038_gb300.adjoint import SiteProblem
+    wl = synth.cfg3_adjoint_2d(steps=steps)
+    sp = wl.species[0]
+    m = wl.meta
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=B.BP_DEPOSIT_SORTED)
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    for L in wl.lasers:
+        ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    pid = ctx.add_probe(wl.probe_comp, wl.probe_nodes, steps)
+    prob = SiteProblem(ctx, sid, pid, m["site_of_ion"], m["off"], m["column"], steps, K)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sites = m["sites"]
+    x0 = sites[m["site_of_ion"]] + m["off"]
+
+    def plain():
+        ctx.reset()
+        ctx.load_particles(sid, x0, None, m["column"])
+        ctx.step(steps)
+        ctx.sync()
+
+    plain()  # warm-up
+    t_plain = timed(plain)
+    probe = prob.run(sp.omega_b, sites)  # warm-up of the checkpointed path
+    dl = (2.0 * probe).astype(np.float32)
+    prob.gradients(dl, len(sp.omega_b))
+    t_fwd = timed(lambda: prob.run(sp.omega_b, sites))
+    t_bwd = timed(lambda: prob.gradients(dl, len(sp.omega_b)))
+    ctx.close()
+    return {"workload": "cfg3_adjoint_2d: 1024x1024 cells, dx=lambda/32, 524288 ions on 4096 sites, "
+                        "1024 per-column omega_b, 400 steps, checkpoint every 20",
+            "plain_forward_ms": t_plain, "ckpt_forward_ms": t_fwd, "backward_ms": t_bwd,
+            "ratio": (t_fwd + t_bwd) / t_plain}
+
+
+def our_config(n_ion, mode, world):
+    return {"workload": "cfg2_neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
+                        f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, {mode} deposit",
+            "l2": "inputs larger than L2 (particles 13.7 GB)", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: W untimed and K timed
+    steps of a bounded sample of the 3D workload (a 16^3-cell periodic box
+    with the workload's dx, dt, 8 ions per cell, thermal momenta, omega_b),
+    on rank 0 only."""
     if rank != 0:
         return
-    base = cpu_baseline_cfg2(seconds_target=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
-    # bounded sample per step, the whole run within minutes
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cfg2_neutral_3d sample", "sample": base["sample"]},
-            "cpu_baseline": {k: base[k] for k in ("kind", "cores", "sample", "value", "unit")},
-            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    import oracle as O
+    from paper_2208_08038_gb300 import synth
+    n = (16, 16, 16)
+    wl = synth.cfg2_neutral_3d(n=n, margin=0)
+    wl.bc = (0, 0, 0)
+    sp = wl.species[0]
+    s = O.Sim(3, n, wl.dx, wl.dt, wl.bc)
+    sid = s.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    s.load(sid, sp.x, sp.u)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    el = time.perf_counter() - t0
+    s.close()
+    value = len(sp.x) * args.steps / el
+    wl_full, n_ion = workload_cfg2()
+    sample = f"16^3-cell periodic box of the 3D workload ({len(sp.x)} ions, 8/cell), FP64, {args.steps} timed steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(our_config(n_ion, "oracle", world), sample=sample),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -185,6 +263,9 @@ def main():
     ap.add_argument("--mode", default="sorted", choices=["sorted", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
+                    help="only the adjoint/forward ratio of the 2D adjoint workload over STEPS steps")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the 3D workload on 128x64x64 cells (profiling)")
     args = ap.parse_args()
@@ -195,6 +276,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.adjoint_only:
+        import torch
+        torch.cuda.set_device(local)
+        if rank == 0:
+            print(json.dumps({"adjoint": run_adjoint_ratio(steps=args.adjoint_only)}), flush=True)
         return
 
     import torch
@@ -270,10 +357,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "cfg2_neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
-                               f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, "
-                               f"{args.mode} deposit", "l2": "inputs larger than L2 (particles 13.7 GB)",
-                   "parallelism": f"replicas x{world}"},
+        "config": our_config(n_ion, args.mode, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "k_push<3,sorted>",
                      "peak_source": src, "push_ms_per_launch": push_avg},
@@ -283,6 +367,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_cfg2()
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = run_adjoint_ratio()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -71,7 +71,7 @@ typedef struct {
  * E_y at (i, j+1/2, k), E_z at (i, j, k+1/2), B_x at (i, j+1/2, k+1/2), B_y at
  * (i+1/2, j, k+1/2), B_z at (i+1/2, j+1/2, k); J with E.  Open axes use Mur
  * first-order absorbing faces on the tangential E; periodic axes wrap.
- * Tiles are 64 cells (1D), 32 x 32 (2D), 8 x 8 x 8 (3D); n[a] must be a
+ * Tiles are 16 cells (1D), 16 x 16 (2D), 8 x 8 x 8 (3D); n[a] must be a
  * multiple of the tile and the bit widths of n[0..2] may sum to at most 31. */
 typedef struct {
   int dims;           /* 1, 2 or 3 */

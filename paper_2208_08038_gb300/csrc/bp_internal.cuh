@@ -41,11 +41,11 @@ template <int D>
 struct Geo;
 template <>
 struct Geo<1> {
-  static constexpr int L0 = 64, L1 = 1, L2 = 1, M = 8;
+  static constexpr int L0 = 16, L1 = 1, L2 = 1, M = 8;
 };
 template <>
 struct Geo<2> {
-  static constexpr int L0 = 32, L1 = 32, L2 = 1, M = 2;
+  static constexpr int L0 = 16, L1 = 16, L2 = 1, M = 2;
 };
 template <>
 struct Geo<3> {

@@ -242,37 +242,40 @@ __device__ void boris_adj(float h, const float E[3], const float B[3], const flo
   }
 }
 
-// gather transposed for one component of stagger PAT at one body: scatter
-// e * weights into the accumulator box, add e * d(interpolated field)/dX
-template <int D, int PAT>
-__device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, float *Acc, const int d[3],
-                                                const float f[3], float e, float Xb[3]) {
+// gather transposed for one component of stagger PAT at NB bodies whose
+// stencils start at the same node (NB = 2: one atomic per node for both):
+// scatter e * weights into the accumulator box, add e * d(field)/dX
+template <int D, int PAT, int NB>
+__device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, float *Acc, const int (*d)[3],
+                                                const float (*f)[3], const float *e, float (*Xb)[3]) {
   constexpr int gb0 = Box<D>::G0, gb1 = Box<D>::G1;
   int b[3];
-  float w[3][3], dw[3][3];
+  float w[NB][3][3], dw[NB][3][3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a < D) {
-      const bool half = (PAT >> a) & 1;
-      float xi;
-      if (half) {
-        b[a] = d[a] + Box<D>::OG - 1;
-        xi = f[a] - 0.5f;
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < D) {
+        const bool half = (PAT >> a) & 1;
+        float xi;
+        if (half) {
+          b[a] = d[q][a] + Box<D>::OG - 1;
+          xi = f[q][a] - 0.5f;
+        } else {
+          int up = f[q][a] >= 0.5f ? 1 : 0;
+          b[a] = d[q][a] + Box<D>::OG + up - 1;
+          xi = f[q][a] - (float)up;
+        }
+        qweights(xi, w[q][a]);
+        dw[q][a][0] = -(0.5f - xi);
+        dw[q][a][1] = -2.0f * xi;
+        dw[q][a][2] = 0.5f + xi;
       } else {
-        int up = f[a] >= 0.5f ? 1 : 0;
-        b[a] = d[a] + Box<D>::OG + up - 1;
-        xi = f[a] - (float)up;
+        b[a] = 0;
+        w[q][a][0] = 1.0f; w[q][a][1] = w[q][a][2] = 0.0f;
+        dw[q][a][0] = dw[q][a][1] = dw[q][a][2] = 0.0f;
       }
-      qweights(xi, w[a]);
-      dw[a][0] = -(0.5f - xi);
-      dw[a][1] = -2.0f * xi;
-      dw[a][2] = 0.5f + xi;
-    } else {
-      b[a] = 0;
-      w[a][0] = 1.0f; w[a][1] = w[a][2] = 0.0f;
-      dw[a][0] = dw[a][1] = dw[a][2] = 0.0f;
     }
-  }
   constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
 #pragma unroll
   for (int k = 0; k < NK; ++k)
@@ -281,184 +284,245 @@ __device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, flo
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const int idx = (b[0] + i) + gb0 * ((b[1] + j) + gb1 * (b[2] + k));
-        const float F = G[idx] * e;
-        atomicAdd(Acc + idx, w[0][i] * w[1][j] * w[2][k] * e);
-        Xb[0] += dw[0][i] * w[1][j] * w[2][k] * F;
-        if (D >= 2) Xb[1] += w[0][i] * dw[1][j] * w[2][k] * F;
-        if (D >= 3) Xb[2] += w[0][i] * w[1][j] * dw[2][k] * F;
+        const float g = G[idx];
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const float F = g * e[q];
+          acc += w[q][0][i] * w[q][1][j] * w[q][2][k] * e[q];
+          Xb[q][0] += dw[q][0][i] * w[q][1][j] * w[q][2][k] * F;
+          if (D >= 2) Xb[q][1] += w[q][0][i] * dw[q][1][j] * w[q][2][k] * F;
+          if (D >= 3) Xb[q][2] += w[q][0][i] * w[q][1][j] * dw[q][2][k] * F;
+        }
+        atomicAdd(Acc + idx, acc);
       }
 }
 
-template <int D>
-__device__ __forceinline__ void gather_adj_all(const float *G, float *Acc, const int d[3], const float f[3],
-                                               const float Eb[3], const float Bb[3], float Xb[3]) {
-  constexpr int gc = Box<D>::GCELLS;
-  gather_adj_comp<D, 1>(G + 0 * gc, Acc + 0 * gc, d, f, Eb[0], Xb);
-  gather_adj_comp<D, 2>(G + 1 * gc, Acc + 1 * gc, d, f, Eb[1], Xb);
-  gather_adj_comp<D, 4>(G + 2 * gc, Acc + 2 * gc, d, f, Eb[2], Xb);
-  gather_adj_comp<D, 6>(G + 3 * gc, Acc + 3 * gc, d, f, Bb[0], Xb);
-  gather_adj_comp<D, 5>(G + 4 * gc, Acc + 4 * gc, d, f, Bb[1], Xb);
-  gather_adj_comp<D, 3>(G + 5 * gc, Acc + 5 * gc, d, f, Bb[2], Xb);
-}
-
-// Esirkepov transposed for one body: reads the current adjoint lam on the
-// five-node window (like a gather) and returns d(lam . J)/dX0, /dX1 (cells)
-// and /dv
-template <int D>
-__device__ void deposit_adj(const float *__restrict__ Jl, const int d[3], const float f[3], const float de[3],
-                            float qw, const float v[3], const float dxdt[3], float X0b[3], float X1b[3],
-                            float vb[3]) {
-  constexpr int jc = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
-  float S0[3][5], DS[3][5], gS0[3][5], gDS[3][5], dS0[3][5], dS1[3][5];
-  int n0[3];
+// stencil base of one component's gather at a body (to test for sharing)
+template <int D, int PAT>
+__device__ __forceinline__ bool same_base(const int d1[3], const float f1[3], const int d2[3], const float f2[3]) {
+  bool s = true;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a < D) {
-      int up = f[a] >= 0.5f ? 1 : 0;
-      float xi = f[a] - (float)up;
-      n0[a] = d[a] + Box<D>::OJ + up;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        float u = xi - (float)(m - 2);
-        S0[a][m] = qshape(u);
-        DS[a][m] = qshape(u + de[a]) - S0[a][m];
-        dS0[a][m] = dqshape(u);
-        dS1[a][m] = dqshape(u + de[a]);
-      }
-    } else {
-      n0[a] = 2;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        S0[a][m] = m == 2 ? 1.0f : 0.0f;
-        DS[a][m] = dS0[a][m] = dS1[a][m] = 0.0f;
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m) gS0[a][m] = gDS[a][m] = 0.0f;
+  for (int a = 0; a < D; ++a) {
+    if ((PAT >> a) & 1) s &= d1[a] == d2[a];
+    else s &= (d1[a] + (f1[a] >= 0.5f ? 1 : 0)) == (d2[a] + (f2[a] >= 0.5f ? 1 : 0));
   }
-  const int bx = n0[0] - 2, by = n0[1] - 2, bz = n0[2] - 2;
+  return s;
+}
+
+template <int D, int PAT>
+__device__ __forceinline__ void gather_adj_pair(const float *G, float *Acc, const int d1[3], const float f1[3],
+                                                float e1, float X1[3], const int d2[3], const float f2[3], float e2,
+                                                float X2[3], bool two) {
+  if (two && same_base<D, PAT>(d1, f1, d2, f2)) {
+    int dd[2][3] = {{d1[0], d1[1], d1[2]}, {d2[0], d2[1], d2[2]}};
+    float ff[2][3] = {{f1[0], f1[1], f1[2]}, {f2[0], f2[1], f2[2]}};
+    float ee[2] = {e1, e2};
+    float XX[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    gather_adj_comp<D, PAT, 2>(G, Acc, dd, ff, ee, XX);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { X1[a] += XX[0][a]; X2[a] += XX[1][a]; }
+  } else {
+    int dd[1][3] = {{d1[0], d1[1], d1[2]}};
+    float ff[1][3] = {{f1[0], f1[1], f1[2]}};
+    float XX[1][3] = {{0, 0, 0}};
+    gather_adj_comp<D, PAT, 1>(G, Acc, dd, ff, &e1, XX);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) X1[a] += XX[0][a];
+    if (two) {
+      int de[1][3] = {{d2[0], d2[1], d2[2]}};
+      float fe[1][3] = {{f2[0], f2[1], f2[2]}};
+      float XY[1][3] = {{0, 0, 0}};
+      gather_adj_comp<D, PAT, 1>(G, Acc, de, fe, &e2, XY);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) X2[a] += XY[0][a];
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void gather_adj_all(const float *G, float *Acc, const int d1[3], const float f1[3],
+                                               const float Eb1[3], const float Bb1[3], float X1[3], const int d2[3],
+                                               const float f2[3], const float Eb2[3], const float Bb2[3], float X2[3],
+                                               bool two) {
+  constexpr int gc = Box<D>::GCELLS;
+  gather_adj_pair<D, 1>(G + 0 * gc, Acc + 0 * gc, d1, f1, Eb1[0], X1, d2, f2, Eb2[0], X2, two);
+  gather_adj_pair<D, 2>(G + 1 * gc, Acc + 1 * gc, d1, f1, Eb1[1], X1, d2, f2, Eb2[1], X2, two);
+  gather_adj_pair<D, 4>(G + 2 * gc, Acc + 2 * gc, d1, f1, Eb1[2], X1, d2, f2, Eb2[2], X2, two);
+  gather_adj_pair<D, 6>(G + 3 * gc, Acc + 3 * gc, d1, f1, Bb1[0], X1, d2, f2, Bb2[0], X2, two);
+  gather_adj_pair<D, 5>(G + 4 * gc, Acc + 4 * gc, d1, f1, Bb1[1], X1, d2, f2, Bb2[1], X2, two);
+  gather_adj_pair<D, 3>(G + 5 * gc, Acc + 5 * gc, d1, f1, Bb1[2], X1, d2, f2, Bb2[2], X2, two);
+}
+
+// Esirkepov transposed on a window of W nodes per axis (W = 3: every
+// position keeps one nearest node; W = 5: general), for NB bodies sharing the
+// window: reads the current adjoint lam once (like a gather) and returns, per
+// body, d(lam . J)/dX0, /dX1 (cells) and /dv.  S0 = S(xi - m), DS = S(xi + de -
+// m) - S(xi - m) on the window; then X0b = sum (gS0 - gDS) S'(xi - m),
+// X1b = sum gDS S'(xi + de - m).
+template <int D, int W, int NB>
+__device__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const float (*xi)[3],
+                            const float (*de)[3], const float *qw, const float (*v)[3], const float dxdt[3],
+                            float (*X0b)[3], float (*X1b)[3], float (*vb)[3]) {
+  constexpr int jc = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  constexpr int H = W / 2;  // window nodes n0 - H .. n0 + H
+  float S0[NB][3][W], DS[NB][3][W], gS0[NB][3][W], gDS[NB][3][W];
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int m = 0; m < W; ++m) {
+        if (a < D) {
+          const float u = xi[q][a] - (float)(m - H);
+          S0[q][a][m] = qshape(u);
+          DS[q][a][m] = qshape(u + de[q][a]) - S0[q][a][m];
+        } else {
+          S0[q][a][m] = m == H ? 1.0f : 0.0f;
+          DS[q][a][m] = 0.0f;
+        }
+        gS0[q][a][m] = gDS[q][a][m] = 0.0f;
+      }
+  const int bx = n0[0] - H, by = D >= 2 ? n0[1] - H : 0, bz = D >= 3 ? n0[2] - H : 0;
   auto L = [&](int comp, int i, int j, int k) -> float {
     return Jl[comp * jc + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k))];
   };
   if constexpr (D == 1) {
-    const float cx = -qw * dxdt[0];
     float suf = 0.0f;
 #pragma unroll
-    for (int i = 3; i >= 0; --i) {
+    for (int i = W - 2; i >= 0; --i) {
       suf += L(0, i, 0, 0);
-      gDS[0][i] += cx * suf;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) gDS[q][0][i] += -qw[q] * dxdt[0] * suf;
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      float ly = L(1, i, 0, 0), lz = L(2, i, 0, 0);
-      float sbar = S0[0][i] + 0.5f * DS[0][i];
-      float t = qw * (v[1] * ly + v[2] * lz);
-      gS0[0][i] += t;
-      gDS[0][i] += 0.5f * t;
-      vb[1] += qw * ly * sbar;
-      vb[2] += qw * lz * sbar;
+    for (int i = 0; i < W; ++i) {
+      const float ly = L(1, i, 0, 0), lz = L(2, i, 0, 0);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const float sbar = S0[q][0][i] + 0.5f * DS[q][0][i];
+        const float t = qw[q] * (v[q][1] * ly + v[q][2] * lz);
+        gS0[q][0][i] += t;
+        gDS[q][0][i] += 0.5f * t;
+        vb[q][1] += qw[q] * ly * sbar;
+        vb[q][2] += qw[q] * lz * sbar;
+      }
     }
   } else if constexpr (D == 2) {
-    const float cx = -qw * dxdt[0], cy = -qw * dxdt[1];
+    // J_x on faces i (W - 1 of them) at rows j, J_y likewise with axes swapped
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      const float fac = S0[1][j] + 0.5f * DS[1][j];
-      float P = 0.0f, sumLP = 0.0f;
-      float suf = 0.0f;
+    for (int ax = 0; ax < 2; ++ax) {
+      const int ox = 1 - ax;  // the other axis
 #pragma unroll
-      for (int i = 3; i >= 0; --i) {
-        suf += L(0, i, j, 0);
-        gDS[0][i] += cx * suf * fac;
+      for (int t = 0; t < W; ++t) {
+        float lv[W - 1];
+#pragma unroll
+        for (int s = 0; s < W - 1; ++s) lv[s] = ax == 0 ? L(0, s, t, 0) : L(1, t, s, 0);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const float c = -qw[q] * dxdt[ax];
+          const float fac = S0[q][ox][t] + 0.5f * DS[q][ox][t];
+          float suf = 0.0f, P = 0.0f, sumLP = 0.0f;
+#pragma unroll
+          for (int s = W - 2; s >= 0; --s) {
+            suf += lv[s];
+            gDS[q][ax][s] += c * suf * fac;
+          }
+#pragma unroll
+          for (int s = 0; s < W - 1; ++s) {
+            P += DS[q][ax][s];
+            sumLP += lv[s] * P;
+          }
+          gS0[q][ox][t] += c * sumLP;
+          gDS[q][ox][t] += 0.5f * c * sumLP;
+        }
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        P += DS[0][i];
-        sumLP += L(0, i, j, 0) * P;
-      }
-      gS0[1][j] += cx * sumLP;
-      gDS[1][j] += 0.5f * cx * sumLP;
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const float fac = S0[0][i] + 0.5f * DS[0][i];
-      float P = 0.0f, sumLP = 0.0f;
-      float suf = 0.0f;
+    for (int j = 0; j < W; ++j)
 #pragma unroll
-      for (int j = 3; j >= 0; --j) {
-        suf += L(1, i, j, 0);
-        gDS[1][j] += cy * suf * fac;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        P += DS[1][j];
-        sumLP += L(1, i, j, 0) * P;
-      }
-      gS0[0][i] += cy * sumLP;
-      gDS[0][i] += 0.5f * cy * sumLP;
-    }
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < W; ++i) {
         const float l = L(2, i, j, 0);
-        const float wz = S0[0][i] * S0[1][j] + 0.5f * (DS[0][i] * S0[1][j] + S0[0][i] * DS[1][j]) +
-                         (1.0f / 3.0f) * DS[0][i] * DS[1][j];
-        const float c = qw * v[2] * l;
-        vb[2] += qw * l * wz;
-        gS0[0][i] += c * (S0[1][j] + 0.5f * DS[1][j]);
-        gDS[0][i] += c * (0.5f * S0[1][j] + (1.0f / 3.0f) * DS[1][j]);
-        gS0[1][j] += c * (S0[0][i] + 0.5f * DS[0][i]);
-        gDS[1][j] += c * (0.5f * S0[0][i] + (1.0f / 3.0f) * DS[0][i]);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const float wz = S0[q][0][i] * S0[q][1][j] + 0.5f * (DS[q][0][i] * S0[q][1][j] + S0[q][0][i] * DS[q][1][j]) +
+                           (1.0f / 3.0f) * DS[q][0][i] * DS[q][1][j];
+          const float c = qw[q] * v[q][2] * l;
+          vb[q][2] += qw[q] * l * wz;
+          gS0[q][0][i] += c * (S0[q][1][j] + 0.5f * DS[q][1][j]);
+          gDS[q][0][i] += c * (0.5f * S0[q][1][j] + (1.0f / 3.0f) * DS[q][1][j]);
+          gS0[q][1][j] += c * (S0[q][0][i] + 0.5f * DS[q][0][i]);
+          gDS[q][1][j] += c * (0.5f * S0[q][0][i] + (1.0f / 3.0f) * DS[q][0][i]);
+        }
       }
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int b = (a + 1) % 3, c = (a + 2) % 3;
-      const float ca = -qw * dxdt[a];
 #pragma unroll 1
-      for (int kb = 0; kb < 5; ++kb)
+      for (int kb = 0; kb < W; ++kb)
 #pragma unroll 1
-        for (int kc = 0; kc < 5; ++kc) {
-          const float fac = S0[b][kb] * S0[c][kc] + 0.5f * (DS[b][kb] * S0[c][kc] + S0[b][kb] * DS[c][kc]) +
-                            (1.0f / 3.0f) * DS[b][kb] * DS[c][kc];
-          float lv[4];
+        for (int kc = 0; kc < W; ++kc) {
+          float lv[W - 1];
 #pragma unroll
-          for (int ka = 0; ka < 4; ++ka) {
+          for (int ka = 0; ka < W - 1; ++ka) {
             int idx[3];
             idx[a] = ka;
             idx[b] = kb;
             idx[c] = kc;
             lv[ka] = L(a, idx[0], idx[1], idx[2]);
           }
-          float suf = 0.0f, P = 0.0f, sumLP = 0.0f;
 #pragma unroll
-          for (int ka = 3; ka >= 0; --ka) {
-            suf += lv[ka];
-            gDS[a][ka] += ca * suf * fac;
-          }
+          for (int q = 0; q < NB; ++q) {
+            const float ca = -qw[q] * dxdt[a];
+            const float fac = S0[q][b][kb] * S0[q][c][kc] +
+                              0.5f * (DS[q][b][kb] * S0[q][c][kc] + S0[q][b][kb] * DS[q][c][kc]) +
+                              (1.0f / 3.0f) * DS[q][b][kb] * DS[q][c][kc];
+            float suf = 0.0f, P = 0.0f, sumLP = 0.0f;
 #pragma unroll
-          for (int ka = 0; ka < 4; ++ka) {
-            P += DS[a][ka];
-            sumLP += lv[ka] * P;
+            for (int ka = W - 2; ka >= 0; --ka) {
+              suf += lv[ka];
+              gDS[q][a][ka] += ca * suf * fac;
+            }
+#pragma unroll
+            for (int ka = 0; ka < W - 1; ++ka) {
+              P += DS[q][a][ka];
+              sumLP += lv[ka] * P;
+            }
+            gS0[q][b][kb] += ca * sumLP * (S0[q][c][kc] + 0.5f * DS[q][c][kc]);
+            gDS[q][b][kb] += ca * sumLP * (0.5f * S0[q][c][kc] + (1.0f / 3.0f) * DS[q][c][kc]);
+            gS0[q][c][kc] += ca * sumLP * (S0[q][b][kb] + 0.5f * DS[q][b][kb]);
+            gDS[q][c][kc] += ca * sumLP * (0.5f * S0[q][b][kb] + (1.0f / 3.0f) * DS[q][b][kb]);
           }
-          gS0[b][kb] += ca * sumLP * (S0[c][kc] + 0.5f * DS[c][kc]);
-          gDS[b][kb] += ca * sumLP * (0.5f * S0[c][kc] + (1.0f / 3.0f) * DS[c][kc]);
-          gS0[c][kc] += ca * sumLP * (S0[b][kb] + 0.5f * DS[b][kb]);
-          gDS[c][kc] += ca * sumLP * (0.5f * S0[b][kb] + (1.0f / 3.0f) * DS[b][kb]);
         }
     }
   }
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    float x0 = 0.0f, x1 = 0.0f;
+  for (int q = 0; q < NB; ++q)
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      x0 += (gS0[a][m] - gDS[a][m]) * dS0[a][m];
-      x1 += gDS[a][m] * dS1[a][m];
+    for (int a = 0; a < D; ++a) {
+      float x0 = 0.0f, x1 = 0.0f;
+#pragma unroll
+      for (int m = 0; m < W; ++m) {
+        const float u = xi[q][a] - (float)(m - H);
+        x0 += (gS0[q][a][m] - gDS[q][a][m]) * dqshape(u);
+        x1 += gDS[q][a][m] * dqshape(u + de[q][a]);
+      }
+      X0b[q][a] += x0;
+      X1b[q][a] += x1;
     }
-    X0b[a] += x0;
-    X1b[a] += x1;
-  }
+}
+
+// the rare case out of line (keeps the fast path's registers)
+template <int D>
+__device__ __noinline__ void deposit_adj_general(const float *Jl, const int *nn, const int *n2, const float (*xi)[3],
+                                                 const float (*dd)[3], const float *qw, const float (*vv)[3],
+                                                 const float *dxdt, float (*X0)[3], float (*X1)[3], float (*vb)[3],
+                                                 bool two) {
+  int a1[3] = {nn[0], nn[1], nn[2]}, a2[3] = {n2[0], n2[1], n2[2]};
+  float dx3[3] = {dxdt[0], dxdt[1], dxdt[2]};
+  deposit_adj<D, 5, 1>(Jl, a1, xi, dd, qw, vv, dx3, X0, X1, vb);
+  if (two) deposit_adj<D, 5, 1>(Jl, a2, xi + 1, dd + 1, qw + 1, vv + 1, dx3, X0 + 1, X1 + 1, vb + 1);
 }
 
 struct AdjState {
@@ -553,11 +617,47 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
     }
   }
   const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
-  // deposit transposed
+  // deposit transposed: three-node window shared by both bodies when every
+  // position keeps one nearest node, else five-node windows per body
   float X10b[3] = {0, 0, 0}, X11b[3] = {0, 0, 0}, X20b[3] = {0, 0, 0}, X21b[3] = {0, 0, 0};
   float v1b[3] = {0, 0, 0}, v2b[3] = {0, 0, 0};
-  deposit_adj<D>(Jl, d, f, de1, sp.qw1, v1, dxdt, X10b, X11b, v1b);
-  if (two) deposit_adj<D>(Jl, d2, f2, de2, sp.qw2, v2, dxdt, X20b, X21b, v2b);
+  {
+    bool fast = true;
+    float xi[2][3] = {{0, 0, 0}, {0, 0, 0}}, dd[2][3], vv[2][3];
+    int nn[3] = {2, 2, 2}, n2[3] = {2, 2, 2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dd[0][a] = de1[a];
+      dd[1][a] = de2[a];
+      vv[0][a] = v1[a];
+      vv[1][a] = v2[a];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int up1 = f[a] >= 0.5f ? 1 : 0, up2 = f2[a] >= 0.5f ? 1 : 0;
+      xi[0][a] = f[a] - (float)up1;
+      xi[1][a] = f2[a] - (float)up2;
+      nn[a] = d[a] + Box<D>::OJ + up1;
+      n2[a] = d2[a] + Box<D>::OJ + up2;
+      const float x1n = xi[0][a] + de1[a], x2n = xi[1][a] + de2[a];
+      fast &= x1n >= -0.5f && x1n < 0.5f;
+      if (two) fast &= nn[a] == n2[a] && x2n >= -0.5f && x2n < 0.5f;
+    }
+    const float qw[2] = {sp.qw1, sp.qw2};
+    float X0[2][3] = {{0, 0, 0}, {0, 0, 0}}, X1[2][3] = {{0, 0, 0}, {0, 0, 0}}, vb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (fast && two) {
+      deposit_adj<D, 3, 2>(Jl, nn, xi, dd, qw, vv, dxdt, X0, X1, vb);
+    } else if (fast) {
+      deposit_adj<D, 3, 1>(Jl, nn, xi, dd, qw, vv, dxdt, X0, X1, vb);
+    } else {
+      deposit_adj_general<D>(Jl, nn, n2, xi, dd, qw, vv, dxdt, X0, X1, vb, two);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      X10b[a] = X0[0][a]; X11b[a] = X1[0][a]; v1b[a] = vb[0][a];
+      X20b[a] = X0[1][a]; X21b[a] = X1[1][a]; v2b[a] = vb[1][a];
+    }
+  }
   // carried adjoints of x^{n+1}, u^{n+1/2}
   const long long sc = S.cap;
   float xb1[3], xb2[3], ub1[3], ub2[3];
@@ -610,8 +710,7 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
   }
   // gather transposed; old positions through the deposit
   float Xg1[3] = {0, 0, 0}, Xg2[3] = {0, 0, 0};
-  gather_adj_all<D>(Gsm, Acc, d, f, Eb1, Bb1, Xg1);
-  if (two) gather_adj_all<D>(Gsm, Acc, d2, f2, Eb2, Bb2, Xg2);
+  gather_adj_all<D>(Gsm, Acc, d, f, Eb1, Bb1, Xg1, d2, f2, Eb2, Bb2, Xg2, two);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     xb1[a] += (Xg1[a] + X10b[a]) * g.idx[a];
@@ -627,7 +726,7 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_push(GridP g, AdjArgs A) {
+__global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjArgs A) {
   using BX = Box<D>;
   constexpr int GC = BX::GCELLS, JC = BX::JCELLS;
   extern __shared__ __align__(16) unsigned char smem[];

@@ -223,7 +223,7 @@ def cfg0_neutral_1d(ppc: int = 16, seed: int = 0, steps: int = 3000, nb: float =
     n = (nx, 1, 1)
     probe = np.array([_lin(n, int(probe_x * cells_per_lambda))], dtype=np.int64)
     return Workload("cfg0_neutral_1d", 1, (nx,), (dx,), 0.95 * dx, (1,), steps, sp, las,
-                    tile=(64,), probe_comp=1, probe_nodes=probe,
+                    tile=(16,), probe_comp=1, probe_nodes=probe,
                     meta=dict(slab=(lo, hi), ppc=ppc, nb=nb, omega_b=omega_b, Zb=Zb))
 
 
@@ -256,7 +256,7 @@ def cfg1_bragg_2d(seed: int = 1, steps: int = 4000, n: int = 2048, cells_per_lam
     las = [Laser(comp=1, a0=1e-3, theta=th, waist=waist_lambda * LAMBDA0, fwhm=fwhm, t0=1.5 * fwhm,
                  ia=ia, yc=yc)]
     dt = 0.95 * dx / math.sqrt(2.0)
-    return Workload("cfg1_bragg_2d", 2, (n, n), (dx, dx), dt, (1, 1), steps, sp, las, tile=(32, 32),
+    return Workload("cfg1_bragg_2d", 2, (n, n), (dx, dx), dt, (1, 1), steps, sp, las, tile=(16, 16),
                     meta=dict(d=d, sites=sites, theta=th, origin=origin))
 
 
@@ -315,7 +315,7 @@ def cfg3_adjoint_2d(seed: int = 3, target_seed: int = 33, steps: int = 400, n=(1
     ip = int(probe_x * cells_per_lambda)
     probe = np.array([_lin((nx, ny, 1), ip, j) for j in range(ny)], dtype=np.int64)
     return Workload("cfg3_adjoint_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
-                    tile=(32, 32), probe_comp=2, probe_nodes=probe,
+                    tile=(16, 16), probe_comp=2, probe_nodes=probe,
                     meta=dict(sites=sites, off=off, site_of_ion=site_of_ion, column=column,
                               per_site=per_site, omega=omega))
 
@@ -352,5 +352,5 @@ def cfg4_ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), ce
     las = [Laser(comp=1, a0=a0, fwhm=fwhm, t0=1.5 * fwhm, ia=8)]
     dt = 0.95 * dx / math.sqrt(2.0)
     return Workload("cfg4_ionized_crystal_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
-                    tile=(32, 32), free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
+                    tile=(16, 16), free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
                     meta=dict(sites=st, lo=lo, hi=hi, sigma=sigma))
