@@ -215,9 +215,12 @@ def run_adjoint_ratio(steps=400, K=20):
             "ratio": (t_fwd + t_bwd) / t_plain}
 
 
-def our_config(n_ion, mode, world):
+def our_config(n_ion, mode, world, warmup=3, steps=500):
     return {"workload": "cfg2_neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
                         f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, {mode} deposit",
+            "timed": f"steps {warmup}..{warmup + steps} of the run from t=0 (the field front crosses the "
+                     "medium during the run; an ion it has not reached is a co-moving neutral pair and "
+                     "deposits nothing)",
             "l2": "inputs larger than L2 (particles 13.7 GB)", "parallelism": f"replicas x{world}"}
 
 
@@ -230,7 +233,10 @@ def run_reference(args, rank, world):
         return
     import oracle as O
     from paper_2208_08038_gb300 import synth
-    n = (16, 16, 16)
+    # box side sized so that the K timed steps take about a minute at the
+    # oracle's ~1.7e5 ion-pushes/s
+    side = int(max(8, min(16, round((60.0 * 1.7e5 / max(args.steps, 1) / 8) ** (1.0 / 3.0)))))
+    n = (side, side, side)
     wl = synth.cfg2_neutral_3d(n=n, margin=0)
     wl.bc = (0, 0, 0)
     sp = wl.species[0]
@@ -244,7 +250,7 @@ def run_reference(args, rank, world):
     s.close()
     value = len(sp.x) * args.steps / el
     wl_full, n_ion = workload_cfg2()
-    sample = f"16^3-cell periodic box of the 3D workload ({len(sp.x)} ions, 8/cell), FP64, {args.steps} timed steps"
+    sample = f"{side}^3-cell periodic box of the 3D workload ({len(sp.x)} ions, 8/cell), FP64, {args.steps} timed steps"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -257,12 +263,13 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500,
+                    help="timed steps (default: the workload's whole 500-step run)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="sorted", choices=["sorted", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default: --steps)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only the adjoint/forward ratio of the 2D adjoint workload over STEPS steps")
@@ -343,8 +350,9 @@ def main():
     # (bp_load_particles: copy, device-side conversion, sort), runs the steps
     # and reads every step's E_y field back to pinned host memory
     e2e = None
-    if args.e2e_steps > 0:
-        e2e = run_e2e(wl, n_ion, mode, args.e2e_steps, rank, world)
+    e2e_steps = args.steps if args.e2e_steps < 0 else args.e2e_steps
+    if e2e_steps > 0:
+        e2e = run_e2e(wl, n_ion, mode, e2e_steps, rank, world)
     hbm, src = peaks()
     # algorithmic bytes of one push launch: every ion's state read and written
     # (2 x 52 B: cell, 3 offsets, r, u1, u2), E and B read once (24 B/cell),
@@ -357,7 +365,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": our_config(n_ion, args.mode, world),
+        "config": our_config(n_ion, args.mode, world, args.warmup, args.steps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "k_push<3,sorted>",
                      "peak_source": src, "push_ms_per_launch": push_avg},

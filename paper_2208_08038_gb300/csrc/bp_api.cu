@@ -71,7 +71,10 @@ int check_launch(bp_ctx *c, const char *what) {
 }
 
 // fixed-point scale of the sorted deposit: a power of two such that one
-// particle's largest contribution (|q w| max(1, dx/dt)) maps to about 2^40
+// particle's largest contribution (|q w| max(1, dx/dt)) maps to about 2^36.
+// A node of a tile box then holds the exact sum of up to 2^26 such maximal
+// contributions, and a quantum is about 1e-11 of the largest one (below the
+// FP32 rounding of the contributions themselves).
 void update_jscale(bp_ctx *c) {
   if (!c->det) {
     c->jscale = c->jinv = 0.0f;
@@ -81,7 +84,7 @@ void update_jscale(bp_ctx *c) {
   for (int a = 0; a < c->g.D; ++a) f = std::max(f, c->g.dxd[a] / c->g.dtd);
   for (auto &s : c->sp) B = std::max({B, std::fabs(s.sp.q1d * s.sp.wd), std::fabs(s.sp.q2d * s.sp.wd)});
   if (B <= 0) B = 1.0;
-  int k = 40 - (int)std::ceil(std::log2(B * f));
+  int k = 36 - (int)std::ceil(std::log2(B * f));
   k = std::max(-100, std::min(100, k));
   c->jscale = std::ldexp(1.0f, k);
   c->jinv = std::ldexp(1.0f, -k);

@@ -33,6 +33,8 @@ __device__ __forceinline__ void make_loc(const int d[3], const float f[3], Loc &
 
 // one field component with stagger pattern PAT (bit a: half cell along a)
 // at two bodies; loads are shared when both stencils start at the same node
+// for every active lane of the warp (a warp-uniform choice: both forms give
+// the same sums, and a uniform branch keeps the warp from running both)
 template <int D, int PAT>
 __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const Loc &A, const Loc &Bo, float &oa,
                                             float &ob) {
@@ -49,7 +51,8 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
     wb[a] = half ? Bo.wh[a] : Bo.wn[a];
   }
   constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
-  const bool same = (ba[0] == bb[0]) && (D < 2 || ba[1] == bb[1]) && (D < 3 || ba[2] == bb[2]);
+  const bool same = __all_sync(__activemask(),
+                               (ba[0] == bb[0]) && (D < 2 || ba[1] == bb[1]) && (D < 3 || ba[2] == bb[2]));
   float sa = 0.0f, sb = 0.0f;
   if (same) {
 #pragma unroll

@@ -6,7 +6,10 @@
 // modified Coulomb force, body currents q v / dV).  One CTA per tile:
 //   1. stage E and B of the tile plus halo in shared memory (FP32),
 //   2. push every particle of the tile (all species), accumulating the
-//      current of both bodies in a shared-memory box (tile + halo):
+//      current of both bodies in a shared-memory box (tile + halo).  A
+//      particle whose bodies keep their nearest nodes deposits on the spot
+//      (three-node windows); the others leave a five-node record that the
+//      whole block deposits after the pass.  The box holds
 //        BP_DEPOSIT_SORTED: 64-bit fixed point (integer adds are associative,
 //                           so the box is bit-identical whatever the order),
 //        BP_DEPOSIT_ATOMIC: FP32 shared atomics,
@@ -20,290 +23,170 @@
 
 namespace {
 
+// capacity of the deferred-deposit records per tile (shared memory); a tile
+// with more general-case particles deposits the rest in place
+__host__ __device__ constexpr int push_qmax(int D) { return D == 3 ? 96 : (D == 2 ? 128 : 64); }
+
+// float -> int64, rounded to nearest even, on the FP32 and integer pipes
+// (the 64-bit conversion runs on the slow FP64 unit).  Adding 1.5 * 2^23 to
+// a float of magnitude below 2^22 rounds it to an integer held in the low
+// mantissa bits; x is split exactly as h 2^22 + l with h = rne(x / 2^22) and
+// |l| <= 2^21, and both parts are rounded that way.  Valid for |x| < 2^44.
+__device__ __forceinline__ long long f2ll_rn(float x) {
+  constexpr float M = 12582912.0f;
+  const float hs = __fadd_rn(x * 2.384185791015625e-07f, M);
+  const float h = __fsub_rn(hs, M);
+  const float l = fmaf(-h, 4194304.0f, x);
+  const int hi = __float_as_int(hs) - 0x4B400000;
+  const int lo = __float_as_int(__fadd_rn(l, M)) - 0x4B400000;
+  return (long long)hi * 4194304LL + (long long)lo;
+}
+
+// add v (already in fixed-point units in the sorted mode) to a current node.
+// Sorted mode: each 64-bit node word (biased by 2^31, see JBIAS) is updated
+// with the GPU's native 32-bit shared atomics: the low word takes the low 32
+// bits of the contribution and returns its old value, and the high word
+// takes the high 32 bits plus the carry out of the low word -- usually zero,
+// so usually one atomic.  The final word is the exact 64-bit sum whatever
+// the order.  (64-bit and FP32 shared atomic adds are compare-and-swap loops
+// on this GPU; 32-bit integer adds are single instructions.)
+// Atomic mode: FP32 shared atomics.  Zero contributions are skipped.
+constexpr long long JBIAS = 0x80000000LL;
+
 template <bool DET, typename JT>
-__device__ __forceinline__ void jadd(JT *p, float v, float scale) {
-  if (v == 0.0f) return;
+__device__ __forceinline__ void jput(JT *p, float v) {
   if constexpr (DET) {
-    long long q = __float2ll_rn(v * scale);
-    if (q) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)q);
+    if (fabsf(v) <= 0.5f) return;
+    unsigned int lo;
+    int hi;
+    if (fabsf(v) < 2147483648.0f) {
+      const int q = __float2int_rn(v);
+      lo = (unsigned int)q;
+      hi = q < 0 ? -1 : 0;
+    } else {
+      const long long q = f2ll_rn(v);
+      lo = (unsigned int)(unsigned long long)q;
+      hi = (int)(q >> 32);
+    }
+    unsigned int *w = reinterpret_cast<unsigned int *>(p);
+    const unsigned int old = atomicAdd(w, lo);
+    hi += (old + lo < old) ? 1 : 0;
+    if (hi) atomicAdd(reinterpret_cast<int *>(w + 1), hi);
   } else {
+    if (v == 0.0f) return;
     atomicAdd(p, v);
   }
 }
 
-// Esirkepov density decomposition for NB bodies sharing one window:
-//   3D W_x = DSx (S0y S0z + (DSy S0z + S0y DSz)/2 + DSy DSz/3) (cyclic),
-//   2D W_x = DSx (S0y + DSy/2), J_z with S0x S0y + (DSx S0y + S0x DSy)/2 + DSx DSy/3,
-//   1D W_x = DSx, J_y/z with S0 + DS/2,
-// J_a on the face after node i = -qw dx_a/dt * sum_{i' <= i} W_a(i').
-template <int D, bool DET, int NB, typename JT>
-__device__ __forceinline__ void esirkepov(JT *__restrict__ J, const int n0[3], const float (*S0)[3][5],
-                                          const float (*DS)[3][5], const float *qw, const float (*v)[3],
-                                          const float dxdt[3], float scale) {
-  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
-  JT *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
-  const int bx = n0[0] - 2, by = n0[1] - 2, bz = n0[2] - 2;
-  if constexpr (D == 1) {
-    float run[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        run[b] += DS[b][0][i];
-        jx += -qw[b] * dxdt[0] * run[b];
-        float sb = S0[b][0][i] + 0.5f * DS[b][0][i];
-        jy += qw[b] * v[b][1] * sb;
-        jz += qw[b] * v[b][2] * sb;
-      }
-      if (i < 4) jadd<DET>(Jx + bx + i, jx, scale);
-      jadd<DET>(Jy + bx + i, jy, scale);
-      jadd<DET>(Jz + bx + i, jz, scale);
-    }
-  } else if constexpr (D == 2) {
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      float fac[NB];
-      bool any = false;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        fac[b] = S0[b][1][j] + 0.5f * DS[b][1][j];
-        any |= fac[b] != 0.0f;
-      }
-      if (!any) continue;
-      float run[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float jx = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          run[b] += DS[b][0][i];
-          jx += -qw[b] * dxdt[0] * run[b] * fac[b];
-        }
-        jadd<DET>(Jx + (bx + i) + jb0 * (by + j), jx, scale);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      float fac[NB];
-      bool any = false;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        fac[b] = S0[b][0][i] + 0.5f * DS[b][0][i];
-        any |= fac[b] != 0.0f;
-      }
-      if (!any) continue;
-      float run[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float jy = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          run[b] += DS[b][1][j];
-          jy += -qw[b] * dxdt[1] * run[b] * fac[b];
-        }
-        jadd<DET>(Jy + (bx + i) + jb0 * (by + j), jy, scale);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        float jz = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          float w = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
-                    (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
-          jz += qw[b] * v[b][2] * w;
-        }
-        jadd<DET>(Jz + (bx + i) + jb0 * (by + j), jz, scale);
-      }
-  } else {
-    // J_x
-#pragma unroll 1
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        float fac[NB];
-        bool any = false;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          fac[b] = S0[b][1][j] * S0[b][2][k] + 0.5f * (DS[b][1][j] * S0[b][2][k] + S0[b][1][j] * DS[b][2][k]) +
-                   (1.0f / 3.0f) * DS[b][1][j] * DS[b][2][k];
-          any |= fac[b] != 0.0f;
-        }
-        if (!any) continue;
-        float run[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          float jx = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            run[b] += DS[b][0][i];
-            jx += -qw[b] * dxdt[0] * run[b] * fac[b];
-          }
-          jadd<DET>(Jx + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jx, scale);
-        }
-      }
-    // J_y
-#pragma unroll 1
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        float fac[NB];
-        bool any = false;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          fac[b] = S0[b][0][i] * S0[b][2][k] + 0.5f * (DS[b][0][i] * S0[b][2][k] + S0[b][0][i] * DS[b][2][k]) +
-                   (1.0f / 3.0f) * DS[b][0][i] * DS[b][2][k];
-          any |= fac[b] != 0.0f;
-        }
-        if (!any) continue;
-        float run[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float jy = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            run[b] += DS[b][1][j];
-            jy += -qw[b] * dxdt[1] * run[b] * fac[b];
-          }
-          jadd<DET>(Jy + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jy, scale);
-        }
-      }
-    // J_z
-#pragma unroll 1
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        float fac[NB];
-        bool any = false;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          fac[b] = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
-                   (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
-          any |= fac[b] != 0.0f;
-        }
-        if (!any) continue;
-        float run[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) run[b] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float jz = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            run[b] += DS[b][2][k];
-            jz += -qw[b] * dxdt[2] * run[b] * fac[b];
-          }
-          jadd<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k)), jz, scale);
-        }
-      }
-  }
+template <bool DET, typename JT>
+__device__ __forceinline__ void jadd(JT *p, float v, float scale) {
+  jput<DET>(p, DET ? v * scale : v);
 }
-
 
 // Fast path: all four positions (both bodies, before and after the move)
 // share one nearest node per axis, so the window is the three nodes around
 // it and S1 - S0 has a closed form in the move d (no cancellation):
 //   node n-1: -d (1 - 2 xi - d) / 2,  node n: -d (2 xi + d),  node n+1: d (1 + 2 xi + d) / 2
 // with xi = old position - n.  J along a simulated axis then lives on the two
-// faces inside the window.
+// faces inside the window, with partial sums DS(n-1) and DS(n-1) + DS(n) =
+// -DS(n+1).  The Esirkepov factor of the two transverse axes is written
+//   S0y S0z + (DSy S0z + S0y DSz)/2 + DSy DSz/3 = Ay Az + DSy DSz/12,
+// A = S0 + DS/2 the mid-step shape.  In the sorted mode the charge factors
+// carry the fixed-point scale (a power of two, so the products round
+// exactly as unscaled ones).  The two bodies' terms are added without FMA
+// contraction so that a neutral pair moving together cancels exactly.
 template <int D, bool DET, int NB, typename JT>
 __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], const float (*xi)[3],
                                            const float (*de)[3], const float *qw, const float (*v)[3],
                                            const float dxdt[3], float scale) {
   constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
-  float S0[NB][3][3], DS[NB][3][3], P[NB][3][2];
+  constexpr float K12 = 1.0f / 12.0f;
+  const float sc = DET ? scale : 1.0f;
+  float A[NB][3][3], DS[NB][3][3], DK[NB][3][3], cP[NB][3][2];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a < D) {
         const float x = xi[b][a], d = de[b][a];
-        qweights(x, S0[b][a]);
-        DS[b][a][0] = -0.5f * d * (1.0f - 2.0f * x - d);
-        DS[b][a][1] = -d * (2.0f * x + d);
-        DS[b][a][2] = 0.5f * d * (1.0f + 2.0f * x + d);
-        P[b][a][0] = DS[b][a][0];
-        P[b][a][1] = DS[b][a][0] + DS[b][a][1];
+        float S0[3];
+        qweights(x, S0);
+        const float d0 = -0.5f * d * (1.0f - 2.0f * x - d);
+        const float d1 = -d * (2.0f * x + d);
+        const float d2 = 0.5f * d * (1.0f + 2.0f * x + d);
+        A[b][a][0] = fmaf(0.5f, d0, S0[0]);
+        A[b][a][1] = fmaf(0.5f, d1, S0[1]);
+        A[b][a][2] = fmaf(0.5f, d2, S0[2]);
+        DS[b][a][0] = d0;
+        DS[b][a][1] = d1;
+        DS[b][a][2] = d2;
+        DK[b][a][0] = K12 * d0;
+        DK[b][a][1] = K12 * d1;
+        DK[b][a][2] = K12 * d2;
+        const float c = -qw[b] * dxdt[a] * sc;
+        cP[b][a][0] = c * d0;
+        cP[b][a][1] = -c * d2;
       } else {
-        S0[b][a][0] = S0[b][a][2] = 0.0f;
-        S0[b][a][1] = 1.0f;
+        A[b][a][0] = A[b][a][2] = 0.0f;
+        A[b][a][1] = 1.0f;
         DS[b][a][0] = DS[b][a][1] = DS[b][a][2] = 0.0f;
-        P[b][a][0] = P[b][a][1] = 0.0f;
+        DK[b][a][0] = DK[b][a][1] = DK[b][a][2] = 0.0f;
+        cP[b][a][0] = cP[b][a][1] = 0.0f;
       }
     }
   JT *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
   const int bx = n[0] - 1, by = n[1] - 1, bz = n[2] - 1;
-  float cq[NB][3];
-#pragma unroll
-  for (int b = 0; b < NB; ++b)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) cq[b][a] = -qw[b] * dxdt[a];
   if constexpr (D == 1) {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      float jx = 0.0f;
+      float jx = cP[0][0][f];
+      if constexpr (NB == 2) jx = __fadd_rn(jx, cP[1][0][f]);
+      jput<DET>(Jx + bx + f, jx);
+    }
+    float qy[NB], qz[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) jx = __fadd_rn(jx, __fmul_rn(cq[b][0], P[b][0][f]));
-      jadd<DET>(Jx + bx + f, jx, scale);
+    for (int b = 0; b < NB; ++b) {
+      qy[b] = qw[b] * v[b][1] * sc;
+      qz[b] = qw[b] * v[b][2] * sc;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      float jy = 0.0f, jz = 0.0f;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        float sb = S0[b][0][i] + 0.5f * DS[b][0][i];
-        jy = __fadd_rn(jy, __fmul_rn(qw[b] * v[b][1], sb));
-        jz = __fadd_rn(jz, __fmul_rn(qw[b] * v[b][2], sb));
+      float jy = __fmul_rn(qy[0], A[0][0][i]), jz = __fmul_rn(qz[0], A[0][0][i]);
+      if constexpr (NB == 2) {
+        jy = __fadd_rn(jy, __fmul_rn(qy[1], A[1][0][i]));
+        jz = __fadd_rn(jz, __fmul_rn(qz[1], A[1][0][i]));
       }
-      jadd<DET>(Jy + bx + i, jy, scale);
-      jadd<DET>(Jz + bx + i, jz, scale);
+      jput<DET>(Jy + bx + i, jy);
+      jput<DET>(Jz + bx + i, jz);
     }
   } else if constexpr (D == 2) {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
-        float jx = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-          jx = __fadd_rn(jx, __fmul_rn(cq[b][0] * P[b][0][f], S0[b][1][j] + 0.5f * DS[b][1][j]));
-        jadd<DET>(Jx + (bx + f) + jb0 * (by + j), jx, scale);
+        float jx = __fmul_rn(cP[0][0][f], A[0][1][j]);
+        if constexpr (NB == 2) jx = __fadd_rn(jx, __fmul_rn(cP[1][0][f], A[1][1][j]));
+        jput<DET>(Jx + (bx + f) + jb0 * (by + j), jx);
       }
 #pragma unroll
     for (int g = 0; g < 2; ++g)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        float jy = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-          jy = __fadd_rn(jy, __fmul_rn(cq[b][1] * P[b][1][g], S0[b][0][i] + 0.5f * DS[b][0][i]));
-        jadd<DET>(Jy + (bx + i) + jb0 * (by + g), jy, scale);
+        float jy = __fmul_rn(cP[0][1][g], A[0][0][i]);
+        if constexpr (NB == 2) jy = __fadd_rn(jy, __fmul_rn(cP[1][1][g], A[1][0][i]));
+        jput<DET>(Jy + (bx + i) + jb0 * (by + g), jy);
       }
+    float qz[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) qz[b] = qw[b] * v[b][2] * sc;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        float jz = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          float w = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
-                    (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
-          jz = __fadd_rn(jz, __fmul_rn(qw[b] * v[b][2], w));
-        }
-        jadd<DET>(Jz + (bx + i) + jb0 * (by + j), jz, scale);
+        float jz = __fmul_rn(qz[0], fmaf(A[0][0][i], A[0][1][j], DK[0][0][i] * DS[0][1][j]));
+        if constexpr (NB == 2)
+          jz = __fadd_rn(jz, __fmul_rn(qz[1], fmaf(A[1][0][i], A[1][1][j], DK[1][0][i] * DS[1][1][j])));
+        jput<DET>(Jz + (bx + i) + jb0 * (by + j), jz);
       }
   } else {
 #pragma unroll
@@ -312,15 +195,12 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
       for (int j = 0; j < 3; ++j) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-          F[b] = S0[b][1][j] * S0[b][2][k] + 0.5f * (DS[b][1][j] * S0[b][2][k] + S0[b][1][j] * DS[b][2][k]) +
-                 (1.0f / 3.0f) * DS[b][1][j] * DS[b][2][k];
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][1][j], A[b][2][k], DK[b][1][j] * DS[b][2][k]);
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
-          float jx = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) jx = __fadd_rn(jx, __fmul_rn(cq[b][0] * P[b][0][f], F[b]));
-          jadd<DET>(Jx + (bx + f) + jb0 * ((by + j) + jb1 * (bz + k)), jx, scale);
+          float jx = __fmul_rn(cP[0][0][f], F[0]);
+          if constexpr (NB == 2) jx = __fadd_rn(jx, __fmul_rn(cP[1][0][f], F[1]));
+          jput<DET>(Jx + (bx + f) + jb0 * ((by + j) + jb1 * (bz + k)), jx);
         }
       }
 #pragma unroll
@@ -329,15 +209,12 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
       for (int i = 0; i < 3; ++i) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-          F[b] = S0[b][0][i] * S0[b][2][k] + 0.5f * (DS[b][0][i] * S0[b][2][k] + S0[b][0][i] * DS[b][2][k]) +
-                 (1.0f / 3.0f) * DS[b][0][i] * DS[b][2][k];
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], A[b][2][k], DK[b][0][i] * DS[b][2][k]);
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-          float jy = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) jy = __fadd_rn(jy, __fmul_rn(cq[b][1] * P[b][1][g], F[b]));
-          jadd<DET>(Jy + (bx + i) + jb0 * ((by + g) + jb1 * (bz + k)), jy, scale);
+          float jy = __fmul_rn(cP[0][1][g], F[0]);
+          if constexpr (NB == 2) jy = __fadd_rn(jy, __fmul_rn(cP[1][1][g], F[1]));
+          jput<DET>(Jy + (bx + i) + jb0 * ((by + g) + jb1 * (bz + k)), jy);
         }
       }
 #pragma unroll
@@ -346,58 +223,117 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
       for (int i = 0; i < 3; ++i) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-          F[b] = S0[b][0][i] * S0[b][1][j] + 0.5f * (DS[b][0][i] * S0[b][1][j] + S0[b][0][i] * DS[b][1][j]) +
-                 (1.0f / 3.0f) * DS[b][0][i] * DS[b][1][j];
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], A[b][1][j], DK[b][0][i] * DS[b][1][j]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float jz = 0.0f;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) jz = __fadd_rn(jz, __fmul_rn(cq[b][2] * P[b][2][h], F[b]));
-          jadd<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + h)), jz, scale);
+          float jz = __fmul_rn(cP[0][2][h], F[0]);
+          if constexpr (NB == 2) jz = __fadd_rn(jz, __fmul_rn(cP[1][2][h], F[1]));
+          jput<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + h)), jz);
         }
       }
   }
 }
 
-// general case (a position changes nearest node, or the bodies straddle a
-// node boundary): five-node windows per body; kept out of line so the fast
-// path keeps its registers
-template <int D, bool DET, typename JT>
-__device__ __noinline__ void general_deposit(JT *Jsm, const GridP &g, const float *f, const float *de1, const int *d,
-                                             const float *f2, const float *de2, const int *d2, bool two, float qw1,
-                                             float qw2, const float *v1, const float *v2, float scale) {
-  const float dxdt[3] = {g.dx[0] / g.dt, g.dx[1] / g.dt, g.dx[2] / g.dt};
-  float S0[2][3][5], DS[2][3][5];
-  float vv[2][3];
-  float qw[2] = {qw1, qw2};
-  int n1[3], n2[3];
-  float fa[3], fb[3], da[3], db[3];
-  int ia[3], ib[3];
+// Deferred general deposits.  A thread whose particle leaves the fast path
+// finishes the push and stores the particle's five-node windows in a
+// shared-memory record; after the main pass the whole block deposits the
+// records row by row (one row: one current component along one line of the
+// window), so the rare general case does not leave most of the block idle.
+struct QRec {
+  float S0[2][3][5];
+  float DS[2][3][5];
+  float cq[2][3];  // component along a simulated axis: -qw dx/dt; otherwise qw v
+  int n0[2][3];
+  int nb;
+};
+
+// a general-case particle's deposit inputs, gathered into one object inside
+// the rare branch (so the main path's arrays stay in registers)
+struct QIn {
+  float f[3], de1[3], f2[3], de2[3], v1[3], v2[3], dxdt[3];
+  int d[3], d2[3];
+  float qw1, qw2;
+  int two;
+};
+
+template <int D>
+__device__ __noinline__ void queue_record(QRec &R, const QIn &in) {
+  float S0[3][5], DS[3][5];
+  int n0[3];
+  const int nb = in.two ? 2 : 1;
+  for (int b = 0; b < nb; ++b) {
+    window<D>(b ? in.f2 : in.f, b ? in.de2 : in.de1, S0, DS, n0, b ? in.d2 : in.d);
+    const float qw = b ? in.qw2 : in.qw1;
+    const float *v = b ? in.v2 : in.v1;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    vv[0][a] = v1[a];
-    vv[1][a] = v2[a];
-    fa[a] = f[a]; fb[a] = f2[a]; da[a] = de1[a]; db[a] = de2[a]; ia[a] = d[a]; ib[a] = d2[a];
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        R.S0[b][a][m] = S0[a][m];
+        R.DS[b][a][m] = DS[a][m];
+      }
+      R.n0[b][a] = n0[a];
+      R.cq[b][a] = a < D ? -qw * in.dxdt[a] : qw * v[a];
+    }
   }
-  window<D>(fa, da, S0[0], DS[0], n1, ia);
-  if (two) {
-    window<D>(fb, db, S0[1], DS[1], n2, ib);
-    const bool same = (n1[0] == n2[0]) && (D < 2 || n1[1] == n2[1]) && (D < 3 || n1[2] == n2[2]);
-    if (same) {
-      esirkepov<D, DET, 2>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
-    } else {
-      esirkepov<D, DET, 1>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
-      esirkepov<D, DET, 1>(Jsm, n2, S0 + 1, DS + 1, qw + 1, vv + 1, dxdt, scale);
+  R.nb = nb;
+}
+
+// rows of component c: one per node of the window along each simulated axis
+// other than c
+template <int D>
+__host__ __device__ constexpr int qrows(int c) {
+  return (((c == 0 ? 1 : 0) < D) ? 5 : 1) * (((c == 2 ? 1 : 2) < D) ? 5 : 1);
+}
+
+template <int D, bool DET, typename JT>
+__device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, int row, float scale) {
+  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  const int p = c == 0 ? 1 : 0, q = c == 2 ? 1 : 2;  // the other two axes, p < q
+  const int ip = p < D ? row % 5 : 2, iq = q < D ? row / 5 : 2;
+  const float sp = R.S0[b][p][ip], dp = R.DS[b][p][ip], sq = R.S0[b][q][iq], dq = R.DS[b][q][iq];
+  const float fac = sp * sq + 0.5f * (dp * sq + sp * dq) + (1.0f / 3.0f) * dp * dq;
+  if (fac == 0.0f) return;
+  int node[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) node[a] = 0;
+  if (p < D) node[p] = R.n0[b][p] - 2 + ip;
+  if (q < D) node[q] = R.n0[b][q] - 2 + iq;
+  const float cq = R.cq[b][c];
+  JT *Jc = J + c * jcells;
+  if (c < D) {
+    const int b0 = R.n0[b][c] - 2;
+    const int stride = c == 0 ? 1 : (c == 1 ? jb0 : jb0 * jb1);
+    const int lin0 = (c == 0 ? 0 : node[0]) + jb0 * ((c == 1 ? 0 : node[1]) + jb1 * (c == 2 ? 0 : node[2]));
+    float run = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      run += R.DS[b][c][i];
+      jadd<DET>(Jc + lin0 + (b0 + i) * stride, cq * run * fac, scale);
     }
   } else {
-    esirkepov<D, DET, 1>(Jsm, n1, S0, DS, qw, vv, dxdt, scale);
+    jadd<DET>(Jc + node[0] + jb0 * (node[1] + jb1 * node[2]), cq * fac, scale);
   }
+}
+
+// a general-case particle when the record queue is full: the same rows, in
+// place (so the sorted mode's sums do not depend on which particles overflow)
+template <int D, bool DET, typename JT>
+__device__ __noinline__ void deposit_in_place(JT *Jsm, const QIn &in, float scale) {
+  QRec R;
+  queue_record<D>(R, in);
+  constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
+  for (int b = 0; b < R.nb; ++b)
+    for (int it = 0; it < IPB; ++it) {
+      const int c = it < NR0 ? 0 : (it < NR0 + NR1 ? 1 : 2);
+      const int row = it - (c == 0 ? 0 : (c == 1 ? NR0 : NR0 + NR1));
+      queued_row<D, DET, JT>(Jsm, R, b, c, row, scale);
+    }
 }
 
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
-                              const float *Gsm, JT *Jsm, int *status, float scale, int *qbuf, int *qn, int qmax) {
+                              const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   int cell = P.cell[i];
@@ -506,28 +442,40 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       fast &= (d2[a] == d[a]) && (u2p == u1p) && (x2n >= -0.5f) && (x2n < 0.5f);
     }
   }
-  if (!fast && qbuf) {
-    int slot = atomicAdd(qn, 1);
-    if (slot < qmax) {
-      qbuf[slot] = (int)i;  // redone by the whole block after the main pass
-      return;
-    }
-  }
-  if (fast) {
-    float qw[2] = {sp.qw1, sp.qw2};
-    float vv[2][3];
-    float dd[2][3];
+  // a neutral ion whose bodies coincide and move together carries no
+  // current (its two bodies' terms cancel exactly; Sec. 2 starts every ion
+  // so, and it stays so until a field acts on it): nothing to deposit
+  bool silent = two && sp.qw1 == -sp.qw2;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vv[0][a] = v1[a];
-      vv[1][a] = v2[a];
-      dd[0][a] = de1[a];
-      dd[1][a] = de2[a];
+  for (int a = 0; a < 3; ++a) silent &= (r[a] == 0.0f) && (v1[a] == v2[a]);
+  if (!silent) {
+    if (fast) {
+      float qw[2] = {sp.qw1, sp.qw2};
+      float vv[2][3];
+      float dd[2][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vv[0][a] = v1[a];
+        vv[1][a] = v2[a];
+        dd[0][a] = de1[a];
+        dd[1][a] = de2[a];
+      }
+      if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+      else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+    } else {
+      QIn in;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        in.f[a] = f[a]; in.de1[a] = de1[a]; in.f2[a] = f2[a]; in.de2[a] = de2[a];
+        in.v1[a] = v1[a]; in.v2[a] = v2[a]; in.dxdt[a] = dxdt[a]; in.d[a] = d[a]; in.d2[a] = d2[a];
+      }
+      in.qw1 = sp.qw1;
+      in.qw2 = sp.qw2;
+      in.two = two;
+      const int slot = atomicAdd(qn, 1);
+      if (slot < qmax) queue_record<D>(qrec[slot], in);
+      else deposit_in_place<D, DET, JT>(Jsm, in, scale);
     }
-    if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
-    else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
-  } else {
-    general_deposit<D, DET, JT>(Jsm, g, f, de1, d, f2, de2, d2, two, sp.qw1, sp.qw2, v1, v2, scale);
   }
   // new cell of body 1.  On open axes a free particle whose cell leaves
   // [2, n-2) is removed (after its last deposit); a two-body ion leaving the
@@ -597,7 +545,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   tc[1] = (t / g.nt[0]) % g.nt[1];
   tc[2] = t / (g.nt[0] * g.nt[1]);
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  for (int q = tid; q < 3 * JC; q += bs) Jsm[q] = (JT)0;
+  for (int q = tid; q < 3 * JC; q += bs) Jsm[q] = DET ? (JT)JBIAS : (JT)0;
   // stage E, B of the tile plus halo (zero outside open faces)
   for (int q = tid; q < GC; q += bs) {
     int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
@@ -621,25 +569,31 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
   }
   __syncthreads();
-  constexpr int QMAX = 512;
-  __shared__ int qbuf[QMAX];
+  QRec *qrec = reinterpret_cast<QRec *>(smem + sizeof(JT) * 3 * (size_t)JC + sizeof(float) * 6 * (size_t)GC);
+  constexpr int QMAX = push_qmax(D);
+  constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
   __shared__ int qn;
   for (int s = 0; s < A.nsp; ++s) {
     if (tid == 0) qn = 0;
     __syncthreads();
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
     for (long long i = beg + tid; i < end; i += bs)
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qbuf, &qn, QMAX);
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX);
     __syncthreads();
-    // particles leaving their node: general five-node window, compacted
-    const int nq = min(qn, QMAX);
-    for (int k = tid; k < nq; k += bs)
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], qbuf[k], T0, Gsm, Jsm, A.status, A.jscale, nullptr, nullptr, 0);
+    // the deferred general deposits, one row per thread
+    const int nitem = min(qn, QMAX) * 2 * IPB;
+    for (int k = tid; k < nitem; k += bs) {
+      const int e = k / (2 * IPB), rem = k - e * (2 * IPB), b = rem / IPB, it = rem - b * IPB;
+      if (b >= qrec[e].nb) continue;
+      const int c = it < NR0 ? 0 : (it < NR0 + NR1 ? 1 : 2);
+      const int row = it - (c == 0 ? 0 : (c == 1 ? NR0 : NR0 + NR1));
+      queued_row<D, DET, JT>(Jsm, qrec[e], b, c, row, A.jscale);
+    }
     __syncthreads();
   }
   float *out = A.jbox + (size_t)t * 3 * JC;
   for (int q = tid; q < 3 * JC; q += bs) {
-    if constexpr (DET) out[q] = (float)((double)Jsm[q] * (double)A.jinv);
+    if constexpr (DET) out[q] = __ll2float_rn((long long)Jsm[q] - JBIAS) * A.jinv;  // jinv = 2^-k: one rounding
     else out[q] = Jsm[q];
   }
   if (tid == 0) A.occ[t] = 1;
@@ -665,7 +619,7 @@ size_t push_smem_bytes(const GridP &g, int det) {
   if (g.D == 1) { jc = Box<1>::JCELLS; gc = Box<1>::GCELLS; }
   if (g.D == 2) { jc = Box<2>::JCELLS; gc = Box<2>::GCELLS; }
   if (g.D == 3) { jc = Box<3>::JCELLS; gc = Box<3>::GCELLS; }
-  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc;
+  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc + sizeof(QRec) * (size_t)push_qmax(g.D);
 }
 
 int push_prepare(const GridP &g, int det) {
