@@ -51,6 +51,11 @@ template <>
 struct Geo<3> {
   static constexpr int L0 = 8, L1 = 8, L2 = 8, M = 1;
 };
+// bank-friendly plane stride: the smallest n' >= n with n' = 8 (mod 32)
+// words, so that a node's x-, y- and z-neighbours (offsets 1, row, plane)
+// fall in different shared-memory banks
+__host__ __device__ constexpr int pad_plane(int n) { return n + ((8 - n % 32) + 32) % 32; }
+
 template <int D>
 struct Box {
   static constexpr int M = Geo<D>::M;
@@ -59,7 +64,14 @@ struct Box {
   static constexpr int J0 = Geo<D>::L0 + 2 * M + 7, J1 = D >= 2 ? Geo<D>::L1 + 2 * M + 7 : 1,
                        J2 = D >= 3 ? Geo<D>::L2 + 2 * M + 7 : 1;
   static constexpr int OG = M + 2, OJ = M + 3;
-  static constexpr int GCELLS = G0 * G1 * G2, JCELLS = J0 * J1 * J2;
+  // shared-memory layout: x fastest, row stride G0 / J0, padded plane stride
+  static constexpr int GP = D >= 3 ? pad_plane(G0 * G1) : G0 * G1;
+  static constexpr int JP = D >= 3 ? pad_plane(J0 * J1) : J0 * J1;
+  static constexpr int GCELLS = GP * G2, JCELLS = JP * J2;
+  // global per-tile box layout (compact, x fastest)
+  static constexpr int GCOMP = G0 * G1 * G2, JCOMP = J0 * J1 * J2;
+  __host__ __device__ static constexpr int gi(int x, int y, int z) { return x + G0 * y + GP * z; }
+  __host__ __device__ static constexpr int ji(int x, int y, int z) { return x + J0 * y + JP * z; }
 };
 
 // particle cell index: the three cell coordinates packed in bit fields

@@ -38,7 +38,6 @@ __device__ __forceinline__ void make_loc(const int d[3], const float f[3], Loc &
 template <int D, int PAT>
 __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const Loc &A, const Loc &Bo, float &oa,
                                             float &ob) {
-  constexpr int gb0 = Box<D>::G0, gb1 = Box<D>::G1;
   int ba[3], bb[3];
   const float *wa[3];
   const float *wb[3];
@@ -59,7 +58,7 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
     for (int k = 0; k < NK; ++k)
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
-        const float *row = G + ba[0] + gb0 * ((ba[1] + j) + gb1 * (ba[2] + k));
+        const float *row = G + Box<D>::gi(ba[0], ba[1] + j, ba[2] + k);
         float ra = 0.0f, rb = 0.0f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -75,8 +74,8 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
     for (int k = 0; k < NK; ++k)
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
-        const float *ra_ = G + ba[0] + gb0 * ((ba[1] + j) + gb1 * (ba[2] + k));
-        const float *rb_ = G + bb[0] + gb0 * ((bb[1] + j) + gb1 * (bb[2] + k));
+        const float *ra_ = G + Box<D>::gi(ba[0], ba[1] + j, ba[2] + k);
+        const float *rb_ = G + Box<D>::gi(bb[0], bb[1] + j, bb[2] + k);
         float ra = 0.0f, rb = 0.0f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {

@@ -248,7 +248,6 @@ __device__ void boris_adj(float h, const float E[3], const float B[3], const flo
 template <int D, int PAT, int NB>
 __device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, float *Acc, const int (*d)[3],
                                                 const float (*f)[3], const float *e, float (*Xb)[3]) {
-  constexpr int gb0 = Box<D>::G0, gb1 = Box<D>::G1;
   int b[3];
   float w[NB][3][3], dw[NB][3][3];
 #pragma unroll
@@ -283,7 +282,7 @@ __device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, flo
     for (int j = 0; j < NJ; ++j)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const int idx = (b[0] + i) + gb0 * ((b[1] + j) + gb1 * (b[2] + k));
+        const int idx = Box<D>::gi(b[0] + i, b[1] + j, b[2] + k);
         const float g = G[idx];
         float acc = 0.0f;
 #pragma unroll
@@ -364,7 +363,7 @@ template <int D, int W, int NB>
 __device__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const float (*xi)[3],
                             const float (*de)[3], const float *qw, const float (*v)[3], const float dxdt[3],
                             float (*X0b)[3], float (*X1b)[3], float (*vb)[3]) {
-  constexpr int jc = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  constexpr int jc = Box<D>::JCELLS;
   constexpr int H = W / 2;  // window nodes n0 - H .. n0 + H
   float S0[NB][3][W], DS[NB][3][W], gS0[NB][3][W], gDS[NB][3][W];
 #pragma unroll
@@ -385,7 +384,7 @@ __device__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const
       }
   const int bx = n0[0] - H, by = D >= 2 ? n0[1] - H : 0, bz = D >= 3 ? n0[2] - H : 0;
   auto L = [&](int comp, int i, int j, int k) -> float {
-    return Jl[comp * jc + (bx + i) + jb0 * ((by + j) + jb1 * (bz + k))];
+    return Jl[comp * jc + Box<D>::ji(bx + i, by + j, bz + k)];
   };
   if constexpr (D == 1) {
     float suf = 0.0f;
@@ -743,8 +742,9 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
   }
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  for (int q = tid; q < GC; q += bs) {
+  for (int q = tid; q < BX::GCOMP; q += bs) {
     int bidx[3] = {q % BX::G0, (q / BX::G0) % BX::G1, q / (BX::G0 * BX::G1)};
+    const int si = BX::gi(bidx[0], bidx[1], bidx[2]);
     long long gi = 0, stride = 1;
     bool ok = true;
 #pragma unroll
@@ -759,14 +759,15 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      Gsm[cc * GC + q] = ok ? A.E[cc][gi] : 0.0f;
-      Gsm[(3 + cc) * GC + q] = ok ? A.B[cc][gi] : 0.0f;
+      Gsm[cc * GC + si] = ok ? A.E[cc][gi] : 0.0f;
+      Gsm[(3 + cc) * GC + si] = ok ? A.B[cc][gi] : 0.0f;
     }
 #pragma unroll
-    for (int cc = 0; cc < 6; ++cc) Acc[cc * GC + q] = 0.0f;
+    for (int cc = 0; cc < 6; ++cc) Acc[cc * GC + si] = 0.0f;
   }
-  for (int q = tid; q < JC; q += bs) {
+  for (int q = tid; q < BX::JCOMP; q += bs) {
     int bidx[3] = {q % BX::J0, (q / BX::J0) % BX::J1, q / (BX::J0 * BX::J1)};
+    const int si = BX::ji(bidx[0], bidx[1], bidx[2]);
     long long gi = 0, stride = 1;
     bool ok = true;
 #pragma unroll
@@ -780,7 +781,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
       stride *= g.n[a];
     }
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + q] = ok ? A.lamJ[cc][gi] : 0.0f;
+    for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + si] = ok ? A.lamJ[cc][gi] : 0.0f;
   }
   __syncthreads();
   for (int s = 0; s < A.nsp; ++s) {
@@ -788,8 +789,13 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
     for (long long i = beg + tid; i < end; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, Acc);
   }
   __syncthreads();
-  float *out = A.box + (size_t)t * 6 * GC;
-  for (int q = tid; q < 6 * GC; q += bs) out[q] = Acc[q];
+  // the box to global memory in the compact layout
+  constexpr int GN = BX::GCOMP;
+  float *out = A.box + (size_t)t * 6 * GN;
+  for (int q = tid; q < 6 * GN; q += bs) {
+    const int cc = q / GN, r = q - cc * GN;
+    out[q] = Acc[cc * GC + BX::gi(r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1))];
+  }
   if (tid == 0) A.occ[t] = 1;
 }
 

@@ -25,7 +25,7 @@ namespace {
 
 // capacity of the deferred-deposit records per tile (shared memory); a tile
 // with more general-case particles deposits the rest in place
-__host__ __device__ constexpr int push_qmax(int D) { return D == 3 ? 96 : (D == 2 ? 128 : 64); }
+__host__ __device__ constexpr int push_qmax(int D) { return D == 2 ? 128 : 64; }
 
 // float -> int64, rounded to nearest even, on the FP32 and integer pipes
 // (the 64-bit conversion runs on the slow FP64 unit).  Adding 1.5 * 2^23 to
@@ -43,44 +43,48 @@ __device__ __forceinline__ long long f2ll_rn(float x) {
 }
 
 // add v (already in fixed-point units in the sorted mode) to a current node.
-// Sorted mode: each 64-bit node word (biased by 2^31, see JBIAS) is updated
-// with the GPU's native 32-bit shared atomics: the low word takes the low 32
-// bits of the contribution and returns its old value, and the high word
-// takes the high 32 bits plus the carry out of the low word -- usually zero,
-// so usually one atomic.  The final word is the exact 64-bit sum whatever
-// the order.  (64-bit and FP32 shared atomic adds are compare-and-swap loops
-// on this GPU; 32-bit integer adds are single instructions.)
+// Sorted mode: a node's 64-bit fixed-point sum (biased by 2^31, see JBIAS) is
+// kept as a low word (unsigned) and a high word (signed) in two arrays, the
+// high words 3 * JCELLS entries after the low ones, and updated with the
+// GPU's native 32-bit shared atomics: the low word takes the low 32 bits of
+// the contribution and returns its old value, and the high word takes the
+// high 32 bits plus the carry out of the low word -- usually zero, so usually
+// one atomic.  The final pair is the exact 64-bit sum whatever the order.
+// (64-bit and FP32 shared atomic adds are compare-and-swap loops on this GPU;
+// 32-bit integer adds are single instructions.)
 // Atomic mode: FP32 shared atomics.  Zero contributions are skipped.
 constexpr long long JBIAS = 0x80000000LL;
 
-template <bool DET, typename JT>
+template <int D, bool DET, bool SKIP0 = true, typename JT>
 __device__ __forceinline__ void jput(JT *p, float v) {
   if constexpr (DET) {
-    if (fabsf(v) <= 0.5f) return;
+    if (SKIP0 && fabsf(v) <= 0.5f) return;
     unsigned int lo;
     int hi;
     if (fabsf(v) < 2147483648.0f) {
       const int q = __float2int_rn(v);
       lo = (unsigned int)q;
-      hi = q < 0 ? -1 : 0;
+      hi = q >> 31;
     } else {
       const long long q = f2ll_rn(v);
       lo = (unsigned int)(unsigned long long)q;
       hi = (int)(q >> 32);
     }
-    unsigned int *w = reinterpret_cast<unsigned int *>(p);
-    const unsigned int old = atomicAdd(w, lo);
-    hi += (old + lo < old) ? 1 : 0;
-    if (hi) atomicAdd(reinterpret_cast<int *>(w + 1), hi);
+    const unsigned int old = atomicAdd(p, lo);
+    // hi + carry out of old + lo
+    unsigned int sum;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=r"(sum), "+r"(hi) : "r"(old), "r"(lo));
+    (void)sum;
+    if (hi) atomicAdd(reinterpret_cast<int *>(p + 3 * Box<D>::JCELLS), hi);
   } else {
-    if (v == 0.0f) return;
+    if (SKIP0 && v == 0.0f) return;
     atomicAdd(p, v);
   }
 }
 
-template <bool DET, typename JT>
+template <int D, bool DET, typename JT>
 __device__ __forceinline__ void jadd(JT *p, float v, float scale) {
-  jput<DET>(p, DET ? v * scale : v);
+  jput<D, DET>(p, DET ? v * scale : v);
 }
 
 // Fast path: all four positions (both bodies, before and after the move)
@@ -99,7 +103,7 @@ template <int D, bool DET, int NB, typename JT>
 __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], const float (*xi)[3],
                                            const float (*de)[3], const float *qw, const float (*v)[3],
                                            const float dxdt[3], float scale) {
-  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  constexpr int jcells = Box<D>::JCELLS;
   constexpr float K12 = 1.0f / 12.0f;
   const float sc = DET ? scale : 1.0f;
   float A[NB][3][3], DS[NB][3][3], DK[NB][3][3], cP[NB][3][2];
@@ -141,7 +145,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
     for (int f = 0; f < 2; ++f) {
       float jx = cP[0][0][f];
       if constexpr (NB == 2) jx = __fadd_rn(jx, cP[1][0][f]);
-      jput<DET>(Jx + bx + f, jx);
+      jput<D, DET, false>(Jx + bx + f, jx);
     }
     float qy[NB], qz[NB];
 #pragma unroll
@@ -156,8 +160,8 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         jy = __fadd_rn(jy, __fmul_rn(qy[1], A[1][0][i]));
         jz = __fadd_rn(jz, __fmul_rn(qz[1], A[1][0][i]));
       }
-      jput<DET>(Jy + bx + i, jy);
-      jput<DET>(Jz + bx + i, jz);
+      jput<D, DET, false>(Jy + bx + i, jy);
+      jput<D, DET, false>(Jz + bx + i, jz);
     }
   } else if constexpr (D == 2) {
 #pragma unroll
@@ -166,7 +170,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
       for (int f = 0; f < 2; ++f) {
         float jx = __fmul_rn(cP[0][0][f], A[0][1][j]);
         if constexpr (NB == 2) jx = __fadd_rn(jx, __fmul_rn(cP[1][0][f], A[1][1][j]));
-        jput<DET>(Jx + (bx + f) + jb0 * (by + j), jx);
+        jput<D, DET, false>(Jx + Box<D>::ji(bx + f, by + j, 0), jx);
       }
 #pragma unroll
     for (int g = 0; g < 2; ++g)
@@ -174,7 +178,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
       for (int i = 0; i < 3; ++i) {
         float jy = __fmul_rn(cP[0][1][g], A[0][0][i]);
         if constexpr (NB == 2) jy = __fadd_rn(jy, __fmul_rn(cP[1][1][g], A[1][0][i]));
-        jput<DET>(Jy + (bx + i) + jb0 * (by + g), jy);
+        jput<D, DET, false>(Jy + Box<D>::ji(bx + i, by + g, 0), jy);
       }
     float qz[NB];
 #pragma unroll
@@ -186,7 +190,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         float jz = __fmul_rn(qz[0], fmaf(A[0][0][i], A[0][1][j], DK[0][0][i] * DS[0][1][j]));
         if constexpr (NB == 2)
           jz = __fadd_rn(jz, __fmul_rn(qz[1], fmaf(A[1][0][i], A[1][1][j], DK[1][0][i] * DS[1][1][j])));
-        jput<DET>(Jz + (bx + i) + jb0 * (by + j), jz);
+        jput<D, DET, false>(Jz + Box<D>::ji(bx + i, by + j, 0), jz);
       }
   } else {
 #pragma unroll
@@ -200,7 +204,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         for (int f = 0; f < 2; ++f) {
           float jx = __fmul_rn(cP[0][0][f], F[0]);
           if constexpr (NB == 2) jx = __fadd_rn(jx, __fmul_rn(cP[1][0][f], F[1]));
-          jput<DET>(Jx + (bx + f) + jb0 * ((by + j) + jb1 * (bz + k)), jx);
+          jput<D, DET, false>(Jx + Box<D>::ji(bx + f, by + j, bz + k), jx);
         }
       }
 #pragma unroll
@@ -214,7 +218,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         for (int g = 0; g < 2; ++g) {
           float jy = __fmul_rn(cP[0][1][g], F[0]);
           if constexpr (NB == 2) jy = __fadd_rn(jy, __fmul_rn(cP[1][1][g], F[1]));
-          jput<DET>(Jy + (bx + i) + jb0 * ((by + g) + jb1 * (bz + k)), jy);
+          jput<D, DET, false>(Jy + Box<D>::ji(bx + i, by + g, bz + k), jy);
         }
       }
 #pragma unroll
@@ -228,7 +232,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         for (int h = 0; h < 2; ++h) {
           float jz = __fmul_rn(cP[0][2][h], F[0]);
           if constexpr (NB == 2) jz = __fadd_rn(jz, __fmul_rn(cP[1][2][h], F[1]));
-          jput<DET>(Jz + (bx + i) + jb0 * ((by + j) + jb1 * (bz + h)), jz);
+          jput<D, DET, false>(Jz + Box<D>::ji(bx + i, by + j, bz + h), jz);
         }
       }
   }
@@ -288,7 +292,7 @@ __host__ __device__ constexpr int qrows(int c) {
 
 template <int D, bool DET, typename JT>
 __device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, int row, float scale) {
-  constexpr int jcells = Box<D>::JCELLS, jb0 = Box<D>::J0, jb1 = Box<D>::J1;
+  constexpr int jcells = Box<D>::JCELLS;
   const int p = c == 0 ? 1 : 0, q = c == 2 ? 1 : 2;  // the other two axes, p < q
   const int ip = p < D ? row % 5 : 2, iq = q < D ? row / 5 : 2;
   const float sp = R.S0[b][p][ip], dp = R.DS[b][p][ip], sq = R.S0[b][q][iq], dq = R.DS[b][q][iq];
@@ -303,16 +307,16 @@ __device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, i
   JT *Jc = J + c * jcells;
   if (c < D) {
     const int b0 = R.n0[b][c] - 2;
-    const int stride = c == 0 ? 1 : (c == 1 ? jb0 : jb0 * jb1);
-    const int lin0 = (c == 0 ? 0 : node[0]) + jb0 * ((c == 1 ? 0 : node[1]) + jb1 * (c == 2 ? 0 : node[2]));
+    const int stride = c == 0 ? 1 : (c == 1 ? Box<D>::J0 : Box<D>::JP);
+    const int lin0 = Box<D>::ji(c == 0 ? 0 : node[0], c == 1 ? 0 : node[1], c == 2 ? 0 : node[2]);
     float run = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       run += R.DS[b][c][i];
-      jadd<DET>(Jc + lin0 + (b0 + i) * stride, cq * run * fac, scale);
+      jadd<D, DET>(Jc + lin0 + (b0 + i) * stride, cq * run * fac, scale);
     }
   } else {
-    jadd<DET>(Jc + node[0] + jb0 * (node[1] + jb1 * node[2]), cq * fac, scale);
+    jadd<D, DET>(Jc + Box<D>::ji(node[0], node[1], node[2]), cq * fac, scale);
   }
 }
 
@@ -526,12 +530,13 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
 
 template <int D, bool DET>
 __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A) {
-  using JT = typename std::conditional<DET, long long, float>::type;
+  using JT = typename std::conditional<DET, unsigned int, float>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   using BX = Box<D>;
   constexpr int JC = BX::JCELLS, GC = BX::GCELLS;
+  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * JC;  // low (and high) words
   JT *Jsm = reinterpret_cast<JT *>(smem);
-  float *Gsm = reinterpret_cast<float *>(smem + sizeof(JT) * 3 * (size_t)JC);
+  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
   const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
   int total = 0;
@@ -545,11 +550,15 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   tc[1] = (t / g.nt[0]) % g.nt[1];
   tc[2] = t / (g.nt[0] * g.nt[1]);
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  for (int q = tid; q < 3 * JC; q += bs) Jsm[q] = DET ? (JT)JBIAS : (JT)0;
+  for (int q = tid; q < 3 * JC; q += bs) {
+    Jsm[q] = DET ? (JT)JBIAS : (JT)0;
+    if constexpr (DET) Jsm[3 * JC + q] = 0;
+  }
   // stage E, B of the tile plus halo (zero outside open faces)
-  for (int q = tid; q < GC; q += bs) {
+  for (int q = tid; q < BX::GCOMP; q += bs) {
     int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     int bidx[3] = {b0, b1, b2};
+    const int si = BX::gi(b0, b1, b2);
     long long gi = 0, stride = 1;
     bool ok = true;
 #pragma unroll
@@ -564,12 +573,12 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      Gsm[cc * GC + q] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
-      Gsm[(3 + cc) * GC + q] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
+      Gsm[cc * GC + si] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
+      Gsm[(3 + cc) * GC + si] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
     }
   }
   __syncthreads();
-  QRec *qrec = reinterpret_cast<QRec *>(smem + sizeof(JT) * 3 * (size_t)JC + sizeof(float) * 6 * (size_t)GC);
+  QRec *qrec = reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
   constexpr int QMAX = push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
   __shared__ int qn;
@@ -591,10 +600,18 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
     __syncthreads();
   }
-  float *out = A.jbox + (size_t)t * 3 * JC;
-  for (int q = tid; q < 3 * JC; q += bs) {
-    if constexpr (DET) out[q] = __ll2float_rn((long long)Jsm[q] - JBIAS) * A.jinv;  // jinv = 2^-k: one rounding
-    else out[q] = Jsm[q];
+  // the box to global memory in the compact layout
+  constexpr int JN = BX::JCOMP;
+  float *out = A.jbox + (size_t)t * 3 * JN;
+  for (int q = tid; q < 3 * JN; q += bs) {
+    const int cc = q / JN, r = q - cc * JN;
+    const int k = cc * JC + BX::ji(r % BX::J0, (r / BX::J0) % BX::J1, r / (BX::J0 * BX::J1));
+    if constexpr (DET) {
+      const long long w = (long long)(((unsigned long long)Jsm[3 * JC + k] << 32) | Jsm[k]) - JBIAS;
+      out[q] = __ll2float_rn(w) * A.jinv;  // jinv = 2^-k: one rounding
+    } else {
+      out[q] = Jsm[k];
+    }
   }
   if (tid == 0) A.occ[t] = 1;
 }
