@@ -91,6 +91,7 @@ void update_jscale(bp_ctx *c) {
 }
 
 int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
+  c->sort_dirty = true;
   const int D = c->g.D;
   const bool two = s.sp.kind == BP_TWO_BODY;
   long long cap = std::max(1LL, n);
@@ -122,6 +123,7 @@ int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
     return fail(c, BP_ERR_OOM, "particle arrays (%lld particles)", n);
   // sort scratch, shared by all species
   const int nf = D + (two ? 9 : 3);
+  c->sort_dirty = true;
   if (!c->sb.hist) {
     c->sb.hist = (int *)dalloc(c, sizeof(int) * (c->g.ncell + 1));
     c->sb.bsum = (int *)dalloc(c, sizeof(int) * (sort_scan_blocks(c->g) + 4));
@@ -277,6 +279,9 @@ void bp_destroy(bp_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (auto e : c->ev) cudaEventDestroy(e);
+  if (c->sort_exec) cudaGraphExecDestroy(c->sort_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->sort_runs) cudaFreeHost(c->sort_runs);
   std::vector<void *> all = c->owned;
   for (void *p : all) dfree(c, p);
   delete c;
@@ -523,6 +528,50 @@ void copy_parts(bp_ctx *c, const PartP &src, PartP &dst, int D, bool two) {
 
 // one leapfrog step; when snap_fields is given, E^n and B^n (after the first
 // half step) and the particle state before the push are copied there
+// the re-sort graph of the current particle arrays (built on first use and
+// after any reallocation); false if the CUDA runtime cannot build it, in
+// which case the step launches the sort pipeline directly
+bool sort_graph(bp_ctx *c) {
+  if (c->sort_exec && !c->sort_dirty) return true;
+  if (c->sort_exec) {
+    cudaGraphExecDestroy(c->sort_exec);
+    c->sort_exec = nullptr;
+  }
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_stream = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  if (!c->sort_runs) {
+    if (cudaHostAlloc((void **)&c->sort_runs, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->sort_runs_dev, c->sort_runs, 0) != cudaSuccess) {
+      if (c->sort_runs) cudaFreeHost(c->sort_runs);
+      c->sort_runs = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    *c->sort_runs = 0;
+  }
+  SpecP sp[BP_MAX_SPECIES];
+  PartP pp[BP_MAX_SPECIES];
+  int n = 0;
+  for (auto &s : c->sp)
+    if (s.loaded && n < BP_MAX_SPECIES) {
+      sp[n] = s.sp;
+      pp[n] = s.p;
+      ++n;
+    }
+  cudaGraphExec_t ex = nullptr;
+  if (make_sort_graph(c->g, n, sp, pp, c->sb, c->status, c->sort_runs_dev, c->cap_stream, &ex) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->sort_exec = ex;
+  c->sort_nsp = n;
+  c->sort_dirty = false;
+  return true;
+}
+
 int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fields,
              std::vector<bp_part_copy> *snap_parts) {
   const GridP &g = c->g;
@@ -533,10 +582,15 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
   for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
   // re-sort when a particle left its tile margin in the previous step
   if (nsp) {
-    for (auto &s : c->sp)
-      if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
-    launch_clear_sort_flag(c->status, st);
-    c->launches += nsp * sort_launches() + 1;
+    if (sort_graph(c)) {
+      cudaGraphLaunch(c->sort_exec, st);
+      c->launches += 1;  // the condition kernel; a re-sort that ran is counted by bp_kernel_launches
+    } else {
+      for (auto &s : c->sp)
+        if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
+      launch_clear_sort_flag(c->status, st);
+      c->launches += nsp * sort_launches() + 1;
+    }
   }
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
   if (snap_fields) {
@@ -721,7 +775,12 @@ int bp_residual(bp_ctx *c, double *dst, int on_device) {
   return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "residual");
 }
 
-int64_t bp_kernel_launches(const bp_ctx *c) { return c ? c->launches : 0; }
+int64_t bp_kernel_launches(const bp_ctx *c) {
+  if (!c) return 0;
+  // re-sorts run inside the step graph are counted on the device
+  const long long runs = c->sort_runs ? *(volatile int *)c->sort_runs : 0;
+  return c->launches + runs * ((long long)c->sort_nsp * sort_launches() + 1);
+}
 
 int bp_time_push(bp_ctx *c, int enable) {
   if (!c) return BP_ERR_ARG;

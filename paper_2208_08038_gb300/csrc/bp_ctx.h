@@ -77,4 +77,12 @@ struct bp_ctx {
   std::string err;
   float jscale = 0.0f, jinv = 0.0f;
   bp_adjoint adj;
+  // per-step re-sort as a conditional graph (rebuilt when a particle array,
+  // the sort scratch or the set of loaded species changes)
+  cudaGraphExec_t sort_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool sort_dirty = true;
+  int *sort_runs = nullptr;      // host-mapped counter of re-sorts that ran
+  int *sort_runs_dev = nullptr;
+  int sort_nsp = 0;              // species in the graph's sort pipeline
 };

@@ -133,6 +133,9 @@ __host__ __device__ __forceinline__ int wrap_mod(int i, int n) {
   int m = i % n;
   return m < 0 ? m + n : m;
 }
+// periodic wrap of an index known to lie in [-n, 2n) (a staged box or a
+// one-cell move on a grid of at least one tile): no integer division
+__host__ __device__ __forceinline__ int wrap_once(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // quadratic B-spline weights for the three nodes around the nearest node,
 // xi = position - nearest node in [-1/2, 1/2)
@@ -209,6 +212,8 @@ struct SortBufs {
 void launch_sort(const GridP &g, const SpecP &sp, PartP &p, SortBufs &b, int *status, cudaStream_t s);
 void launch_clear_sort_flag(int *status, cudaStream_t s);
 void launch_set_sort_flag(int *status, cudaStream_t s);
+cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, SortBufs &b, int *status, int *runs,
+                            cudaStream_t cap, cudaGraphExec_t *out);
 
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
                        uint64_t seed, double sigma, long long first, long long count, cudaStream_t s);

@@ -146,6 +146,13 @@ __device__ __forceinline__ void window(const float f[3], const float de[3], floa
   }
 }
 
+// particle of a tile handled by thread tid in the chunk starting at k0: the
+// lanes of a warp take particles bs/32 apart (bs = block size, a multiple of
+// 32), so that in cell-sorted order they sit in different cells and rarely
+// add to the same shared-memory node at once; the chunk [k0, k0 + bs) is
+// still covered exactly once
+__device__ __forceinline__ int spread_index(int k0, int tid, int bs) { return k0 + (tid & 31) * (bs >> 5) + (tid >> 5); }
+
 // tile-relative cell of a global cell coordinate (periodic: nearest image)
 template <int D>
 __device__ __forceinline__ int rel_cell(const GridP &g, int a, int c, int T0) {

@@ -61,7 +61,7 @@ __device__ __forceinline__ float gint(const GridP &g, const float *G, int comp, 
   int x[3] = {c[0], c[1], c[2]};
   if (o) {
     x[a] += o;
-    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_mod(x[a], g.n[a]);
+    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
     if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
   }
   if (!e_interior(g, comp, x)) return 0.0f;
@@ -73,7 +73,7 @@ __device__ __forceinline__ float bnx(const GridP &g, const float *Bb, int comp, 
   int x[3] = {c[0], c[1], c[2]};
   if (o) {
     x[a] += o;
-    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_mod(x[a], g.n[a]);
+    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
     if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
   }
   if (ext(g, pat[comp], x)) return 0.0f;
@@ -192,7 +192,7 @@ __device__ __forceinline__ float dqshape(float x) {
 
 // reverse of boris(): given the adjoint of the pushed momentum, the adjoints
 // of the old momentum, E and B
-__device__ void boris_adj(float h, const float E[3], const float B[3], const float u0[3], const float ubn[3],
+__device__ __forceinline__ void boris_adj(float h, const float E[3], const float B[3], const float u0[3], const float ubn[3],
                           float ub0[3], float Eb[3], float Bb[3]) {
   float um[3], t[3], sv[3], c1[3];
 #pragma unroll
@@ -313,7 +313,8 @@ template <int D, int PAT>
 __device__ __forceinline__ void gather_adj_pair(const float *G, float *Acc, const int d1[3], const float f1[3],
                                                 float e1, float X1[3], const int d2[3], const float f2[3], float e2,
                                                 float X2[3], bool two) {
-  if (two && same_base<D, PAT>(d1, f1, d2, f2)) {
+  // warp-uniform choice (both forms give the same sums)
+  if (__all_sync(__activemask(), two && same_base<D, PAT>(d1, f1, d2, f2))) {
     int dd[2][3] = {{d1[0], d1[1], d1[2]}, {d2[0], d2[1], d2[2]}};
     float ff[2][3] = {{f1[0], f1[1], f1[2]}, {f2[0], f2[1], f2[2]}};
     float ee[2] = {e1, e2};
@@ -360,7 +361,7 @@ __device__ __forceinline__ void gather_adj_all(const float *G, float *Acc, const
 // m) - S(xi - m) on the window; then X0b = sum (gS0 - gDS) S'(xi - m),
 // X1b = sum gDS S'(xi + de - m).
 template <int D, int W, int NB>
-__device__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const float (*xi)[3],
+__device__ __forceinline__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const float (*xi)[3],
                             const float (*de)[3], const float *qw, const float (*v)[3], const float dxdt[3],
                             float (*X0b)[3], float (*X1b)[3], float (*vb)[3]) {
   constexpr int jc = Box<D>::JCELLS;
@@ -512,16 +513,19 @@ __device__ void deposit_adj(const float *__restrict__ Jl, const int n0[3], const
     }
 }
 
-// the rare case out of line (keeps the fast path's registers)
+// the rare case out of line, its inputs and results in one object built
+// inside the rare branch (the fast path's arrays stay in registers)
+struct AdjGen {
+  int nn[3], n2[3];
+  float xi[2][3], dd[2][3], qw[2], vv[2][3], dxdt[3];
+  float X0[2][3], X1[2][3], vb[2][3];
+  int two;
+};
+
 template <int D>
-__device__ __noinline__ void deposit_adj_general(const float *Jl, const int *nn, const int *n2, const float (*xi)[3],
-                                                 const float (*dd)[3], const float *qw, const float (*vv)[3],
-                                                 const float *dxdt, float (*X0)[3], float (*X1)[3], float (*vb)[3],
-                                                 bool two) {
-  int a1[3] = {nn[0], nn[1], nn[2]}, a2[3] = {n2[0], n2[1], n2[2]};
-  float dx3[3] = {dxdt[0], dxdt[1], dxdt[2]};
-  deposit_adj<D, 5, 1>(Jl, a1, xi, dd, qw, vv, dx3, X0, X1, vb);
-  if (two) deposit_adj<D, 5, 1>(Jl, a2, xi + 1, dd + 1, qw + 1, vv + 1, dx3, X0 + 1, X1 + 1, vb + 1);
+__device__ __noinline__ void deposit_adj_general(const float *Jl, AdjGen &A) {
+  deposit_adj<D, 5, 1>(Jl, A.nn, A.xi, A.dd, A.qw, A.vv, A.dxdt, A.X0, A.X1, A.vb);
+  if (A.two) deposit_adj<D, 5, 1>(Jl, A.n2, A.xi + 1, A.dd + 1, A.qw + 1, A.vv + 1, A.dxdt, A.X0 + 1, A.X1 + 1, A.vb + 1);
 }
 
 struct AdjState {
@@ -649,7 +653,26 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
     } else if (fast) {
       deposit_adj<D, 3, 1>(Jl, nn, xi, dd, qw, vv, dxdt, X0, X1, vb);
     } else {
-      deposit_adj_general<D>(Jl, nn, n2, xi, dd, qw, vv, dxdt, X0, X1, vb, two);
+      AdjGen G;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        G.nn[a] = nn[a]; G.n2[a] = n2[a]; G.dxdt[a] = dxdt[a];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          G.xi[q][a] = xi[q][a]; G.dd[q][a] = dd[q][a]; G.vv[q][a] = vv[q][a];
+          G.X0[q][a] = G.X1[q][a] = G.vb[q][a] = 0.0f;
+        }
+      }
+      G.qw[0] = qw[0];
+      G.qw[1] = qw[1];
+      G.two = two;
+      deposit_adj_general<D>(Jl, G);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          X0[q][a] = G.X0[q][a]; X1[q][a] = G.X1[q][a]; vb[q][a] = G.vb[q][a];
+        }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -751,7 +774,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
     for (int a = 0; a < 3; ++a) {
       int x = T0[a] - (a < D ? BX::OG : 0) + bidx[a];
       if (a < D) {
-        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        if (g.bc[a] == BP_PERIODIC) x = wrap_once(x, g.n[a]);
         else ok &= (x >= 0 && x < g.n[a]);
       }
       gi += (long long)x * stride;
@@ -774,7 +797,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
     for (int a = 0; a < 3; ++a) {
       int x = T0[a] - (a < D ? BX::OJ : 0) + bidx[a];
       if (a < D) {
-        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        if (g.bc[a] == BP_PERIODIC) x = wrap_once(x, g.n[a]);
         else ok &= (x >= 0 && x < g.n[a]);
       }
       gi += (long long)x * stride;
@@ -786,7 +809,10 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
   __syncthreads();
   for (int s = 0; s < A.nsp; ++s) {
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
-    for (long long i = beg + tid; i < end; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, Acc);
+    for (int k0 = 0; k0 < end - beg; k0 += bs) {
+      const int j = spread_index(k0, tid, bs);
+      if (j < end - beg) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], beg + j, T0, Gsm, Jl, Acc);
+    }
   }
   __syncthreads();
   // the box to global memory in the compact layout
@@ -824,7 +850,7 @@ __global__ void k_adj_boxsum(GridP g, const float *box, const unsigned char *occ
         int l = c[a] - (tu * g.L[a] - g.og[a]);
         if (l < 0 || l >= g.gb[a]) continue;
         int tt = tu;
-        if (g.bc[a] == BP_PERIODIC) tt = wrap_mod(tu, g.nt[a]);
+        if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
         else if (tu < 0 || tu >= g.nt[a]) continue;
         tw[a][nc[a]] = tt;
         loc[a][nc[a]] = l;

@@ -19,7 +19,7 @@ __device__ __forceinline__ void cell_coords(const GridP &g, long long q, int c[3
 __device__ __forceinline__ long long nb(const GridP &g, const int c[3], int a, int o) {
   int x[3] = {c[0], c[1], c[2]};
   x[a] += o;
-  if (g.bc[a] == BP_PERIODIC) x[a] = wrap_mod(x[a], g.n[a]);
+  if (g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
   return x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2]);
 }
 
@@ -239,7 +239,7 @@ __global__ void k_jsum(GridP g, const float *__restrict__ jbox, const unsigned c
         int l = c[a] - (tu * g.L[a] - g.oj[a]);
         if (l < 0 || l >= g.jb[a]) continue;
         int tt = tu;
-        if (g.bc[a] == BP_PERIODIC) tt = wrap_mod(tu, g.nt[a]);
+        if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
         else if (tu < 0 || tu >= g.nt[a]) continue;
         tw[a][nc[a]] = tt;
         loc[a][nc[a]] = l;

@@ -496,7 +496,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       if (fn[a] >= 1.0f) { fn[a] = 0.0f; c[a] += 1; }
     }
     if (g.bc[a] == BP_PERIODIC) {
-      c[a] = wrap_mod(c[a], g.n[a]);
+      c[a] = wrap_once(c[a], g.n[a]);
     } else if (two) {
       bad |= (c[a] < 0 || c[a] >= g.n[a]);
     } else {
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     for (int a = 0; a < 3; ++a) {
       int x = T0[a] - (a < D ? BX::OG : 0) + bidx[a];
       if (a < D) {
-        if (g.bc[a] == BP_PERIODIC) x = wrap_mod(x, g.n[a]);
+        if (g.bc[a] == BP_PERIODIC) x = wrap_once(x, g.n[a]);
         else ok &= (x >= 0 && x < g.n[a]);
       }
       gi += (long long)x * stride;
@@ -586,6 +586,8 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     if (tid == 0) qn = 0;
     __syncthreads();
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    // consecutive lanes take consecutive (cell-sorted) particles: their
+    // gather loads share addresses and their state loads coalesce
     for (long long i = beg + tid; i < end; i += bs)
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX);
     __syncthreads();

@@ -175,6 +175,14 @@ __global__ void k_copyback(GridP g, PartP p, const int *tcell, const float *tf, 
 __global__ void k_clear_flag(int *status) { atomicAnd(status, ~ST_NEED_SORT); }
 __global__ void k_set_flag(int *status) { atomicOr(status, ST_NEED_SORT); }
 
+// condition of the re-sort graph: non-zero when a particle left its tile's
+// margin in the previous step; counts the sorts that run
+__global__ void k_sort_cond(cudaGraphConditionalHandle h, const int *status, int *runs) {
+  const bool need = (*(volatile const int *)status) & ST_NEED_SORT;
+  if (need) ++*runs;
+  cudaGraphSetConditional(h, need ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // device medium: ion g = cell rank * ppc + p over the cell box [lo, hi);
 // position x_a = (c_a + U(3g + a)) dx_a, momentum sigma N(3g + a); the
@@ -394,6 +402,56 @@ int sort_scan_blocks(const GridP &g) { return (int)((g.ncell + 1 + SCAN_TILE - 1
 int sort_launches() { return 9; }
 
 void launch_clear_sort_flag(int *status, cudaStream_t s) { k_clear_flag<<<1, 1, 0, s>>>(status); }
+
+// The per-step re-sort as one graph: a one-thread kernel reads the status
+// word and sets the condition of an IF node whose body is the sort pipeline
+// of every species followed by the flag reset.  A step in which no particle
+// left its tile's margin then costs that one kernel instead of the pipeline's
+// nine launches per species.  Captured on the private stream cap (the
+// caller's stream may be one that cannot capture); the executable graph is
+// launched on any stream of the context.  Valid while the particle arrays,
+// the sort scratch and the status word keep their addresses.
+cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, SortBufs &b, int *status, int *runs,
+                            cudaStream_t cap, cudaGraphExec_t *out) {
+  *out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t ncond = nullptr, nif = nullptr;
+  e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    const int *cs = status;
+    void *args[3] = {&h, (void *)&cs, &runs};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)k_sort_cond;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&ncond, graph, nullptr, 0, &kp);
+  }
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&nif, graph, &ncond, nullptr, 1, &np);
+    if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    for (int q = 0; q < nsp; ++q) launch_sort(g, sp[q], p[q], b, status, cap);
+    launch_clear_sort_flag(status, cap);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cap, &captured);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
+}
 void launch_set_sort_flag(int *status, cudaStream_t s) { k_set_flag<<<1, 1, 0, s>>>(status); }
 
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
