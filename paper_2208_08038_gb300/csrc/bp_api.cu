@@ -256,10 +256,11 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   }
   c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
+  c->jbb = (uint2 *)dalloc(c, sizeof(uint2) * g.ntiles);
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!c->jbox || !c->occ || !c->status || (nf && !c->frame)) {
+  if (!c->jbox || !c->occ || !c->jbb || !c->status || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
@@ -486,6 +487,7 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   }
   A.jbox = c->jbox;
   A.occ = c->occ;
+  A.jbb = c->jbb;
   A.status = c->status;
   A.jscale = c->jscale;
   A.jinv = c->jinv;
@@ -615,7 +617,7 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
     cudaEventRecord(c->ev[c->ev_used + 1], st);
     c->ev_used += 2;
   }
-  launch_jsum(g, c->jbox, c->occ, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
+  launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
   launch_yee_e(g, E, cB, cJ, c->frame, st);
   c->launches += 5 + (nopen ? 1 + nopen : 0);

@@ -58,6 +58,7 @@ struct bp_ctx {
   float *F[9] = {};
   float *jbox = nullptr;
   unsigned char *occ = nullptr;
+  uint2 *jbb = nullptr;
   float *frame = nullptr;
   int *status = nullptr;
   std::vector<bp_species_state> sp;

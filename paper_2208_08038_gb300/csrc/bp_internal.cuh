@@ -114,7 +114,8 @@ struct PushArgs {
   const float *E[3];
   const float *B[3];
   float *jbox;             // [ntiles][3][jcells]
-  unsigned char *occ;      // [ntiles]
+  unsigned char *occ;      // [ntiles] the tile's box holds a deposit
+  uint2 *jbb;              // [ntiles] its bounding box: lowest / highest node, one byte per axis
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
 };
@@ -197,7 +198,7 @@ void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], fl
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3],
                   float *frame, cudaStream_t s);
 long long frame_floats(const GridP &g);
-void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, float *const J[3],
+void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
                  const LaserP *las, int nlas, double t, cudaStream_t s);
 void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,
                   cudaStream_t s);

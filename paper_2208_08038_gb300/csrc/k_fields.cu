@@ -7,22 +7,6 @@
 
 namespace {
 
-__device__ __forceinline__ void cell_coords(const GridP &g, long long q, int c[3]) {
-  c[0] = (int)(q % g.n[0]);
-  long long r = q / g.n[0];
-  c[1] = (int)(r % g.n[1]);
-  c[2] = (int)(r / g.n[1]);
-}
-
-// linear index of the neighbour of c offset by o along axis a (periodic wrap;
-// callers only step off an open axis where the rules below forbid it)
-__device__ __forceinline__ long long nb(const GridP &g, const int c[3], int a, int o) {
-  int x[3] = {c[0], c[1], c[2]};
-  x[a] += o;
-  if (g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
-  return x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2]);
-}
-
 // along an open axis a component with half stagger has no value at n-1
 // (exterior), one with node stagger has Mur boundary nodes at 0 and n-1
 __device__ __forceinline__ bool exterior(const GridP &g, int pat, const int c[3]) {
@@ -47,58 +31,106 @@ __device__ __forceinline__ int nbound(const GridP &g, int pat, const int c[3], i
 // stagger pattern of E_x, E_y, E_z (bit a: half cell along axis a)
 __device__ __forceinline__ int pat_e(int comp) { return 1 << comp; }
 
+// One thread per cell; a block covers a chunk of one x row (row = y + n1 z),
+// so coordinates come from one division per block and the neighbours are
+// fixed offsets (+-1, +-n0, +-n0 n1) with the periodic wrap applied once.
+struct Cell {
+  long long q;      // linear index
+  int c[3];         // coordinates
+  long long up[3];  // offset to the +1 neighbour along each axis (periodic wrap)
+  long long dn[3];  // offset to the -1 neighbour
+};
+
+template <int D>
+__device__ __forceinline__ bool row_cell(const GridP &g, Cell &C) {
+  const int n0 = g.n[0];
+  const int chunks = (n0 + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int row = (int)blockIdx.x / chunks;
+  const int x = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
+  if (x >= n0) return false;
+  C.c[0] = x;
+  C.c[1] = D >= 2 ? row % g.n[1] : 0;
+  C.c[2] = D >= 3 ? row / g.n[1] : 0;
+  C.q = (long long)row * n0 + x;
+  long long stride = 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int n = g.n[a];
+    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
+    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
+    stride *= n;
+  }
+  return true;
+}
+
+// along an open axis a component with half stagger has no value at n-1
+// (exterior), one with node stagger has Mur boundary nodes at 0 and n-1
+template <int D>
+__device__ __forceinline__ bool exterior_c(const GridP &g, int pat, const int c[3]) {
+  bool e = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if (g.bc[a] == BP_OPEN && ((pat >> a) & 1)) e |= c[a] == g.n[a] - 1;
+  return e;
+}
+template <int D>
+__device__ __forceinline__ bool mur_node(const GridP &g, int pat, const int c[3]) {
+  bool m = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if (g.bc[a] == BP_OPEN && !((pat >> a) & 1)) m |= c[a] == 0 || c[a] == g.n[a] - 1;
+  return m;
+}
+
 // B <- B - h curl E (forward differences to the B locations)
-__global__ void k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
-                        const float *__restrict__ Ey, const float *__restrict__ Ez, float h) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    cell_coords(g, q, c);
-    const bool y = g.D >= 2, z = g.D >= 3;
-    if (!exterior(g, 6, c)) {
-      float d = 0.0f;
-      if (y) d += (Ez[nb(g, c, 1, 1)] - Ez[q]) * g.idx[1];
-      if (z) d -= (Ey[nb(g, c, 2, 1)] - Ey[q]) * g.idx[2];
-      Bx[q] -= h * d;
-    }
-    if (!exterior(g, 5, c)) {
-      float d = -(Ez[nb(g, c, 0, 1)] - Ez[q]) * g.idx[0];
-      if (z) d += (Ex[nb(g, c, 2, 1)] - Ex[q]) * g.idx[2];
-      By[q] -= h * d;
-    }
-    if (!exterior(g, 3, c)) {
-      float d = (Ey[nb(g, c, 0, 1)] - Ey[q]) * g.idx[0];
-      if (y) d -= (Ex[nb(g, c, 1, 1)] - Ex[q]) * g.idx[1];
-      Bz[q] -= h * d;
-    }
+template <int D>
+__global__ void __launch_bounds__(256) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
+                                               const float *__restrict__ Ey, const float *__restrict__ Ez, float h) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
+  const long long q = C.q;
+  if (!exterior_c<D>(g, 6, C.c)) {
+    float d = 0.0f;
+    if (D >= 2) d += (Ez[q + C.up[1]] - Ez[q]) * g.idx[1];
+    if (D >= 3) d -= (Ey[q + C.up[2]] - Ey[q]) * g.idx[2];
+    Bx[q] -= h * d;
+  }
+  if (!exterior_c<D>(g, 5, C.c)) {
+    float d = -(Ez[q + C.up[0]] - Ez[q]) * g.idx[0];
+    if (D >= 3) d += (Ex[q + C.up[2]] - Ex[q]) * g.idx[2];
+    By[q] -= h * d;
+  }
+  if (!exterior_c<D>(g, 3, C.c)) {
+    float d = (Ey[q + C.up[0]] - Ey[q]) * g.idx[0];
+    if (D >= 2) d -= (Ex[q + C.up[1]] - Ex[q]) * g.idx[1];
+    Bz[q] -= h * d;
   }
 }
 
 // E <- E + dt (curl B - J) on interior nodes (backward differences)
-__global__ void k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
-                        const float *__restrict__ By, const float *__restrict__ Bz, const float *__restrict__ Jx,
-                        const float *__restrict__ Jy, const float *__restrict__ Jz) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3], f;
-    cell_coords(g, q, c);
-    const bool y = g.D >= 2, z = g.D >= 3;
-    if (!exterior(g, 1, c) && nbound(g, 1, c, &f) == 0) {
-      float d = 0.0f;
-      if (y) d += (Bz[q] - Bz[nb(g, c, 1, -1)]) * g.idx[1];
-      if (z) d -= (By[q] - By[nb(g, c, 2, -1)]) * g.idx[2];
-      Ex[q] += g.dt * (d - Jx[q]);
-    }
-    if (!exterior(g, 2, c) && nbound(g, 2, c, &f) == 0) {
-      float d = -(Bz[q] - Bz[nb(g, c, 0, -1)]) * g.idx[0];
-      if (z) d += (Bx[q] - Bx[nb(g, c, 2, -1)]) * g.idx[2];
-      Ey[q] += g.dt * (d - Jy[q]);
-    }
-    if (!exterior(g, 4, c) && nbound(g, 4, c, &f) == 0) {
-      float d = (By[q] - By[nb(g, c, 0, -1)]) * g.idx[0];
-      if (y) d -= (Bx[q] - Bx[nb(g, c, 1, -1)]) * g.idx[1];
-      Ez[q] += g.dt * (d - Jz[q]);
-    }
+template <int D>
+__global__ void __launch_bounds__(256) k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
+                                               const float *__restrict__ By, const float *__restrict__ Bz,
+                                               const float *__restrict__ Jx, const float *__restrict__ Jy,
+                                               const float *__restrict__ Jz) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
+  const long long q = C.q;
+  if (!exterior_c<D>(g, 1, C.c) && !mur_node<D>(g, 1, C.c)) {
+    float d = 0.0f;
+    if (D >= 2) d += (Bz[q] - Bz[q + C.dn[1]]) * g.idx[1];
+    if (D >= 3) d -= (By[q] - By[q + C.dn[2]]) * g.idx[2];
+    Ex[q] += g.dt * (d - Jx[q]);
+  }
+  if (!exterior_c<D>(g, 2, C.c) && !mur_node<D>(g, 2, C.c)) {
+    float d = -(Bz[q] - Bz[q + C.dn[0]]) * g.idx[0];
+    if (D >= 3) d += (Bx[q] - Bx[q + C.dn[2]]) * g.idx[2];
+    Ey[q] += g.dt * (d - Jy[q]);
+  }
+  if (!exterior_c<D>(g, 4, C.c) && !mur_node<D>(g, 4, C.c)) {
+    float d = (By[q] - By[q + C.dn[0]]) * g.idx[0];
+    if (D >= 2) d -= (Bx[q] - Bx[q + C.dn[1]]) * g.idx[1];
+    Ez[q] += g.dt * (d - Jz[q]);
   }
 }
 
@@ -217,62 +249,70 @@ struct LaserSet {
   LaserP l[BP_MAX_LASER];
 };
 
-__global__ void k_jsum(GridP g, const float *__restrict__ jbox, const unsigned char *__restrict__ occ, float *Jx,
-                       float *Jy, float *Jz, LaserSet las, double t) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    cell_coords(g, q, c);
-    int tw[3][3], loc[3][3], nc[3];
+template <int D>
+__global__ void __launch_bounds__(256) k_jsum(GridP g, const float *__restrict__ jbox,
+                                              const unsigned char *__restrict__ occ, const uint2 *__restrict__ jbb,
+                                              float *Jx, float *Jy, float *Jz, LaserSet las, double t) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
+  const int *c = C.c;
+  // the (up to three per axis) tiles whose boxes cover the cell, ascending
+  int tw[3][3], loc[3][3], nc[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      nc[a] = 0;
-      if (a >= g.D) {
-        tw[a][0] = 0;
-        loc[a][0] = 0;
-        nc[a] = 1;
-        continue;
-      }
-      int tb = c[a] / g.L[a];
-      for (int dt = -1; dt <= 1; ++dt) {
-        int tu = tb + dt;
-        int l = c[a] - (tu * g.L[a] - g.oj[a]);
-        if (l < 0 || l >= g.jb[a]) continue;
-        int tt = tu;
-        if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
-        else if (tu < 0 || tu >= g.nt[a]) continue;
-        tw[a][nc[a]] = tt;
-        loc[a][nc[a]] = l;
-        ++nc[a];
-      }
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = 0;
+    if (a >= D) {
+      tw[a][0] = 0;
+      loc[a][0] = 0;
+      nc[a] = 1;
+      continue;
     }
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-    for (int k = 0; k < nc[2]; ++k)
-      for (int j = 0; j < nc[1]; ++j)
-        for (int i = 0; i < nc[0]; ++i) {
-          int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
-          if (!occ[tile]) continue;
-          long long l = loc[0][i] + (long long)g.jb[0] * (loc[1][j] + (long long)g.jb[1] * loc[2][k]);
-          const float *b = jbox + (size_t)tile * 3 * g.jcells;
-          sx += b[l];
-          sy += b[g.jcells + l];
-          sz += b[2 * g.jcells + l];
-        }
-    for (int s = 0; s < las.n; ++s) {
-      const LaserP &L = las.l[s];
-      if (c[0] != L.ia) continue;
-      // the antenna current sits on the E_y (comp 1) or E_z (comp 2) location
-      double y = g.D >= 2 ? (c[1] + (L.comp == 1 ? 0.5 : 0.0)) * g.dxd[1] : 0.0;
-      double z = g.D >= 3 ? (c[2] + (L.comp == 2 ? 0.5 : 0.0)) * g.dxd[2] : 0.0;
-      double amp = -2.0 / g.dxd[0] * (L.comp == 2 ? cos(L.theta) : 1.0);
-      double v = amp * laser_value(L, t, y, z);
-      if (L.comp == 1) sy = (float)((double)sy + v);
-      else sz = (float)((double)sz + v);
+    const int tb = c[a] / g.L[a];
+#pragma unroll
+    for (int dt = -1; dt <= 1; ++dt) {
+      const int tu = tb + dt;
+      const int l = c[a] - (tu * g.L[a] - g.oj[a]);
+      if (l < 0 || l >= g.jb[a]) continue;
+      int tt = tu;
+      if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
+      else if (tu < 0 || tu >= g.nt[a]) continue;
+      tw[a][nc[a]] = tt;
+      loc[a][nc[a]] = l;
+      ++nc[a];
     }
-    Jx[q] = sx;
-    Jy[q] = sy;
-    Jz[q] = sz;
   }
+  float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+  for (int k = 0; k < nc[2]; ++k)
+    for (int j = 0; j < nc[1]; ++j)
+      for (int i = 0; i < nc[0]; ++i) {
+        const int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
+        if (!occ[tile]) continue;
+        // outside the tile's deposit box every entry is zero (and unwritten)
+        const uint2 bb = jbb[tile];
+        const int l0 = loc[0][i], l1 = loc[1][j], l2 = loc[2][k];
+        if (l0 < (int)(bb.x & 255u) || l0 > (int)(bb.y & 255u) || l1 < (int)((bb.x >> 8) & 255u) ||
+            l1 > (int)((bb.y >> 8) & 255u) || l2 < (int)((bb.x >> 16) & 255u) || l2 > (int)((bb.y >> 16) & 255u))
+          continue;
+        const long long l = l0 + (long long)g.jb[0] * (l1 + (long long)g.jb[1] * l2);
+        const float *b = jbox + (size_t)tile * 3 * g.jcells;
+        sx += b[l];
+        sy += b[g.jcells + l];
+        sz += b[2 * g.jcells + l];
+      }
+  for (int s = 0; s < las.n; ++s) {
+    const LaserP &L = las.l[s];
+    if (c[0] != L.ia) continue;
+    // the antenna current sits on the E_y (comp 1) or E_z (comp 2) location
+    double y = D >= 2 ? (c[1] + (L.comp == 1 ? 0.5 : 0.0)) * g.dxd[1] : 0.0;
+    double z = D >= 3 ? (c[2] + (L.comp == 2 ? 0.5 : 0.0)) * g.dxd[2] : 0.0;
+    double amp = -2.0 / g.dxd[0] * (L.comp == 2 ? cos(L.theta) : 1.0);
+    double v = amp * laser_value(L, t, y, z);
+    if (L.comp == 1) sy = (float)((double)sy + v);
+    else sz = (float)((double)sz + v);
+  }
+  Jx[C.q] = sx;
+  Jy[C.q] = sy;
+  Jz[C.q] = sz;
 }
 
 __global__ void k_probe(const float *F, const long long *nodes, long long npts, float *buf) {
@@ -295,15 +335,26 @@ long long frame_floats(const GridP &g) {
   return t;
 }
 
+int row_blocks(const GridP &g, int bs) {
+  const long long rows = g.ncell / g.n[0];
+  return (int)(rows * ((g.n[0] + bs - 1) / bs));
+}
+
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s) {
-  k_yee_b<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  const int nb = row_blocks(g, 256);
+  if (g.D == 1) k_yee_b<1><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  else if (g.D == 2) k_yee_b<2><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  else k_yee_b<3><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
 }
 
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3], float *frame,
                   cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
-  k_yee_e<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
+  const int nb = row_blocks(g, 256);
+  if (g.D == 1) k_yee_e<1><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
+  else if (g.D == 2) k_yee_e<2><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
+  else k_yee_e<3><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
   if (nf) {
     int nopen = 0;
     for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
@@ -312,12 +363,15 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], co
   }
 }
 
-void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, float *const J[3], const LaserP *las,
-                 int nlas, double t, cudaStream_t s) {
+void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
+                 const LaserP *las, int nlas, double t, cudaStream_t s) {
   LaserSet ls;
   ls.n = nlas;
   for (int i = 0; i < nlas; ++i) ls.l[i] = las[i];
-  k_jsum<<<grid_blocks(g.ncell, 256), 256, 0, s>>>(g, jbox, occ, J[0], J[1], J[2], ls, t);
+  const int nb = row_blocks(g, 256);
+  if (g.D == 1) k_jsum<1><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  else if (g.D == 2) k_jsum<2><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  else k_jsum<3><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
 }
 
 void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,

@@ -335,9 +335,31 @@ __device__ __noinline__ void deposit_in_place(JT *Jsm, const QIn &in, float scal
     }
 }
 
+// node bounding box of a thread's deposits, one byte per axis (box
+// coordinates are below 256); axes the grid does not simulate stay at 0
+template <int D>
+__device__ __forceinline__ void bb_add(unsigned &lo, unsigned &hi, const int n[3], int below, int above) {
+  unsigned l = 0, h = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    l |= (unsigned)(n[a] - below) << (8 * a);
+    h |= (unsigned)(n[a] + above) << (8 * a);
+  }
+  lo = __vminu4(lo, l);
+  hi = __vmaxu4(hi, h);
+}
+
+// the five-node window's centre node (as window() places it)
+template <int D>
+__device__ __forceinline__ void window_centre(const float *f, const int *d, int n0[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) n0[a] = a < D ? d[a] + Box<D>::OJ + (f[a] >= 0.5f ? 1 : 0) : 0;
+}
+
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
-                              const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax) {
+                              const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax,
+                              unsigned &blo, unsigned &bhi) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   int cell = P.cell[i];
@@ -466,6 +488,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       }
       if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
       else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+      bb_add<D>(blo, bhi, nn, 1, 1);
     } else {
       QIn in;
 #pragma unroll
@@ -479,6 +502,13 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       const int slot = atomicAdd(qn, 1);
       if (slot < qmax) queue_record<D>(qrec[slot], in);
       else deposit_in_place<D, DET, JT>(Jsm, in, scale);
+      int n0[3];
+      window_centre<D>(f, d, n0);
+      bb_add<D>(blo, bhi, n0, 2, 2);
+      if (two) {
+        window_centre<D>(f2, d2, n0);
+        bb_add<D>(blo, bhi, n0, 2, 2);
+      }
     }
   }
   // new cell of body 1.  On open axes a free particle whose cell leaves
@@ -582,6 +612,9 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   constexpr int QMAX = push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
   __shared__ int qn;
+  __shared__ unsigned sbb[6];
+  if (tid < 6) sbb[tid] = tid < 3 ? 0xFFFFFFFFu : 0u;
+  unsigned blo = 0xFFFFFFFFu, bhi = 0u;
   for (int s = 0; s < A.nsp; ++s) {
     if (tid == 0) qn = 0;
     __syncthreads();
@@ -589,7 +622,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     // consecutive lanes take consecutive (cell-sorted) particles: their
     // gather loads share addresses and their state loads coalesce
     for (long long i = beg + tid; i < end; i += bs)
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX);
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi);
     __syncthreads();
     // the deferred general deposits, one row per thread
     const int nitem = min(qn, QMAX) * 2 * IPB;
@@ -602,20 +635,42 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
     __syncthreads();
   }
-  // the box to global memory in the compact layout
-  constexpr int JN = BX::JCOMP;
-  float *out = A.jbox + (size_t)t * 3 * JN;
-  for (int q = tid; q < 3 * JN; q += bs) {
-    const int cc = q / JN, r = q - cc * JN;
-    const int k = cc * JC + BX::ji(r % BX::J0, (r / BX::J0) % BX::J1, r / (BX::J0 * BX::J1));
-    if constexpr (DET) {
-      const long long w = (long long)(((unsigned long long)Jsm[3 * JC + k] << 32) | Jsm[k]) - JBIAS;
-      out[q] = __ll2float_rn(w) * A.jinv;  // jinv = 2^-k: one rounding
-    } else {
-      out[q] = Jsm[k];
+  // the deposits' bounding box over the block
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const unsigned l = __reduce_min_sync(0xFFFFFFFFu, blo == 0xFFFFFFFFu ? 0xFFFFFFFFu : (blo >> (8 * a)) & 255u);
+    const unsigned h = __reduce_max_sync(0xFFFFFFFFu, (bhi >> (8 * a)) & 255u);
+    if ((tid & 31) == 0 && l != 0xFFFFFFFFu) {
+      atomicMin(&sbb[a], l);
+      atomicMax(&sbb[3 + a], h);
     }
   }
-  if (tid == 0) A.occ[t] = 1;
+  __syncthreads();
+  const bool any = sbb[0] != 0xFFFFFFFFu;
+  // the box's occupied part to global memory (compact per-tile layout)
+  constexpr int JN = BX::JCOMP;
+  float *out = A.jbox + (size_t)t * 3 * JN;
+  if (any) {
+    const int lo0 = sbb[0], lo1 = sbb[1], lo2 = sbb[2];
+    const int nx = sbb[3] - lo0 + 1, ny = sbb[4] - lo1 + 1, nz = sbb[5] - lo2 + 1;
+    const int nbox = nx * ny * nz;
+    for (int q = tid; q < 3 * nbox; q += bs) {
+      const int cc = q / nbox, r = q - cc * nbox;
+      const int x = lo0 + r % nx, y = lo1 + (r / nx) % ny, z = lo2 + r / (nx * ny);
+      const int k = cc * JC + BX::ji(x, y, z);
+      const int o = cc * JN + x + BX::J0 * (y + BX::J1 * z);
+      if constexpr (DET) {
+        const long long w = (long long)(((unsigned long long)Jsm[3 * JC + k] << 32) | Jsm[k]) - JBIAS;
+        out[o] = __ll2float_rn(w) * A.jinv;  // jinv = 2^-k: one rounding
+      } else {
+        out[o] = Jsm[k];
+      }
+    }
+  }
+  if (tid == 0) {
+    A.occ[t] = any ? 1 : 0;
+    A.jbb[t] = make_uint2(sbb[0] | (sbb[1] << 8) | (sbb[2] << 16), sbb[3] | (sbb[4] << 8) | (sbb[5] << 16));
+  }
 }
 
 template <int D, bool DET>
