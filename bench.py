@@ -212,7 +212,10 @@ def run_adjoint_ratio(steps=400, K=20):
     return {"workload": "cfg3_adjoint_2d: 1024x1024 cells, dx=lambda/32, 524288 ions on 4096 sites, "
                         "1024 per-column omega_b, 400 steps, checkpoint every 20",
             "plain_forward_ms": t_plain, "ckpt_forward_ms": t_fwd, "backward_ms": t_bwd,
-            "ratio": (t_fwd + t_bwd) / t_plain}
+            "ratio": (t_fwd + t_bwd) / t_plain,
+            "backward_over_forward": t_bwd / t_plain,
+            "definitions": "ratio = (checkpointed forward + backward) / plain forward; backward_over_forward = "
+                           "backward (segment recompute + reverse steps) / plain forward"}
 
 
 def our_config(n_ion, mode, world, warmup=3, steps=500):

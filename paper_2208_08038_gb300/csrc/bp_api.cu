@@ -513,23 +513,35 @@ int copy_alloc(bp_ctx *c, const PartP &src, int D, bool two, PartP &dst) {
   return BP_OK;
 }
 
-void copy_parts(bp_ctx *c, const PartP &src, PartP &dst, int D, bool two) {
-  cudaStream_t st = c->stream;
-  long long cap = src.cap;
-  cudaMemcpyAsync(dst.cell, src.cell, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(dst.off, src.off, sizeof(float) * D * cap, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(dst.u1, src.u1, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(dst.id, src.id, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(dst.tstart, src.tstart, sizeof(int) * (c->g.ntiles + 1), cudaMemcpyDeviceToDevice, st);
-  if (two) {
-    cudaMemcpyAsync(dst.r, src.r, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(dst.u2, src.u2, sizeof(float) * 3 * cap, cudaMemcpyDeviceToDevice, st);
+// batched device-to-device copies (one kernel per up to 32 arrays)
+void cl_flush(bp_ctx *c, CopyList &L) {
+  if (L.n) {
+    launch_copy_many(L, c->stream);
+    c->launches++;
+    L.n = 0;
   }
-  if (src.pidx) cudaMemcpyAsync(dst.pidx, src.pidx, sizeof(int) * cap, cudaMemcpyDeviceToDevice, st);
+}
+void cl_add(bp_ctx *c, CopyList &L, const void *src, void *dst, long long bytes) {
+  if (L.n == CopyList::MAX) cl_flush(c, L);
+  L.src[L.n] = src;
+  L.dst[L.n] = dst;
+  L.words[L.n] = bytes / 4;
+  ++L.n;
+}
+void cl_parts(bp_ctx *c, CopyList &L, const PartP &src, PartP &dst, int D, bool two) {
+  const long long cap = src.cap;
+  cl_add(c, L, src.cell, dst.cell, sizeof(int) * cap);
+  cl_add(c, L, src.off, dst.off, sizeof(float) * D * cap);
+  cl_add(c, L, src.u1, dst.u1, sizeof(float) * 3 * cap);
+  cl_add(c, L, src.id, dst.id, sizeof(int) * cap);
+  cl_add(c, L, src.tstart, dst.tstart, sizeof(int) * (c->g.ntiles + 1));
+  if (two) {
+    cl_add(c, L, src.r, dst.r, sizeof(float) * 3 * cap);
+    cl_add(c, L, src.u2, dst.u2, sizeof(float) * 3 * cap);
+  }
+  if (src.pidx) cl_add(c, L, src.pidx, dst.pidx, sizeof(int) * cap);
 }
 
-// one leapfrog step; when snap_fields is given, E^n and B^n (after the first
-// half step) and the particle state before the push are copied there
 // the re-sort graph of the current particle arrays (built on first use and
 // after any reallocation); false if the CUDA runtime cannot build it, in
 // which case the step launches the sort pipeline directly
@@ -574,6 +586,8 @@ bool sort_graph(bp_ctx *c) {
   return true;
 }
 
+// one leapfrog step; when snap_fields is given, E^n and B^n (after the first
+// half step) and the particle state before the push are copied there
 int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fields,
              std::vector<bp_part_copy> *snap_parts) {
   const GridP &g = c->g;
@@ -596,11 +610,12 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
   }
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
   if (snap_fields) {
-    for (int k = 0; k < 6; ++k)
-      cudaMemcpyAsync(snap_fields + (size_t)k * g.ncell, c->F[k], sizeof(float) * g.ncell, cudaMemcpyDeviceToDevice, st);
+    CopyList L;
+    for (int k = 0; k < 6; ++k) cl_add(c, L, c->F[k], snap_fields + (size_t)k * g.ncell, sizeof(float) * g.ncell);
     int q = 0;
     for (auto &s : c->sp)
-      if (s.loaded) copy_parts(c, s.p, (*snap_parts)[q++].p, g.D, s.sp.kind == BP_TWO_BODY);
+      if (s.loaded) cl_parts(c, L, s.p, (*snap_parts)[q++].p, g.D, s.sp.kind == BP_TWO_BODY);
+    cl_flush(c, L);
   }
   if (c->timing) {
     if (c->ev_used + 2 > c->ev.size()) {
@@ -897,12 +912,12 @@ int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
   cudaStream_t st = c->stream;
   for (int k = 0; k < nseg; ++k) {
     // the state before step start + k K: E, B^{n-1/2}, particles
-    for (int f = 0; f < 6; ++f)
-      cudaMemcpyAsync(ad.ck_fields[k] + (size_t)f * g.ncell, c->F[f], sizeof(float) * g.ncell,
-                      cudaMemcpyDeviceToDevice, st);
+    CopyList L;
+    for (int f = 0; f < 6; ++f) cl_add(c, L, c->F[f], ad.ck_fields[k] + (size_t)f * g.ncell, sizeof(float) * g.ncell);
     for (size_t q = 0; q < c->sp.size(); ++q)
-      copy_parts(c, c->sp[q].p, ad.ck_parts[k][q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
-    cudaMemcpyAsync(ad.ck_status + 4 * k, c->status, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st);
+      cl_parts(c, L, c->sp[q].p, ad.ck_parts[k][q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
+    cl_add(c, L, c->status, ad.ck_status + 4 * k, sizeof(int) * 4);
+    cl_flush(c, L);
     long long len = std::min<long long>(K, nsteps - (long long)k * K);
     for (long long j = 0; j < len; ++j) {
       int rc = one_step(c, A, nsp, true, nullptr, nullptr);
@@ -937,20 +952,24 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     }
     ad.box = (float *)dalloc(c, sizeof(float) * 6 * (size_t)g.gcells * g.ntiles);
     ad.occ = (unsigned char *)dalloc(c, g.ntiles);
-    if (!ad.box || !ad.occ) return fail(c, BP_ERR_OOM, "adjoint boxes");
+    ad.emax = (unsigned *)dalloc(c, sizeof(unsigned));
+    if (!ad.box || !ad.occ || !ad.emax) return fail(c, BP_ERR_OOM, "adjoint boxes");
   }
   bool xb_ok = ad.xb.size() == c->sp.size() && ad.xb_cap.size() == c->sp.size();
   for (size_t q = 0; xb_ok && q < c->sp.size(); ++q) xb_ok = ad.xb_cap[q] == c->sp[q].p.cap;
   if (!xb_ok) {
     for (auto p : ad.xb) dfree(c, p);
     for (auto p : ad.acb) dfree(c, p);
+    for (auto p : ad.eb) dfree(c, p);
     ad.xb.assign(c->sp.size(), nullptr);
     ad.acb.assign(c->sp.size(), nullptr);
+    ad.eb.assign(c->sp.size(), nullptr);
     ad.xb_cap.assign(c->sp.size(), 0);
     for (size_t q = 0; q < c->sp.size(); ++q) {
       ad.xb[q] = (float *)dalloc(c, sizeof(float) * 12 * c->sp[q].p.cap);
       ad.acb[q] = (double *)dalloc(c, sizeof(double) * c->sp[q].p.cap);
-      if (!ad.xb[q] || !ad.acb[q]) return fail(c, BP_ERR_OOM, "particle adjoints");
+      ad.eb[q] = (float *)dalloc(c, sizeof(float) * 12 * c->sp[q].p.cap);
+      if (!ad.xb[q] || !ad.acb[q] || !ad.eb[q]) return fail(c, BP_ERR_OOM, "particle adjoints");
       ad.xb_cap[q] = c->sp[q].p.cap;
     }
   }
@@ -965,7 +984,9 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   for (int k = 0; k < 3; ++k) {
     cudaMemsetAsync(ad.lamE[k], 0, sizeof(float) * g.ncell, st);
     cudaMemsetAsync(ad.lamB[k], 0, sizeof(float) * g.ncell, st);
+    cudaMemsetAsync(ad.H[k], 0, sizeof(float) * g.ncell, st);
   }
+  cudaMemsetAsync(ad.emax, 0, sizeof(unsigned), st);
   for (size_t q = 0; q < c->sp.size(); ++q) {
     cudaMemsetAsync(ad.xb[q], 0, sizeof(float) * 12 * c->sp[q].p.cap, st);
     cudaMemsetAsync(ad.acb[q], 0, sizeof(double) * c->sp[q].p.cap, st);
@@ -973,23 +994,24 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   int nsp = 0;
   PushArgs A = push_args(c, &nsp);
   std::vector<SpecP> sps;
-  std::vector<float *> xbs;
+  std::vector<float *> xbs, ebs;
   std::vector<double *> acbs;
   std::vector<long long> caps;
   for (size_t q = 0; q < c->sp.size(); ++q) {
     sps.push_back(c->sp[q].sp);
     xbs.push_back(ad.xb[q]);
+    ebs.push_back(ad.eb[q]);
     acbs.push_back(ad.acb[q]);
     caps.push_back(c->sp[q].p.cap);
   }
   for (int seg = ad.nseg - 1; seg >= 0; --seg) {
     // restore the checkpoint and recompute the segment, storing each step
-    for (int f = 0; f < 6; ++f)
-      cudaMemcpyAsync(c->F[f], ad.ck_fields[seg] + (size_t)f * g.ncell, sizeof(float) * g.ncell,
-                      cudaMemcpyDeviceToDevice, st);
+    CopyList L;
+    for (int f = 0; f < 6; ++f) cl_add(c, L, ad.ck_fields[seg] + (size_t)f * g.ncell, c->F[f], sizeof(float) * g.ncell);
     for (size_t q = 0; q < c->sp.size(); ++q)
-      copy_parts(c, ad.ck_parts[seg][q].p, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
-    cudaMemcpyAsync(c->status, ad.ck_status + 4 * seg, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st);
+      cl_parts(c, L, ad.ck_parts[seg][q].p, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
+    cl_add(c, L, ad.ck_status + 4 * seg, c->status, sizeof(int) * 4);
+    cl_flush(c, L);
     const long long base = (long long)seg * ad.K;
     const long long len = std::min<long long>(ad.K, ad.nsteps - base);
     c->step = ad.start + base;
@@ -1004,12 +1026,12 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
         launch_adj_inject(ad.lamE[P.comp], P.nodes, P.npts, ad.dl + n * P.npts, st);
         c->launches++;
       }
-      // E update with Mur faces, transposed
-      for (int k = 0; k < 3; ++k) cudaMemsetAsync(ad.H[k], 0, sizeof(float) * g.ncell, st);
+      // E update with Mur faces, transposed (H is clear: zeroed before the
+      // first reverse step, then by the previous step's B transpose)
       launch_adj_e(g, ad.lamE, ad.H, ad.lamB, ad.lamJ, st);
       for (int k = 0; k < 3; ++k) std::swap(ad.lamE[k], ad.H[k]);
-      // B^{n+1/2} = B^n - dt/2 curl E^n
-      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, st);
+      // B^{n+1/2} = B^n - dt/2 curl E^n; clears H (the old E adjoint) for the next step
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, ad.H, st);
       // particles, with E^n, B^n and the particle state stored for step n
       const float *En[3], *Bn[3], *lJ[3] = {ad.lamJ[0], ad.lamJ[1], ad.lamJ[2]};
       for (int k = 0; k < 3; ++k) {
@@ -1018,11 +1040,15 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
       }
       std::vector<PartP> pp;
       for (size_t q = 0; q < c->sp.size(); ++q) pp.push_back(ad.st_parts[j][q].p);
-      launch_adj_push(g, (int)c->sp.size(), sps.data(), pp.data(), xbs.data(), acbs.data(), caps.data(), En, Bn, lJ,
-                      ad.box, ad.occ, ad.lamE, ad.lamB, st);
+      launch_adj_push(g, (int)c->sp.size(), sps.data(), pp.data(), xbs.data(), acbs.data(), ebs.data(), caps.data(), En,
+                      Bn, lJ, ad.box, ad.occ, ad.emax, ad.lamE, ad.lamB, st);
       // B^n = B^{n-1/2} - dt/2 curl E^n
-      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, st);
-      c->launches += 6;
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, nullptr, st);
+      // E transpose and its Mur passes (one per pass and open axis), two B
+      // transposes, particle adjoint, scatter, box sum
+      int nopen = 0;
+      for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
+      c->launches += 1 + nopen * nopen + 2 + 3;
       int rc = check_launch(c, "backward step");
       if (rc) return rc;
     }

@@ -36,6 +36,8 @@ struct bp_adjoint {
   unsigned char *occ = nullptr;
   std::vector<float *> xb;     // per species [12][cap]
   std::vector<double *> acb;   // per species [cap]
+  std::vector<float *> eb;     // per species [12][cap], the step's gathered-field adjoints by slot
+  unsigned *emax = nullptr;    // their largest magnitude (float bits)
   std::vector<long long> xb_cap;
   float *dl = nullptr;         // probe-loss gradient on the device
   long long dl_len = 0;

@@ -138,6 +138,108 @@ __host__ __device__ __forceinline__ int wrap_mod(int i, int n) {
 // one-cell move on a grid of at least one tile): no integer division
 __host__ __device__ __forceinline__ int wrap_once(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// One thread per cell; a block covers a chunk of one x row (row = y + n1 z),
+// so coordinates come from one division per block and the neighbours are
+// fixed offsets (+-1, +-n0, +-n0 n1) with the periodic wrap applied once.
+struct Cell {
+  long long q;      // linear index
+  int c[3];         // coordinates
+  long long up[3];  // offset to the +1 neighbour along each axis (periodic wrap)
+  long long dn[3];  // offset to the -1 neighbour
+};
+
+template <int D>
+__device__ __forceinline__ bool row_cell(const GridP &g, Cell &C) {
+  const int n0 = g.n[0];
+  const int chunks = (n0 + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int row = (int)blockIdx.x / chunks;
+  const int x = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
+  if (x >= n0) return false;
+  C.c[0] = x;
+  C.c[1] = D >= 2 ? row % g.n[1] : 0;
+  C.c[2] = D >= 3 ? row / g.n[1] : 0;
+  C.q = (long long)row * n0 + x;
+  long long stride = 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int n = g.n[a];
+    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
+    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
+    stride *= n;
+  }
+  return true;
+}
+
+// along an open axis a component with half stagger has no value at n-1
+// (exterior), one with node stagger has Mur boundary nodes at 0 and n-1
+template <int D>
+__device__ __forceinline__ bool exterior_c(const GridP &g, int pat, const int c[3]) {
+  bool e = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if (g.bc[a] == BP_OPEN && ((pat >> a) & 1)) e |= c[a] == g.n[a] - 1;
+  return e;
+}
+template <int D>
+__device__ __forceinline__ bool mur_node(const GridP &g, int pat, const int c[3]) {
+  bool m = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if (g.bc[a] == BP_OPEN && !((pat >> a) & 1)) m |= c[a] == 0 || c[a] == g.n[a] - 1;
+  return m;
+}
+
+// blocks of a row-blocked launch (one block per chunk of bs cells of an x row)
+inline int row_blocks(const GridP &g, int bs) {
+  const long long rows = g.ncell / g.n[0];
+  return (int)(rows * ((g.n[0] + bs - 1) / bs));
+}
+
+// float -> int64, rounded to nearest even, on the FP32 and integer pipes
+// (the 64-bit conversion runs on the slow FP64 unit).  Adding 1.5 * 2^23 to
+// a float of magnitude below 2^22 rounds it to an integer held in the low
+// mantissa bits; x is split exactly as h 2^22 + l with h = rne(x / 2^22) and
+// |l| <= 2^21, and both parts are rounded that way.  Valid for |x| < 2^44.
+__device__ __forceinline__ long long f2ll_rn(float x) {
+  constexpr float M = 12582912.0f;
+  const float hs = __fadd_rn(x * 2.384185791015625e-07f, M);
+  const float h = __fsub_rn(hs, M);
+  const float l = fmaf(-h, 4194304.0f, x);
+  const int hi = __float_as_int(hs) - 0x4B400000;
+  const int lo = __float_as_int(__fadd_rn(l, M)) - 0x4B400000;
+  return (long long)hi * 4194304LL + (long long)lo;
+}
+
+// Exact fixed-point accumulation with the GPU's native 32-bit shared
+// atomics: a node's 64-bit sum is a low word (unsigned, at lo) and a high
+// word (signed, hoff words later).  The low word takes the low 32 bits of
+// rne(v) and returns its old value; the high word takes the high 32 bits plus
+// the carry out of the low word -- usually zero, so usually one atomic.  The
+// final pair is the exact sum whatever the order of the adds.  (64-bit and
+// FP32 shared atomic adds are compare-and-swap loops on this GPU.)
+__device__ __forceinline__ void fx_add(unsigned int *lo, int hoff, float v) {
+  unsigned int l;
+  int hi;
+  if (fabsf(v) < 2147483648.0f) {
+    const int q = __float2int_rn(v);
+    l = (unsigned int)q;
+    hi = q >> 31;
+  } else {
+    const long long q = f2ll_rn(v);
+    l = (unsigned int)(unsigned long long)q;
+    hi = (int)(q >> 32);
+  }
+  const unsigned int old = atomicAdd(lo, l);
+  unsigned int sum;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=r"(sum), "+r"(hi) : "r"(old), "r"(l));
+  (void)sum;
+  if (hi) atomicAdd(reinterpret_cast<int *>(lo + hoff), hi);
+}
+// the value of a biased pair (low word initialised to 2^31, high word to 0)
+__device__ __forceinline__ long long fx_value(const unsigned int *lo, int hoff) {
+  return (long long)(((unsigned long long)lo[hoff] << 32) | lo[0]) - 0x80000000LL;
+}
+
 // quadratic B-spline weights for the three nodes around the nearest node,
 // xi = position - nearest node in [-1/2, 1/2)
 __device__ __forceinline__ void qweights(float xi, float w[3]) {
@@ -226,12 +328,22 @@ void launch_divE_minus(const GridP &g, const float *const E[3], double *R, cudaS
 // adjoint
 void launch_adj_inject(float *lam, const long long *nodes, long long npts, const float *dl, cudaStream_t s);
 void launch_adj_e(const GridP &g, float *G[3], float *H[3], float *lamB[3], float *lamJ[3], cudaStream_t s);
-void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, cudaStream_t s);
+// device-to-device copies of whole 4-byte-word arrays, issued as one kernel
+struct CopyList {
+  static constexpr int MAX = 32;
+  int n = 0;
+  const void *src[MAX];
+  void *dst[MAX];
+  long long words[MAX];
+};
+void launch_copy_many(const CopyList &L, cudaStream_t s);
+// zero (optional): three arrays cleared on the way
+void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float *zero[3], cudaStream_t s);
 size_t adj_push_smem(int D);
 int adj_prepare(int D);
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
-                     const long long *cap, const float *const E[3], const float *const B[3],
-                     const float *const lamJ[3], float *box, unsigned char *occ, float *lamE[3], float *lamB[3],
-                     cudaStream_t s);
+                     float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
+                     const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
+                     float *lamB[3], cudaStream_t s);
 void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
                     const double *acb, const double *scale, double *out, cudaStream_t s);

@@ -24,12 +24,6 @@ int blocks_for(long long n, int bs) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-__device__ __forceinline__ void coords(const GridP &g, long long q, int c[3]) {
-  c[0] = (int)(q % g.n[0]);
-  long long r = q / g.n[0];
-  c[1] = (int)(r % g.n[1]);
-  c[2] = (int)(r / g.n[1]);
-}
 
 
 
@@ -51,35 +45,6 @@ __device__ __forceinline__ int nbnd(const GridP &g, int pat, const int c[3], int
     }
   return k;
 }
-// E component comp updated by the interior formula at c
-__device__ __forceinline__ bool e_interior(const GridP &g, int comp, const int c[3]) {
-  int f;
-  return !ext(g, 1 << comp, c) && nbnd(g, 1 << comp, c, &f) == 0;
-}
-// value of G masked to interior E nodes (0 off the grid)
-__device__ __forceinline__ float gint(const GridP &g, const float *G, int comp, const int c[3], int a, int o) {
-  int x[3] = {c[0], c[1], c[2]};
-  if (o) {
-    x[a] += o;
-    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
-    if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
-  }
-  if (!e_interior(g, comp, x)) return 0.0f;
-  return G[x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2])];
-}
-// B adjoint masked to non-exterior B nodes
-__device__ __forceinline__ float bnx(const GridP &g, const float *Bb, int comp, const int c[3], int a, int o) {
-  static constexpr int pat[3] = {6, 5, 3};
-  int x[3] = {c[0], c[1], c[2]};
-  if (o) {
-    x[a] += o;
-    if (a < g.D && g.bc[a] == BP_PERIODIC) x[a] = wrap_once(x[a], g.n[a]);
-    if (x[a] < 0 || x[a] >= g.n[a]) return 0.0f;
-  }
-  if (ext(g, pat[comp], x)) return 0.0f;
-  return Bb[x[0] + (long long)g.n[0] * (x[1] + (long long)g.n[1] * x[2])];
-}
-
 __global__ void k_adj_inject(float *lam, const long long *nodes, long long npts, const float *dl) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
     atomicAdd(lam + nodes[q], dl[q]);
@@ -120,63 +85,99 @@ __global__ void k_adj_mur(GridP g, float *G0, float *G1, float *G2, float *H0, f
   }
 }
 
+// E node of component comp at coordinates x updated by the interior formula
+template <int D>
+__device__ __forceinline__ bool e_int(const GridP &g, int comp, const int x[3]) {
+  return !exterior_c<D>(g, 1 << comp, x) && !mur_node<D>(g, 1 << comp, x);
+}
+// G of component comp at the +1 neighbour along a, masked to interior E nodes
+// (0 off an open face)
+template <int D>
+__device__ __forceinline__ float g_up(const GridP &g, const float *G, int comp, const Cell &C, int a) {
+  int x[3] = {C.c[0], C.c[1], C.c[2]};
+  if (++x[a] >= g.n[a]) {
+    if (g.bc[a] != BP_PERIODIC) return 0.0f;
+    x[a] = 0;
+  }
+  return e_int<D>(g, comp, x) ? G[C.q + C.up[a]] : 0.0f;
+}
+template <int D>
+__device__ __forceinline__ float g_here(const GridP &g, const float *G, int comp, const Cell &C) {
+  return e_int<D>(g, comp, C.c) ? G[C.q] : 0.0f;
+}
+
 // interior E update transposed: H += G (interior and exterior nodes),
 // lamJ = -dt G (interior), lamB += dt curl_B^T (G on interior nodes)
-__global__ void k_adj_e(GridP g, const float *G0, const float *G1, const float *G2, float *H0, float *H1, float *H2,
-                        float *B0, float *B1, float *B2, float *J0, float *J1, float *J2) {
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_e(GridP g, const float *G0, const float *G1, const float *G2, float *H0,
+                                               float *H1, float *H2, float *B0, float *B1, float *B2, float *J0,
+                                               float *J1, float *J2) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
   const float *G[3] = {G0, G1, G2};
   float *H[3] = {H0, H1, H2}, *J[3] = {J0, J1, J2};
-  const bool y = g.D >= 2, z = g.D >= 3;
   const float dt = g.dt;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    coords(g, q, c);
+  const long long q = C.q;
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const bool ex = ext(g, 1 << comp, c);
-      const bool in = e_interior(g, comp, c);
-      const float v = G[comp][q];
-      if (in || ex) H[comp][q] += v;
-      J[comp][q] = in ? -dt * v : 0.0f;
-    }
-    // B_x: +dt (g_y[q] - g_y[q+z])/dz - dt (g_z[q] - g_z[q+y])/dy
-    float bx = 0.0f, by = 0.0f, bz = 0.0f;
-    if (z) bx += (gint(g, G[1], 1, c, 2, 0) - gint(g, G[1], 1, c, 2, 1)) * g.idx[2];
-    if (y) bx -= (gint(g, G[2], 2, c, 1, 0) - gint(g, G[2], 2, c, 1, 1)) * g.idx[1];
-    // B_y: -dt (g_x[q] - g_x[q+z])/dz + dt (g_z[q] - g_z[q+x])/dx
-    if (z) by -= (gint(g, G[0], 0, c, 2, 0) - gint(g, G[0], 0, c, 2, 1)) * g.idx[2];
-    by += (gint(g, G[2], 2, c, 0, 0) - gint(g, G[2], 2, c, 0, 1)) * g.idx[0];
-    // B_z: +dt (g_x[q] - g_x[q+y])/dy - dt (g_y[q] - g_y[q+x])/dx
-    if (y) bz += (gint(g, G[0], 0, c, 1, 0) - gint(g, G[0], 0, c, 1, 1)) * g.idx[1];
-    bz -= (gint(g, G[1], 1, c, 0, 0) - gint(g, G[1], 1, c, 0, 1)) * g.idx[0];
-    B0[q] += dt * bx;
-    B1[q] += dt * by;
-    B2[q] += dt * bz;
+  for (int comp = 0; comp < 3; ++comp) {
+    const bool ex = exterior_c<D>(g, 1 << comp, C.c);
+    const bool in = !ex && !mur_node<D>(g, 1 << comp, C.c);
+    const float v = G[comp][q];
+    if (in || ex) H[comp][q] += v;
+    J[comp][q] = in ? -dt * v : 0.0f;
   }
+  float bx = 0.0f, by = 0.0f, bz = 0.0f;
+  if (D >= 3) bx += (g_here<D>(g, G[1], 1, C) - g_up<D>(g, G[1], 1, C, 2)) * g.idx[2];
+  if (D >= 2) bx -= (g_here<D>(g, G[2], 2, C) - g_up<D>(g, G[2], 2, C, 1)) * g.idx[1];
+  if (D >= 3) by -= (g_here<D>(g, G[0], 0, C) - g_up<D>(g, G[0], 0, C, 2)) * g.idx[2];
+  by += (g_here<D>(g, G[2], 2, C) - g_up<D>(g, G[2], 2, C, 0)) * g.idx[0];
+  if (D >= 2) bz += (g_here<D>(g, G[0], 0, C) - g_up<D>(g, G[0], 0, C, 1)) * g.idx[1];
+  bz -= (g_here<D>(g, G[1], 1, C) - g_up<D>(g, G[1], 1, C, 0)) * g.idx[0];
+  B0[q] += dt * bx;
+  B1[q] += dt * by;
+  B2[q] += dt * bz;
+}
+
+// B adjoint of component comp (stagger 6, 5, 3) at the -1 neighbour along a,
+// masked to non-exterior B nodes (0 off an open face)
+template <int D>
+__device__ __forceinline__ float b_dn(const GridP &g, const float *Bb, int pat, const Cell &C, int a) {
+  int x[3] = {C.c[0], C.c[1], C.c[2]};
+  if (--x[a] < 0) {
+    if (g.bc[a] != BP_PERIODIC) return 0.0f;
+    x[a] = g.n[a] - 1;
+  }
+  return exterior_c<D>(g, pat, x) ? 0.0f : Bb[C.q + C.dn[a]];
+}
+template <int D>
+__device__ __forceinline__ float b_here(const GridP &g, const float *Bb, int pat, const Cell &C) {
+  return exterior_c<D>(g, pat, C.c) ? 0.0f : Bb[C.q];
 }
 
 // B <- B - h curl E transposed: E adjoint -= h curl_E^T (B adjoint on
-// non-exterior B nodes); the B adjoint itself passes through
-__global__ void k_adj_b(GridP g, float *E0, float *E1, float *E2, const float *B0, const float *B1, const float *B2,
-                        float h) {
-  const float *Bb[3] = {B0, B1, B2};
-  const bool y = g.D >= 2, z = g.D >= 3;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    coords(g, q, c);
-    // (curl_E^T b) at the E locations, b the B adjoint on non-exterior nodes
-    float ex = 0.0f, ey = 0.0f, ez = 0.0f;
-    if (z) ex += (bnx(g, Bb[1], 1, c, 2, -1) - bnx(g, Bb[1], 1, c, 2, 0)) * g.idx[2];
-    if (y) ex -= (bnx(g, Bb[2], 2, c, 1, -1) - bnx(g, Bb[2], 2, c, 1, 0)) * g.idx[1];
-    if (z) ey -= (bnx(g, Bb[0], 0, c, 2, -1) - bnx(g, Bb[0], 0, c, 2, 0)) * g.idx[2];
-    ey += (bnx(g, Bb[2], 2, c, 0, -1) - bnx(g, Bb[2], 2, c, 0, 0)) * g.idx[0];
-    if (y) ez += (bnx(g, Bb[0], 0, c, 1, -1) - bnx(g, Bb[0], 0, c, 1, 0)) * g.idx[1];
-    ez -= (bnx(g, Bb[1], 1, c, 0, -1) - bnx(g, Bb[1], 1, c, 0, 0)) * g.idx[0];
-    E0[q] -= h * ex;
-    E1[q] -= h * ey;
-    E2[q] -= h * ez;
+// non-exterior B nodes); the B adjoint itself passes through.  Z0..Z2, when
+// given, are cleared on the way (the buffer the next E transpose fills).
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_b(GridP g, float *E0, float *E1, float *E2, const float *B0,
+                                               const float *B1, const float *B2, float h, float *Z0, float *Z1,
+                                               float *Z2) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
+  const long long q = C.q;
+  float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+  if (D >= 3) ex += (b_dn<D>(g, B1, 5, C, 2) - b_here<D>(g, B1, 5, C)) * g.idx[2];
+  if (D >= 2) ex -= (b_dn<D>(g, B2, 3, C, 1) - b_here<D>(g, B2, 3, C)) * g.idx[1];
+  if (D >= 3) ey -= (b_dn<D>(g, B0, 6, C, 2) - b_here<D>(g, B0, 6, C)) * g.idx[2];
+  ey += (b_dn<D>(g, B2, 3, C, 0) - b_here<D>(g, B2, 3, C)) * g.idx[0];
+  if (D >= 2) ez += (b_dn<D>(g, B0, 6, C, 1) - b_here<D>(g, B0, 6, C)) * g.idx[1];
+  ez -= (b_dn<D>(g, B1, 5, C, 0) - b_here<D>(g, B1, 5, C)) * g.idx[0];
+  E0[q] -= h * ex;
+  E1[q] -= h * ey;
+  E2[q] -= h * ez;
+  if (Z0) {
+    Z0[q] = 0.0f;
+    Z1[q] = 0.0f;
+    Z2[q] = 0.0f;
   }
 }
 
@@ -242,116 +243,110 @@ __device__ __forceinline__ void boris_adj(float h, const float E[3], const float
   }
 }
 
-// gather transposed for one component of stagger PAT at NB bodies whose
-// stencils start at the same node (NB = 2: one atomic per node for both):
-// scatter e * weights into the accumulator box, add e * d(field)/dX
-template <int D, int PAT, int NB>
-__device__ __forceinline__ void gather_adj_comp(const float *__restrict__ G, float *Acc, const int (*d)[3],
-                                                const float (*f)[3], const float *e, float (*Xb)[3]) {
+// Gather transposed, part 1 (here): the derivative of a gathered component
+// with respect to the body position, e * d/dX sum_ijk w_i w_j w_k g_ijk,
+// written in factored form (sum_i dw_i sum_jk w_j w_k g_ijk, and the same
+// along y and z).  Part 2, the scatter of e w into the field adjoints, is
+// the separate kernel k_adj_scatter (fixed point, exact and order-free).
+template <int D, int PAT>
+__device__ __forceinline__ void gather_deriv_comp(const float *__restrict__ G, const int d[3], const float f[3], float e,
+                                                  float X[3]) {
   int b[3];
-  float w[NB][3][3], dw[NB][3][3];
+  float w[3][3], dw[3][3];
 #pragma unroll
-  for (int q = 0; q < NB; ++q)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a < D) {
-        const bool half = (PAT >> a) & 1;
-        float xi;
-        if (half) {
-          b[a] = d[q][a] + Box<D>::OG - 1;
-          xi = f[q][a] - 0.5f;
-        } else {
-          int up = f[q][a] >= 0.5f ? 1 : 0;
-          b[a] = d[q][a] + Box<D>::OG + up - 1;
-          xi = f[q][a] - (float)up;
-        }
-        qweights(xi, w[q][a]);
-        dw[q][a][0] = -(0.5f - xi);
-        dw[q][a][1] = -2.0f * xi;
-        dw[q][a][2] = 0.5f + xi;
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      const bool half = (PAT >> a) & 1;
+      float xi;
+      if (half) {
+        b[a] = d[a] + Box<D>::OG - 1;
+        xi = f[a] - 0.5f;
       } else {
-        b[a] = 0;
-        w[q][a][0] = 1.0f; w[q][a][1] = w[q][a][2] = 0.0f;
-        dw[q][a][0] = dw[q][a][1] = dw[q][a][2] = 0.0f;
+        const int up = f[a] >= 0.5f ? 1 : 0;
+        b[a] = d[a] + Box<D>::OG + up - 1;
+        xi = f[a] - (float)up;
       }
+      qweights(xi, w[a]);
+      dw[a][0] = -(0.5f - xi);
+      dw[a][1] = -2.0f * xi;
+      dw[a][2] = 0.5f + xi;
+    } else {
+      b[a] = 0;
     }
-  constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
+  }
+  if constexpr (D == 1) {
+    float dx = 0.0f;
 #pragma unroll
-  for (int k = 0; k < NK; ++k)
+    for (int i = 0; i < 3; ++i) dx = fmaf(dw[0][i], G[Box<D>::gi(b[0] + i, 0, 0)], dx);
+    X[0] += e * dx;
+  } else if constexpr (D == 2) {
+    float c[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int j = 0; j < NJ; ++j)
+    for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const int idx = Box<D>::gi(b[0] + i, b[1] + j, b[2] + k);
-        const float g = G[idx];
-        float acc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          const float F = g * e[q];
-          acc += w[q][0][i] * w[q][1][j] * w[q][2][k] * e[q];
-          Xb[q][0] += dw[q][0][i] * w[q][1][j] * w[q][2][k] * F;
-          if (D >= 2) Xb[q][1] += w[q][0][i] * dw[q][1][j] * w[q][2][k] * F;
-          if (D >= 3) Xb[q][2] += w[q][0][i] * w[q][1][j] * dw[q][2][k] * F;
-        }
-        atomicAdd(Acc + idx, acc);
+        const float v = G[Box<D>::gi(b[0] + i, b[1] + j, 0)];
+        c[i] = fmaf(w[1][j], v, c[i]);
+        r[j] = fmaf(w[0][i], v, r[j]);
       }
-}
-
-// stencil base of one component's gather at a body (to test for sharing)
-template <int D, int PAT>
-__device__ __forceinline__ bool same_base(const int d1[3], const float f1[3], const int d2[3], const float f2[3]) {
-  bool s = true;
+    float dx = 0.0f, dy = 0.0f;
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if ((PAT >> a) & 1) s &= d1[a] == d2[a];
-    else s &= (d1[a] + (f1[a] >= 0.5f ? 1 : 0)) == (d2[a] + (f2[a] >= 0.5f ? 1 : 0));
-  }
-  return s;
-}
-
-template <int D, int PAT>
-__device__ __forceinline__ void gather_adj_pair(const float *G, float *Acc, const int d1[3], const float f1[3],
-                                                float e1, float X1[3], const int d2[3], const float f2[3], float e2,
-                                                float X2[3], bool two) {
-  // warp-uniform choice (both forms give the same sums)
-  if (__all_sync(__activemask(), two && same_base<D, PAT>(d1, f1, d2, f2))) {
-    int dd[2][3] = {{d1[0], d1[1], d1[2]}, {d2[0], d2[1], d2[2]}};
-    float ff[2][3] = {{f1[0], f1[1], f1[2]}, {f2[0], f2[1], f2[2]}};
-    float ee[2] = {e1, e2};
-    float XX[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    gather_adj_comp<D, PAT, 2>(G, Acc, dd, ff, ee, XX);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { X1[a] += XX[0][a]; X2[a] += XX[1][a]; }
-  } else {
-    int dd[1][3] = {{d1[0], d1[1], d1[2]}};
-    float ff[1][3] = {{f1[0], f1[1], f1[2]}};
-    float XX[1][3] = {{0, 0, 0}};
-    gather_adj_comp<D, PAT, 1>(G, Acc, dd, ff, &e1, XX);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) X1[a] += XX[0][a];
-    if (two) {
-      int de[1][3] = {{d2[0], d2[1], d2[2]}};
-      float fe[1][3] = {{f2[0], f2[1], f2[2]}};
-      float XY[1][3] = {{0, 0, 0}};
-      gather_adj_comp<D, PAT, 1>(G, Acc, de, fe, &e2, XY);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) X2[a] += XY[0][a];
+    for (int m = 0; m < 3; ++m) {
+      dx = fmaf(dw[0][m], c[m], dx);
+      dy = fmaf(dw[1][m], r[m], dy);
     }
+    X[0] += e * dx;
+    X[1] += e * dy;
+  } else {
+    // s_ij = sum_k w_k g_ijk, t_ij = sum_k dw_k g_ijk
+    float c[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f}, u[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float sij = 0.0f, tij = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float v = G[Box<D>::gi(b[0] + i, b[1] + j, b[2] + k)];
+          sij = fmaf(w[2][k], v, sij);
+          tij = fmaf(dw[2][k], v, tij);
+        }
+        c[i] = fmaf(w[1][j], sij, c[i]);
+        r[j] = fmaf(w[0][i], sij, r[j]);
+        u[i] = fmaf(w[1][j], tij, u[i]);
+      }
+    float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      dx = fmaf(dw[0][m], c[m], dx);
+      dy = fmaf(dw[1][m], r[m], dy);
+      dz = fmaf(w[0][m], u[m], dz);
+    }
+    X[0] += e * dx;
+    X[1] += e * dy;
+    X[2] += e * dz;
   }
 }
 
 template <int D>
-__device__ __forceinline__ void gather_adj_all(const float *G, float *Acc, const int d1[3], const float f1[3],
-                                               const float Eb1[3], const float Bb1[3], float X1[3], const int d2[3],
-                                               const float f2[3], const float Eb2[3], const float Bb2[3], float X2[3],
-                                               bool two) {
+__device__ __forceinline__ void gather_deriv_all(const float *G, const int d1[3], const float f1[3], const float Eb1[3],
+                                                 const float Bb1[3], float X1[3], const int d2[3], const float f2[3],
+                                                 const float Eb2[3], const float Bb2[3], float X2[3], bool two) {
   constexpr int gc = Box<D>::GCELLS;
-  gather_adj_pair<D, 1>(G + 0 * gc, Acc + 0 * gc, d1, f1, Eb1[0], X1, d2, f2, Eb2[0], X2, two);
-  gather_adj_pair<D, 2>(G + 1 * gc, Acc + 1 * gc, d1, f1, Eb1[1], X1, d2, f2, Eb2[1], X2, two);
-  gather_adj_pair<D, 4>(G + 2 * gc, Acc + 2 * gc, d1, f1, Eb1[2], X1, d2, f2, Eb2[2], X2, two);
-  gather_adj_pair<D, 6>(G + 3 * gc, Acc + 3 * gc, d1, f1, Bb1[0], X1, d2, f2, Bb2[0], X2, two);
-  gather_adj_pair<D, 5>(G + 4 * gc, Acc + 4 * gc, d1, f1, Bb1[1], X1, d2, f2, Bb2[1], X2, two);
-  gather_adj_pair<D, 3>(G + 5 * gc, Acc + 5 * gc, d1, f1, Bb1[2], X1, d2, f2, Bb2[2], X2, two);
+  gather_deriv_comp<D, 1>(G + 0 * gc, d1, f1, Eb1[0], X1);
+  gather_deriv_comp<D, 2>(G + 1 * gc, d1, f1, Eb1[1], X1);
+  gather_deriv_comp<D, 4>(G + 2 * gc, d1, f1, Eb1[2], X1);
+  gather_deriv_comp<D, 6>(G + 3 * gc, d1, f1, Bb1[0], X1);
+  gather_deriv_comp<D, 5>(G + 4 * gc, d1, f1, Bb1[1], X1);
+  gather_deriv_comp<D, 3>(G + 5 * gc, d1, f1, Bb1[2], X1);
+  if (two) {
+    gather_deriv_comp<D, 1>(G + 0 * gc, d2, f2, Eb2[0], X2);
+    gather_deriv_comp<D, 2>(G + 1 * gc, d2, f2, Eb2[1], X2);
+    gather_deriv_comp<D, 4>(G + 2 * gc, d2, f2, Eb2[2], X2);
+    gather_deriv_comp<D, 6>(G + 3 * gc, d2, f2, Bb2[0], X2);
+    gather_deriv_comp<D, 5>(G + 4 * gc, d2, f2, Bb2[1], X2);
+    gather_deriv_comp<D, 3>(G + 5 * gc, d2, f2, Bb2[2], X2);
+  }
 }
 
 // Esirkepov transposed on a window of W nodes per axis (W = 3: every
@@ -373,7 +368,16 @@ __device__ __forceinline__ void deposit_adj(const float *__restrict__ Jl, const 
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int m = 0; m < W; ++m) {
-        if (a < D) {
+        if (a < D && W == 3) {
+          // every position keeps its nearest node: closed forms in xi and
+          // the move d (as in the forward fast path)
+          const float x = xi[q][a], dd = de[q][a];
+          float w3[3];
+          qweights(x, w3);
+          S0[q][a][m] = w3[m];
+          DS[q][a][m] = m == 0 ? -0.5f * dd * (1.0f - 2.0f * x - dd)
+                               : (m == 1 ? -dd * (2.0f * x + dd) : 0.5f * dd * (1.0f + 2.0f * x + dd));
+        } else if (a < D) {
           const float u = xi[q][a] - (float)(m - H);
           S0[q][a][m] = qshape(u);
           DS[q][a][m] = qshape(u + de[q][a]) - S0[q][a][m];
@@ -504,9 +508,19 @@ __device__ __forceinline__ void deposit_adj(const float *__restrict__ Jl, const 
       float x0 = 0.0f, x1 = 0.0f;
 #pragma unroll
       for (int m = 0; m < W; ++m) {
-        const float u = xi[q][a] - (float)(m - H);
-        x0 += (gS0[q][a][m] - gDS[q][a][m]) * dqshape(u);
-        x1 += gDS[q][a][m] * dqshape(u + de[q][a]);
+        float d0, d1;
+        if (W == 3) {
+          // S'(x - node) on the three nodes around the nearest one
+          const float x = xi[q][a], y = x + de[q][a];
+          d0 = m == 0 ? -(0.5f - x) : (m == 1 ? -2.0f * x : 0.5f + x);
+          d1 = m == 0 ? -(0.5f - y) : (m == 1 ? -2.0f * y : 0.5f + y);
+        } else {
+          const float u = xi[q][a] - (float)(m - H);
+          d0 = dqshape(u);
+          d1 = dqshape(u + de[q][a]);
+        }
+        x0 += (gS0[q][a][m] - gDS[q][a][m]) * d0;
+        x1 += gDS[q][a][m] * d1;
       }
       X0b[q][a] += x0;
       X1b[q][a] += x1;
@@ -531,6 +545,7 @@ __device__ __noinline__ void deposit_adj_general(const float *Jl, AdjGen &A) {
 struct AdjState {
   float *xb;      // [12][cap] by load id: x1b(3) x2b(3) u1b(3) u2b(3)
   double *acb;    // [cap] adjoint of a_c, accumulated over steps
+  float *eb;      // [12][cap] by slot: adjoints of the gathered E1 B1 E2 B2 (this step)
   long long cap;
 };
 
@@ -541,13 +556,12 @@ struct AdjArgs {
   AdjState st[BP_MAX_SPECIES];
   const float *E[3], *B[3];      // E^n, B^n
   const float *lamJ[3];
-  float *box;                    // [ntiles][6][gcells]
-  unsigned char *occ;
+  unsigned *emax;                // largest |gathered-field adjoint| of the step (float bits)
 };
 
 template <int D>
 __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, AdjState &S, long long i,
-                             const int T0[3], const float *Gsm, const float *Jl, float *Acc) {
+                             const int T0[3], const float *Gsm, const float *Jl, float &emax) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   const int cell = P.cell[i];
@@ -730,9 +744,18 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
     }
     S.acb[id] += (double)(-3.0f * sp.kappa * wr * ac * p52);
   }
-  // gather transposed; old positions through the deposit
+  // gather transposed: position derivatives here, the field-adjoint scatter
+  // by k_adj_scatter from the stored Eb, Bb; old positions through the deposit
   float Xg1[3] = {0, 0, 0}, Xg2[3] = {0, 0, 0};
-  gather_adj_all<D>(Gsm, Acc, d, f, Eb1, Bb1, Xg1, d2, f2, Eb2, Bb2, Xg2, two);
+  gather_deriv_all<D>(Gsm, d, f, Eb1, Bb1, Xg1, d2, f2, Eb2, Bb2, Xg2, two);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S.eb[(0 + a) * sc + i] = Eb1[a];
+    S.eb[(3 + a) * sc + i] = Bb1[a];
+    S.eb[(6 + a) * sc + i] = Eb2[a];
+    S.eb[(9 + a) * sc + i] = Bb2[a];
+    emax = fmaxf(emax, fmaxf(fmaxf(fabsf(Eb1[a]), fabsf(Bb1[a])), fmaxf(fabsf(Eb2[a]), fabsf(Bb2[a]))));
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     xb1[a] += (Xg1[a] + X10b[a]) * g.idx[a];
@@ -753,16 +776,12 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
   constexpr int GC = BX::GCELLS, JC = BX::JCELLS;
   extern __shared__ __align__(16) unsigned char smem[];
   float *Gsm = reinterpret_cast<float *>(smem);  // E^n, B^n
-  float *Acc = Gsm + 6 * GC;                     // adjoints of E^n, B^n
-  float *Jl = Acc + 6 * GC;                      // adjoint of J
+  float *Jl = Gsm + 6 * GC;                      // adjoint of J
   const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
   int total = 0;
   for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
-  if (total == 0) {
-    if (tid == 0) A.occ[t] = 0;
-    return;
-  }
+  if (total == 0) return;
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
   for (int q = tid; q < BX::GCOMP; q += bs) {
@@ -785,8 +804,6 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
       Gsm[cc * GC + si] = ok ? A.E[cc][gi] : 0.0f;
       Gsm[(3 + cc) * GC + si] = ok ? A.B[cc][gi] : 0.0f;
     }
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) Acc[cc * GC + si] = 0.0f;
   }
   for (int q = tid; q < BX::JCOMP; q += bs) {
     int bidx[3] = {q % BX::J0, (q / BX::J0) % BX::J1, q / (BX::J0 * BX::J1)};
@@ -807,70 +824,217 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
     for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + si] = ok ? A.lamJ[cc][gi] : 0.0f;
   }
   __syncthreads();
+  float emax = 0.0f;
   for (int s = 0; s < A.nsp; ++s) {
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
-    for (int k0 = 0; k0 < end - beg; k0 += bs) {
-      const int j = spread_index(k0, tid, bs);
-      if (j < end - beg) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], beg + j, T0, Gsm, Jl, Acc);
+    for (long long i = beg + tid; i < end; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, emax);
+  }
+  // non-negative floats order like their bit patterns
+  const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(emax));
+  if ((tid & 31) == 0 && m) atomicMax(A.emax, m);
+}
+
+// Gather transposed, part 2: scatter the stored field adjoints e of both
+// bodies with the gather weights into a per-tile box, in 64-bit fixed point
+// (exact, independent of the order of the adds; the scale puts the step's
+// largest |e| at 2^30, so a quantum is below 1e-9 of it), then write the box
+// (compact) for k_adj_boxsum.
+struct ScatArgs {
+  int nsp;
+  SpecP sp[BP_MAX_SPECIES];
+  PartP p[BP_MAX_SPECIES];
+  const float *eb[BP_MAX_SPECIES];
+  long long ecap[BP_MAX_SPECIES];
+  const unsigned *emax;
+  float *box;              // [ntiles][6][gcells] (compact)
+  unsigned char *occ;
+};
+
+// stencil base and weights of component PAT at one body
+template <int D, int PAT>
+__device__ __forceinline__ void scat_loc(const int d[3], const float f[3], int b[3], float w[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      const bool half = (PAT >> a) & 1;
+      const int up = half ? 0 : (f[a] >= 0.5f ? 1 : 0);
+      b[a] = d[a] + Box<D>::OG + up - 1;
+      qweights(half ? f[a] - 0.5f : f[a] - (float)up, w[a]);
+    } else {
+      b[a] = 0;
+      w[a][0] = 1.0f;
+      w[a][1] = w[a][2] = 0.0f;
+    }
+  }
+}
+
+// one component PAT: add e1 w(body 1) + e2 w(body 2) (one add per node when
+// both stencils start at the same node -- a decision of the ion alone, so
+// the rounding does not depend on which ions share a warp)
+template <int D, int PAT>
+__device__ __forceinline__ void scatter_comp(unsigned *A, const int d1[3], const float f1[3], float e1,
+                                             const int d2[3], const float f2[3], float e2, bool two) {
+  constexpr int hoff = 6 * Box<D>::GCELLS;
+  constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
+  int b1[3], b2[3];
+  float w1[3][3], w2[3][3];
+  scat_loc<D, PAT>(d1, f1, b1, w1);
+  scat_loc<D, PAT>(d2, f2, b2, w2);
+  const bool same = two && b1[0] == b2[0] && b1[1] == b2[1] && b1[2] == b2[2];
+#pragma unroll
+  for (int k = 0; k < NK; ++k)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float a1 = e1 * w1[1][j] * w1[2][k];
+      if (same) {
+        const float a2 = e2 * w2[1][j] * w2[2][k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          fx_add(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, __fadd_rn(a1 * w1[0][i], a2 * w2[0][i]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) fx_add(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, a1 * w1[0][i]);
+      }
+    }
+  if (two && !same) {
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const float a2 = e2 * w2[1][j] * w2[2][k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) fx_add(A + Box<D>::gi(b2[0] + i, b2[1] + j, b2[2] + k), hoff, a2 * w2[0][i]);
+      }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S) {
+  using BX = Box<D>;
+  constexpr int GC = BX::GCELLS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned *A = reinterpret_cast<unsigned *>(smem);  // [6][GC] low words, then [6][GC] high words
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  int total = 0;
+  for (int s = 0; s < S.nsp; ++s) total += S.p[s].tstart[t + 1] - S.p[s].tstart[t];
+  const unsigned mbits = *S.emax;
+  if (total == 0 || mbits == 0) {
+    if (tid == 0) S.occ[t] = 0;
+    return;
+  }
+  int ex;
+  frexpf(__uint_as_float(mbits), &ex);  // emax < 2^ex
+  const int k = 30 - ex;
+  for (int q = tid; q < 6 * GC; q += bs) {
+    A[q] = 0x80000000u;
+    A[6 * GC + q] = 0u;
+  }
+  __syncthreads();
+  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  for (int s = 0; s < S.nsp; ++s) {
+    const PartP &P = S.p[s];
+    const bool two = S.sp[s].kind == BP_TWO_BODY;
+    const long long cap = P.cap, ec = S.ecap[s];
+    const int beg = P.tstart[t], end = P.tstart[t + 1];
+    for (long long i = beg + tid; i < end; i += bs) {
+      const int cell = P.cell[i];
+      if (cell < 0) continue;
+      int c[3];
+      unpack_cell(g, cell, c);
+      int d[3] = {0, 0, 0}, d2[3] = {0, 0, 0};
+      float f[3] = {0.0f, 0.0f, 0.0f}, f2[3] = {0.0f, 0.0f, 0.0f};
+      bool bad = false;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        f[a] = P.off[a * cap + i];
+        const float ra = two ? P.r[a * cap + i] : 0.0f;
+        // body positions exactly as the adjoint push places them
+        d[a] = rel_cell<D>(g, a, c[a], T0[a]);
+        bad |= outside_margin<D>(a, d[a]) || !(fabsf(ra * g.idx[a]) < 1.0f);
+        float X = f[a] - ra * g.idx[a];
+        float fl = floorf(X);
+        float fr = X - fl;
+        int di = (int)fl;
+        if (fr >= 1.0f) { fr = 0.0f; di += 1; }
+        d2[a] = d[a] + di;
+        f2[a] = fr;
+      }
+      if (bad) continue;
+      float e[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) e[q] = ldexpf(S.eb[s][q * ec + i], k);
+      scatter_comp<D, 1>(A + 0 * GC, d, f, e[0], d2, f2, e[6], two);
+      scatter_comp<D, 2>(A + 1 * GC, d, f, e[1], d2, f2, e[7], two);
+      scatter_comp<D, 4>(A + 2 * GC, d, f, e[2], d2, f2, e[8], two);
+      scatter_comp<D, 6>(A + 3 * GC, d, f, e[3], d2, f2, e[9], two);
+      scatter_comp<D, 5>(A + 4 * GC, d, f, e[4], d2, f2, e[10], two);
+      scatter_comp<D, 3>(A + 5 * GC, d, f, e[5], d2, f2, e[11], two);
     }
   }
   __syncthreads();
-  // the box to global memory in the compact layout
   constexpr int GN = BX::GCOMP;
-  float *out = A.box + (size_t)t * 6 * GN;
+  float *out = S.box + (size_t)t * 6 * GN;
   for (int q = tid; q < 6 * GN; q += bs) {
     const int cc = q / GN, r = q - cc * GN;
-    out[q] = Acc[cc * GC + BX::gi(r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1))];
+    const int si = cc * GC + BX::gi(r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1));
+    out[q] = ldexpf(__ll2float_rn(fx_value(A + si, 6 * GC)), -k);
   }
-  if (tid == 0) A.occ[t] = 1;
+  if (tid == 0) S.occ[t] = 1;
 }
 
 // adds the per-tile gather-adjoint boxes to the field adjoints, in a fixed
 // order of the covering tiles
-__global__ void k_adj_boxsum(GridP g, const float *box, const unsigned char *occ, float *E0, float *E1, float *E2,
-                             float *B0, float *B1, float *B2) {
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_boxsum(GridP g, const float *box, const unsigned char *occ, float *E0,
+                                                    float *E1, float *E2, float *B0, float *B1, float *B2,
+                                                    unsigned *emax) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *emax = 0u;  // the scatter of this step has read it
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
   float *out[6] = {E0, E1, E2, B0, B1, B2};
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    coords(g, q, c);
-    int tw[3][3], loc[3][3], nc[3];
+  const int *c = C.c;
+  int tw[3][3], loc[3][3], nc[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      nc[a] = 0;
-      if (a >= g.D) {
-        tw[a][0] = 0;
-        loc[a][0] = 0;
-        nc[a] = 1;
-        continue;
-      }
-      int tb = c[a] / g.L[a];
-      for (int dt = -1; dt <= 1; ++dt) {
-        int tu = tb + dt;
-        int l = c[a] - (tu * g.L[a] - g.og[a]);
-        if (l < 0 || l >= g.gb[a]) continue;
-        int tt = tu;
-        if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
-        else if (tu < 0 || tu >= g.nt[a]) continue;
-        tw[a][nc[a]] = tt;
-        loc[a][nc[a]] = l;
-        ++nc[a];
-      }
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = 0;
+    if (a >= D) {
+      tw[a][0] = 0;
+      loc[a][0] = 0;
+      nc[a] = 1;
+      continue;
     }
-    float acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < nc[2]; ++k)
-      for (int j = 0; j < nc[1]; ++j)
-        for (int i = 0; i < nc[0]; ++i) {
-          int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
-          if (!occ[tile]) continue;
-          long long l = loc[0][i] + (long long)g.gb[0] * (loc[1][j] + (long long)g.gb[1] * loc[2][k]);
-          const float *b = box + (size_t)tile * 6 * g.gcells;
+    const int tb = c[a] / g.L[a];
 #pragma unroll
-          for (int cc = 0; cc < 6; ++cc) acc[cc] += b[(size_t)cc * g.gcells + l];
-        }
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) out[cc][q] += acc[cc];
+    for (int dt = -1; dt <= 1; ++dt) {
+      const int tu = tb + dt;
+      const int l = c[a] - (tu * g.L[a] - g.og[a]);
+      if (l < 0 || l >= g.gb[a]) continue;
+      int tt = tu;
+      if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
+      else if (tu < 0 || tu >= g.nt[a]) continue;
+      tw[a][nc[a]] = tt;
+      loc[a][nc[a]] = l;
+      ++nc[a];
+    }
   }
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+  bool any = false;
+  for (int k = 0; k < nc[2]; ++k)
+    for (int j = 0; j < nc[1]; ++j)
+      for (int i = 0; i < nc[0]; ++i) {
+        const int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
+        if (!occ[tile]) continue;
+        any = true;
+        const long long l = loc[0][i] + (long long)g.gb[0] * (loc[1][j] + (long long)g.gb[1] * loc[2][k]);
+        const float *b = box + (size_t)tile * 6 * g.gcells;
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) acc[cc] += b[(size_t)cc * g.gcells + l];
+      }
+  if (!any) return;  // no box covers the cell: nothing to add
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) out[cc][C.q] += acc[cc];
 }
 
 // deterministic FP64 row sums: out[r * ncomp + k] = scale[r] * sum over the
@@ -911,56 +1075,87 @@ void launch_adj_e(const GridP &g, float *G[3], float *H[3], float *lamB[3], floa
     for (int a = 0; a < g.D; ++a)
       if (g.bc[a] == BP_OPEN)
         k_adj_mur<<<blocks_for(4 * (g.ncell / g.n[a]), 256), 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], a, p);
-  k_adj_e<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2],
-                                                    lamJ[0], lamJ[1], lamJ[2]);
+  const int nb = row_blocks(g, 256);
+  if (g.D == 1) k_adj_e<1><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
+  else if (g.D == 2) k_adj_e<2><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
+  else k_adj_e<3><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
 }
 
-void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, cudaStream_t s) {
-  k_adj_b<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h);
+void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float *zero[3], cudaStream_t s) {
+  const int nb = row_blocks(g, 256);
+  float *z0 = zero ? zero[0] : nullptr, *z1 = zero ? zero[1] : nullptr, *z2 = zero ? zero[2] : nullptr;
+  if (g.D == 1) k_adj_b<1><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
+  else if (g.D == 2) k_adj_b<2><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
+  else k_adj_b<3><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
 }
 
 size_t adj_push_smem(int D) {
-  if (D == 1) return sizeof(float) * (12 * Box<1>::GCELLS + 3 * Box<1>::JCELLS);
-  if (D == 2) return sizeof(float) * (12 * Box<2>::GCELLS + 3 * Box<2>::JCELLS);
-  return sizeof(float) * (12 * Box<3>::GCELLS + 3 * Box<3>::JCELLS);
+  if (D == 1) return sizeof(float) * (6 * Box<1>::GCELLS + 3 * Box<1>::JCELLS);
+  if (D == 2) return sizeof(float) * (6 * Box<2>::GCELLS + 3 * Box<2>::JCELLS);
+  return sizeof(float) * (6 * Box<3>::GCELLS + 3 * Box<3>::JCELLS);
+}
+size_t adj_scatter_smem(int D) {
+  if (D == 1) return sizeof(unsigned) * 12 * Box<1>::GCELLS;
+  if (D == 2) return sizeof(unsigned) * 12 * Box<2>::GCELLS;
+  return sizeof(unsigned) * 12 * Box<3>::GCELLS;
+}
+
+template <int D>
+cudaError_t adj_prepare_one() {
+  cudaError_t e = cudaFuncSetAttribute(k_adj_push<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(D));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_scatter_smem(D));
+  return e;
 }
 
 int adj_prepare(int D) {
-  cudaError_t e = cudaSuccess;
-  if (D == 1) e = cudaFuncSetAttribute(k_adj_push<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(1));
-  if (D == 2) e = cudaFuncSetAttribute(k_adj_push<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(2));
-  if (D == 3) e = cudaFuncSetAttribute(k_adj_push<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(3));
+  cudaError_t e = D == 1 ? adj_prepare_one<1>() : (D == 2 ? adj_prepare_one<2>() : adj_prepare_one<3>());
   return e == cudaSuccess ? 0 : -1;
 }
 
-// the particle adjoint of one step, then the sum of its boxes
+template <int D>
+void adj_launch_all(const GridP &g, const AdjArgs &A, const ScatArgs &S, float *lamE[3], float *lamB[3],
+                    unsigned *emax, cudaStream_t s) {
+  k_adj_push<D><<<g.ntiles, 256, adj_push_smem(D), s>>>(g, A);
+  k_adj_scatter<D><<<g.ntiles, 256, adj_scatter_smem(D), s>>>(g, S);
+  k_adj_boxsum<D><<<row_blocks(g, 256), 256, 0, s>>>(g, S.box, S.occ, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1],
+                                                        lamB[2], emax);
+}
+
+// the particle adjoint of one step: reversed push with the position
+// derivatives of the gather (k_adj_push), the field-adjoint scatter
+// (k_adj_scatter), then the sum of the tile boxes into lamE, lamB
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
-                     const long long *cap, const float *const E[3], const float *const B[3],
-                     const float *const lamJ[3], float *box, unsigned char *occ, float *lamE[3], float *lamB[3],
-                     cudaStream_t s) {
+                     float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
+                     const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
+                     float *lamB[3], cudaStream_t s) {
   AdjArgs A;
   memset(&A, 0, sizeof A);
-  A.nsp = nsp;
+  ScatArgs S;
+  memset(&S, 0, sizeof S);
+  A.nsp = S.nsp = nsp;
   for (int k = 0; k < nsp; ++k) {
-    A.sp[k] = sp[k];
-    A.p[k] = p[k];
+    A.sp[k] = S.sp[k] = sp[k];
+    A.p[k] = S.p[k] = p[k];
     A.st[k].xb = xb[k];
     A.st[k].acb = acb[k];
+    A.st[k].eb = eb[k];
     A.st[k].cap = cap[k];
+    S.eb[k] = eb[k];
+    S.ecap[k] = cap[k];
   }
   for (int c = 0; c < 3; ++c) {
     A.E[c] = E[c];
     A.B[c] = B[c];
     A.lamJ[c] = lamJ[c];
   }
-  A.box = box;
-  A.occ = occ;
-  size_t smem = adj_push_smem(g.D);
-  if (g.D == 1) k_adj_push<1><<<g.ntiles, 256, smem, s>>>(g, A);
-  if (g.D == 2) k_adj_push<2><<<g.ntiles, 256, smem, s>>>(g, A);
-  if (g.D == 3) k_adj_push<3><<<g.ntiles, 256, smem, s>>>(g, A);
-  k_adj_boxsum<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g, box, occ, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1],
-                                                         lamB[2]);
+  A.emax = emax;
+  S.emax = emax;
+  S.box = box;
+  S.occ = occ;
+  if (g.D == 1) adj_launch_all<1>(g, A, S, lamE, lamB, emax, s);
+  else if (g.D == 2) adj_launch_all<2>(g, A, S, lamE, lamB, emax, s);
+  else adj_launch_all<3>(g, A, S, lamE, lamB, emax, s);
 }
 
 void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,

@@ -31,57 +31,6 @@ __device__ __forceinline__ int nbound(const GridP &g, int pat, const int c[3], i
 // stagger pattern of E_x, E_y, E_z (bit a: half cell along axis a)
 __device__ __forceinline__ int pat_e(int comp) { return 1 << comp; }
 
-// One thread per cell; a block covers a chunk of one x row (row = y + n1 z),
-// so coordinates come from one division per block and the neighbours are
-// fixed offsets (+-1, +-n0, +-n0 n1) with the periodic wrap applied once.
-struct Cell {
-  long long q;      // linear index
-  int c[3];         // coordinates
-  long long up[3];  // offset to the +1 neighbour along each axis (periodic wrap)
-  long long dn[3];  // offset to the -1 neighbour
-};
-
-template <int D>
-__device__ __forceinline__ bool row_cell(const GridP &g, Cell &C) {
-  const int n0 = g.n[0];
-  const int chunks = (n0 + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int row = (int)blockIdx.x / chunks;
-  const int x = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
-  if (x >= n0) return false;
-  C.c[0] = x;
-  C.c[1] = D >= 2 ? row % g.n[1] : 0;
-  C.c[2] = D >= 3 ? row / g.n[1] : 0;
-  C.q = (long long)row * n0 + x;
-  long long stride = 1;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int n = g.n[a];
-    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
-    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
-    stride *= n;
-  }
-  return true;
-}
-
-// along an open axis a component with half stagger has no value at n-1
-// (exterior), one with node stagger has Mur boundary nodes at 0 and n-1
-template <int D>
-__device__ __forceinline__ bool exterior_c(const GridP &g, int pat, const int c[3]) {
-  bool e = false;
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-    if (g.bc[a] == BP_OPEN && ((pat >> a) & 1)) e |= c[a] == g.n[a] - 1;
-  return e;
-}
-template <int D>
-__device__ __forceinline__ bool mur_node(const GridP &g, int pat, const int c[3]) {
-  bool m = false;
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-    if (g.bc[a] == BP_OPEN && !((pat >> a) & 1)) m |= c[a] == 0 || c[a] == g.n[a] - 1;
-  return m;
-}
-
 // B <- B - h curl E (forward differences to the B locations)
 template <int D>
 __global__ void __launch_bounds__(256) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
@@ -335,11 +284,6 @@ long long frame_floats(const GridP &g) {
   return t;
 }
 
-int row_blocks(const GridP &g, int bs) {
-  const long long rows = g.ncell / g.n[0];
-  return (int)(rows * ((g.n[0] + bs - 1) / bs));
-}
-
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s) {
   const int nb = row_blocks(g, 256);
   if (g.D == 1) k_yee_b<1><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
@@ -372,6 +316,29 @@ void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, co
   if (g.D == 1) k_jsum<1><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
   else if (g.D == 2) k_jsum<2><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
   else k_jsum<3><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+}
+
+// one block row per copy; 16-byte moves when both ends allow, then the tail
+__global__ void k_copy_many(CopyList L) {
+  const int k = blockIdx.y;
+  const long long n = L.words[k];
+  const unsigned *src = static_cast<const unsigned *>(L.src[k]);
+  unsigned *dst = static_cast<unsigned *>(L.dst[k]);
+  const bool v4 = (((size_t)src | (size_t)dst) & 15) == 0;
+  const long long nv = v4 ? n / 4 : 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += stride)
+    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+  for (long long i = 4 * nv + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+void launch_copy_many(const CopyList &L, cudaStream_t s) {
+  if (L.n <= 0) return;
+  long long most = 0;
+  for (int k = 0; k < L.n; ++k) most = most > L.words[k] ? most : L.words[k];
+  long long bx = (most / 4 + 255) / 256;
+  bx = bx < 1 ? 1 : (bx > 152 * 8 ? 152 * 8 : bx);
+  k_copy_many<<<dim3((unsigned)bx, (unsigned)L.n), 256, 0, s>>>(L);
 }
 
 void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,

@@ -27,21 +27,6 @@ namespace {
 // with more general-case particles deposits the rest in place
 __host__ __device__ constexpr int push_qmax(int D) { return D == 2 ? 128 : 64; }
 
-// float -> int64, rounded to nearest even, on the FP32 and integer pipes
-// (the 64-bit conversion runs on the slow FP64 unit).  Adding 1.5 * 2^23 to
-// a float of magnitude below 2^22 rounds it to an integer held in the low
-// mantissa bits; x is split exactly as h 2^22 + l with h = rne(x / 2^22) and
-// |l| <= 2^21, and both parts are rounded that way.  Valid for |x| < 2^44.
-__device__ __forceinline__ long long f2ll_rn(float x) {
-  constexpr float M = 12582912.0f;
-  const float hs = __fadd_rn(x * 2.384185791015625e-07f, M);
-  const float h = __fsub_rn(hs, M);
-  const float l = fmaf(-h, 4194304.0f, x);
-  const int hi = __float_as_int(hs) - 0x4B400000;
-  const int lo = __float_as_int(__fadd_rn(l, M)) - 0x4B400000;
-  return (long long)hi * 4194304LL + (long long)lo;
-}
-
 // add v (already in fixed-point units in the sorted mode) to a current node.
 // Sorted mode: a node's 64-bit fixed-point sum (biased by 2^31, see JBIAS) is
 // kept as a low word (unsigned) and a high word (signed) in two arrays, the
@@ -59,23 +44,7 @@ template <int D, bool DET, bool SKIP0 = true, typename JT>
 __device__ __forceinline__ void jput(JT *p, float v) {
   if constexpr (DET) {
     if (SKIP0 && fabsf(v) <= 0.5f) return;
-    unsigned int lo;
-    int hi;
-    if (fabsf(v) < 2147483648.0f) {
-      const int q = __float2int_rn(v);
-      lo = (unsigned int)q;
-      hi = q >> 31;
-    } else {
-      const long long q = f2ll_rn(v);
-      lo = (unsigned int)(unsigned long long)q;
-      hi = (int)(q >> 32);
-    }
-    const unsigned int old = atomicAdd(p, lo);
-    // hi + carry out of old + lo
-    unsigned int sum;
-    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=r"(sum), "+r"(hi) : "r"(old), "r"(lo));
-    (void)sum;
-    if (hi) atomicAdd(reinterpret_cast<int *>(p + 3 * Box<D>::JCELLS), hi);
+    fx_add(p, 3 * Box<D>::JCELLS, v);
   } else {
     if (SKIP0 && v == 0.0f) return;
     atomicAdd(p, v);

@@ -6,9 +6,8 @@ group ('site') positions.  Both adjoints get the same loss gradient dL/dp
 the FP32 forward's effect on a small residual p - target.  Gradients are
 end-of-run quantities of a run of hundreds of FP32 steps, compared at the
 end-of-run FP32 tolerance, 1e-3 relative to the largest component (FP32
-forward and adjoint, FP64 reductions); the gather transpose adds with FP32
-shared atomics, so reruns agree to rounding, not bit for bit.  The probe
-itself is compared at 1e-5."""
+forward and adjoint, FP64 reductions).  The probe itself is compared at
+1e-5.  Reruns give bit-identical gradients."""
 
 GRAD_TOL = 1e-3
 import numpy as np
@@ -80,6 +79,21 @@ def test_checkpoint_interval_does_not_change_gradients(case):
     for go, gs in out[1:]:
         assert np.abs(go - out[0][0]).max() <= GRAD_TOL * np.abs(out[0][0]).max()
         assert np.abs(gs - out[0][1]).max() <= GRAD_TOL * np.abs(out[0][1]).max()
+
+
+def test_gradients_bit_exact_rerun(case):
+    """The adjoint's only cross-particle sums are the field-adjoint scatter
+    (64-bit fixed point), the tile-box sum and the FP64 reductions (fixed
+    order): two runs give identical gradients."""
+    wl, steps, groups, target, probe_o, *_ = case
+    out = []
+    for _ in range(2):
+        prob = gpu_problem(wl, steps, K=7)
+        prob.run(wl.species[0].omega_b, np.zeros((groups, wl.D)))
+        out.append(prob.gradients(2.0 * (probe_o - target), groups))
+        prob.ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
 
 
 def test_autograd_function(case):
