@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/fwd ratio"
+# DRAM bytes (read + write) of one k_push<3, sorted> launch on this workload,
+# from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass; profiles/k_push_3d_full_traffic.md)
+PUSH_TRAFFIC = 29.0e9
 UNIT = "ion-pushes/s"
 
 
@@ -370,7 +374,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": our_config(n_ion, args.mode, world, args.warmup, args.steps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_push<3,sorted>",
+                     "frac": achieved / hbm, "traffic": PUSH_TRAFFIC, "traffic_unit": "bytes per launch",
+                     "kernel": "k_push<3,sorted>",
                      "peak_source": src, "push_ms_per_launch": push_avg},
         "clocks": clocks,
         "gpu_launches": launches,
