@@ -174,6 +174,16 @@ int bp_read_probe(bp_ctx *ctx, int probe_id, float *dst, int64_t cap, int64_t *n
 int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, double *u1, double *u2,
                       int64_t cap, int64_t *n);
 
+/* Copy the states of the particles with load ids ids[0..n) (load order of
+ * bp_load_particles / bp_set_medium, any order, repeats allowed) to host
+ * arrays in the order of ids: x1, x2, u1, u2 [n][3] as bp_read_particles
+ * (any may be NULL).  found[k] (may be NULL) receives 1 if particle ids[k]
+ * is alive, else 0 (its rows are then 0).  A device search over the species'
+ * particles (no host copy of the whole species); allocates scratch through
+ * the context's allocator; synchronous.  BP_ERR_ARG for a negative id. */
+int bp_read_particles_by_id(bp_ctx *ctx, int species_id, const int64_t *ids, int64_t n, double *x1, double *x2,
+                            double *u1, double *u2, unsigned char *found);
+
 /* Gauss-law residual R = div E - rho at every node, in FP64 on the device
  * (rho deposited in FP64 from the stored FP32 positions with the quadratic
  * shape).  dst holds nz*ny*nx doubles (device pointer if on_device). */

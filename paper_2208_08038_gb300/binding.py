@@ -80,6 +80,7 @@ _SIGS = {
     "bp_write_field": (_i, [_p, _i, _p, _i]),
     "bp_read_probe": (_i, [_p, _i, _p, _i64, C.POINTER(_i64)]),
     "bp_read_particles": (_i, [_p, _i, _p, _p, _p, _p, _i64, C.POINTER(_i64)]),
+    "bp_read_particles_by_id": (_i, [_p, _i, _p, _i64, _p, _p, _p, _p, _p]),
     "bp_residual": (_i, [_p, _p, _i]),
     "bp_residual_noalloc": (_i, [_p, _p]),
     "bp_reset": (_i, [_p]),
@@ -285,6 +286,17 @@ class Context:
                                               C.byref(n)), "bp_read_particles")
         k = min(n.value, cap)
         return x1[:k], x2[:k], u1[:k], u2[:k]
+
+    def read_particles_by_id(self, sid: int, ids):
+        """States of the particles with the given load ids: x1, x2, u1, u2
+        [n][3] and found [n] (bool)."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        n = len(ids)
+        x1, x2, u1, u2 = (np.zeros((n, 3)) for _ in range(4))
+        found = np.zeros(n, dtype=np.uint8)
+        self._check(self._L.bp_read_particles_by_id(self._h, sid, _ptr(ids), n, _ptr(x1), _ptr(x2), _ptr(u1),
+                                                    _ptr(u2), _ptr(found)), "bp_read_particles_by_id")
+        return x1, x2, u1, u2, found.astype(bool)
 
     def residual(self) -> np.ndarray:
         nx, ny, nz = self.n

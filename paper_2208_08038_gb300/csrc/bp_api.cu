@@ -766,6 +766,76 @@ int bp_read_particles(bp_ctx *c, int sid, double *x1, double *x2, double *u1, do
   return BP_OK;
 }
 
+int bp_read_particles_by_id(bp_ctx *c, int sid, const int64_t *ids, int64_t n, double *x1, double *x2,
+                            double *u1, double *u2, unsigned char *found) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size() || n < 0 || (n > 0 && !ids) || n > INT32_MAX) return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (!s.loaded) return fail(c, BP_ERR_STATE, "species not loaded");
+  if (n == 0) return BP_OK;
+  const GridP &g = c->g;
+  const int D = g.D;
+  const bool two = s.sp.kind == BP_TWO_BODY;
+  cudaStream_t st = c->stream;
+  // the ids sorted, with the output row of each
+  std::vector<std::pair<long long, int>> key(n);
+  for (long long k = 0; k < n; ++k) {
+    if (ids[k] < 0 || ids[k] > INT32_MAX) return fail(c, BP_ERR_ARG, "bp_read_particles_by_id: id out of range");
+    key[k] = {ids[k], (int)k};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int> sid_h(n), srow_h(n);
+  for (long long k = 0; k < n; ++k) {
+    sid_h[k] = (int)key[k].first;
+    srow_h[k] = key[k].second;
+  }
+  int *d_sid = (int *)dalloc(c, sizeof(int) * n), *d_srow = (int *)dalloc(c, sizeof(int) * n);
+  int *d_cell = (int *)dalloc(c, sizeof(int) * n);
+  float *d_out = (float *)dalloc(c, sizeof(float) * 12 * n);
+  unsigned char *d_found = (unsigned char *)dalloc(c, n);
+  auto release = [&]() {
+    dfree(c, d_sid);
+    dfree(c, d_srow);
+    dfree(c, d_cell);
+    dfree(c, d_out);
+    dfree(c, d_found);
+  };
+  if (!d_sid || !d_srow || !d_cell || !d_out || !d_found) {
+    release();
+    return fail(c, BP_ERR_OOM, "bp_read_particles_by_id scratch");
+  }
+  cudaMemcpyAsync(d_sid, sid_h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_srow, srow_h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(d_found, 0, n, st);
+  cudaStreamSynchronize(st);
+  int cnt = 0;
+  cudaMemcpy(&cnt, s.p.tstart + g.ntiles, sizeof(int), cudaMemcpyDeviceToHost);
+  launch_pick(s.p, D, two ? 1 : 0, cnt, d_sid, d_srow, (int)n, d_cell, d_out, d_found, st);
+  c->launches++;
+  std::vector<int> cell(n);
+  std::vector<float> raw(12 * (size_t)n);
+  std::vector<unsigned char> fnd(n);
+  cudaMemcpyAsync(cell.data(), d_cell, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(raw.data(), d_out, sizeof(float) * 12 * n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(fnd.data(), d_found, n, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "read particles by id");
+  for (long long k = 0; k < n; ++k) {
+    if (found) found[k] = fnd[k];
+    int cc[3] = {0, 0, 0};
+    if (fnd[k]) unpack_cell(g, cell[k], cc);
+    const float *o = raw.data() + 12 * (size_t)k;
+    for (int a = 0; a < 3; ++a) {
+      const double xa = fnd[k] && a < D ? ((double)cc[a] + (double)o[a]) * g.dxd[a] : 0.0;
+      if (x1) x1[3 * k + a] = xa;
+      if (x2) x2[3 * k + a] = fnd[k] && two ? xa - (double)o[3 + a] : 0.0;
+      if (u1) u1[3 * k + a] = fnd[k] ? (double)o[6 + a] : 0.0;
+      if (u2) u2[3 * k + a] = fnd[k] && two ? (double)o[9 + a] : 0.0;
+    }
+  }
+  return BP_OK;
+}
+
 int bp_residual(bp_ctx *c, double *dst, int on_device) {
   if (!c || !dst) return BP_ERR_ARG;
   const GridP &g = c->g;

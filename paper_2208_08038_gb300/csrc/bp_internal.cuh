@@ -314,6 +314,8 @@ struct SortBufs {
 };
 void launch_sort(const GridP &g, const SpecP &sp, PartP &p, SortBufs &b, int *status, cudaStream_t s);
 void launch_clear_sort_flag(int *status, cudaStream_t s);
+void launch_pick(const PartP &p, int D, int two, long long count, const int *sid, const int *srow, int n,
+                 int *cell_out, float *out, unsigned char *found, cudaStream_t s);
 void launch_set_sort_flag(int *status, cudaStream_t s);
 cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, SortBufs &b, int *status, int *runs,
                             cudaStream_t cap, cudaGraphExec_t *out);

@@ -454,6 +454,41 @@ cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, 
 }
 void launch_set_sort_flag(int *status, cudaStream_t s) { k_set_flag<<<1, 1, 0, s>>>(status); }
 
+// particles whose load id is in the sorted list sid[0..n): copy the raw
+// state of particle slot i to row k of out (k = position of its id in the
+// list): cell, then D offsets, r[3], u1[3], u2[3] as floats
+__global__ void k_pick(PartP p, int D, int two, long long count, const int *sid, const int *srow, int n, int *cell_out,
+                       float *out, unsigned char *found) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = p.cell[i];
+    if (c < 0) continue;
+    const int id = p.id[i];
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sid[mid] < id) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= n || sid[lo] != id) continue;
+    const int k = srow[lo];
+    cell_out[k] = c;
+    float *o = out + (size_t)k * 12;
+    for (int a = 0; a < D; ++a) o[a] = p.off[a * p.cap + i];
+    for (int a = 0; a < 3; ++a) {
+      o[3 + a] = two ? p.r[a * p.cap + i] : 0.0f;
+      o[6 + a] = p.u1[a * p.cap + i];
+      o[9 + a] = two ? p.u2[a * p.cap + i] : 0.0f;
+    }
+    found[k] = 1;
+  }
+}
+
+void launch_pick(const PartP &p, int D, int two, long long count, const int *sid, const int *srow, int n,
+                 int *cell_out, float *out, unsigned char *found, cudaStream_t s) {
+  k_pick<<<blocks_for(count, 256), 256, 0, s>>>(p, D, two, count, sid, srow, n, cell_out, out, found);
+}
+
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
                        uint64_t seed, double sigma, long long first, long long count, cudaStream_t s) {
   uint64_t kpos = sm64_key(seed, 1), kmom = sm64_key(seed, 3);

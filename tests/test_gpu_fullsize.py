@@ -1,0 +1,252 @@
+"""Parity at the full sizes of the configurations.
+
+Where the oracle can run the whole configuration for a few steps (the 2D
+Bragg crystal, 2048^2 cells; the 2D adjoint workload, 1024^2 cells and
+524,288 ions) the fields are compared element by element: relative L2
+<= 1e-5 after one step, <= 1e-3 later.  Where it cannot (the 3D medium of
+264 M ions that the benchmark times, in its launch configuration; the
+ionized crystal with 25 M free electrons), sampled particles are checked one
+by one: the oracle gets the GPU's fields E^n, B^{n-1/2} on the full grid and
+the sampled particles' states, pushes them one step, and the result must
+match the GPU's own step for those particles.  Properties that hold at any
+size complete it: Gauss's law kept by the deposit, bit-identical reruns in
+the sorted mode, and the device-side medium against the host definition.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2208_08038_gb300 import synth
+from _common import field_rel_l2, gpu_from_workload, oracle_from_workload, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2208_08038_gb300 import binding
+    binding.lib()
+
+
+def cfg2_context(wl, mode=1):
+    """The 3D medium exactly as the benchmark builds it (device generator)."""
+    from paper_2208_08038_gb300 import binding as B
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=mode, tile=wl.tile)
+    sp = wl.species[0]
+    m = wl.meta
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    ctx.set_medium(sid, m["lo"], m["hi"], m["ppc"], m["seed"], m["sigma_u"])
+    for L in wl.lasers:
+        ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    n_ion = m["ppc"] * int(np.prod([m["hi"][a] - m["lo"][a] for a in range(3)]))
+    return ctx, sid, n_ion
+
+
+def gauss_change(R, R0, wl):
+    """Largest change of div E - rho away from the antenna planes (a sheet
+    current with a transverse profile charges its own plane) and from open x
+    faces (first-order Mur)."""
+    keep = np.ones(wl.n[0], dtype=bool)
+    for L in wl.lasers:
+        keep[max(0, L.ia - 2):L.ia + 3] = False
+    if wl.bc[0] == 1:
+        keep[:3] = False
+        keep[-3:] = False
+    return float(np.abs((R - R0)[..., keep]).max())
+
+
+def wrap_diff(a, b, L):
+    return (a - b + 0.5 * L) % L - 0.5 * L
+
+
+def sampled_step(wl, ctx, sids, ids_per_species):
+    """One GPU step for the sampled particles against the oracle's push of the
+    same states in the same fields.  Returns per species (gpu, oracle) body
+    states after the step, for the particles alive on both sides."""
+    before = [ctx.read_particles_by_id(sids[k], ids) for k, ids in enumerate(ids_per_species)]
+    F = [ctx.read_field(c) for c in range(6)]
+    ctx.step(1)
+    ctx.sync()
+    after = [ctx.read_particles_by_id(sids[k], ids) for k, ids in enumerate(ids_per_species)]
+    ora = O.Sim(wl.D, wl.n, wl.dx, wl.dt, wl.bc)
+    ora.set_switches(fields_on=True, deposit_on=False)
+    lo = [2.0 if (a < wl.D and wl.bc[a] == 1) else -1e300 for a in range(3)]
+    hi = [wl.n[a] - 2.0 if (a < wl.D and wl.bc[a] == 1) else 1e300 for a in range(3)]
+    ora.set_free_bounds(lo, hi)
+    for c in range(6):
+        ora.field(c)[...] = F[c]
+    out = []
+    for k, sp in enumerate(wl.species):
+        x1, x2, u1, u2, found = before[k]
+        keep = found
+        if isinstance(sp, synth.TwoBody):
+            osid = ora.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+        else:
+            osid = ora.add_free(sp.q, sp.m, sp.w)
+        D = wl.D
+        ora.load(osid, x1[keep, :D], u1[keep])
+        if isinstance(sp, synth.TwoBody):
+            ora.set_bodies(osid, x1[keep], x2[keep], u1[keep], u2[keep])
+        out.append((osid, keep))
+    ora.step(1)
+    res = []
+    for k, sp in enumerate(wl.species):
+        osid, keep = out[k]
+        ox1, ox2, ou1, ou2 = ora.bodies(osid)
+        alive_o = ora.alive(osid).astype(bool)
+        gx1, gx2, gu1, gu2, gfound = after[k]
+        gsel = gfound[keep]
+        both = alive_o & gsel
+        res.append(((gx1[keep][both], gx2[keep][both], gu1[keep][both], gu2[keep][both]),
+                    (ox1[both], ox2[both], ou1[both], ou2[both]), int(both.sum())))
+    ora.close()
+    return res
+
+
+def check_sampled(wl, res, two_body):
+    L = np.array([wl.n[a] * wl.dx[a] if a < wl.D else 1.0 for a in range(3)])
+    dxmin = min(wl.dx[:wl.D])
+    for (g, o, n), two in zip(res, two_body):
+        assert n > 0
+        for b in ((0, 1) if two else (0,)):
+            d = wrap_diff(g[b][:, :wl.D], o[b][:, :wl.D], L[:wl.D])
+            assert np.abs(d).max() < 1e-5 * dxmin, (b, np.abs(d).max())
+        assert rel_l2(g[2], o[2]) < 1e-5
+        if two:
+            assert rel_l2(g[3], o[3]) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# config 2: the 3D medium of the benchmark (264,241,152 ions), sampled
+
+def test_cfg2_full_medium_matches_definition_and_sampled_push():
+    wl = synth.cfg2_neutral_3d(build_particles=False)
+    m = wl.meta
+    ctx, sid, n_ion = cfg2_context(wl)
+    rng = np.random.default_rng(12)
+    # ions of the first 40 x cells (reached by the field within 40 steps) and random ones
+    ext = [m["hi"][a] - m["lo"][a] for a in range(3)]
+    near = []
+    while len(near) < 1500:
+        g = int(rng.integers(0, n_ion))
+        if (g // m["ppc"]) % ext[0] < 40:
+            near.append(g)
+    ids = np.unique(np.concatenate([np.array(near), rng.choice(n_ion, 1500, replace=False)]))
+    # the device generator against the host definition (FP32 storage)
+    x1, x2, u1, u2, found = ctx.read_particles_by_id(sid, ids)
+    assert found.all()
+    xs = np.stack([synth.medium(m["seed"], 3, wl.dx, m["lo"], m["hi"], m["ppc"], m["sigma_u"], first=int(g),
+                                count=1)[0][0] for g in ids[:400]])
+    us = np.stack([synth.medium(m["seed"], 3, wl.dx, m["lo"], m["hi"], m["ppc"], m["sigma_u"], first=int(g),
+                                count=1)[1][0] for g in ids[:400]])
+    assert np.abs(x1[:400] - xs).max() < 1e-6 * wl.dx[0]
+    assert np.array_equal(x1, x2) and np.array_equal(u1, u2)
+    assert np.abs(u1[:400] - us).max() < 1e-6 * np.abs(us).max()
+    ctx.step(40)
+    ctx.sync()
+    res = sampled_step(wl, ctx, [sid], [ids])
+    check_sampled(wl, res, [True])
+    ctx.close()
+
+
+def test_cfg2_full_gauss_and_bit_exact_rerun():
+    """Charge conservation and bit-identical reruns of the benchmark's own
+    launch configuration over its first steps."""
+    wl = synth.cfg2_neutral_3d(build_particles=False)
+    wl.lasers[0].a0 = 0.05  # a stronger pulse: ions near the antenna deposit within the first steps
+    outs = []
+    for rep in range(2):
+        ctx, sid, _ = cfg2_context(wl)
+        if rep == 0:
+            R0 = ctx.residual()
+        ctx.step(12)
+        ctx.sync()
+        if rep == 0:
+            R = ctx.residual()
+            qw = abs(wl.species[0].w) * wl.species[0].Zb
+            assert gauss_change(R, R0, wl) < 1e-4 * qw
+        outs.append(np.stack([ctx.read_field(c) for c in (1, 5, 7)]))
+        ctx.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------
+# config 1: the 2D Bragg crystal on its full 2048^2 grid
+
+def test_cfg1_full_grid_parity():
+    wl = synth.cfg1_bragg_2d()
+    ora, osid, _ = oracle_from_workload(wl, probe_cap=1)
+    gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
+    out = []
+    done = 0
+    for s in (1, 120):
+        ora.step(s - done)
+        gpu.step(s - done)
+        gpu.sync()
+        done = s
+        out.append(field_rel_l2(gpu.fields(), ora.fields()))
+    assert out[0] < 1e-5 and out[1] < 1e-3, out
+    x1o, _, u1o, _ = ora.bodies(osid[0])
+    x1g, _, u1g, _ = gpu.read_particles(gsid[0], len(x1o))
+    assert np.abs(x1g - x1o).max() < 1e-5 * wl.dx[0]
+    gpu.close()
+    ora.close()
+
+
+def test_cfg1_full_run_gauss():
+    """The whole 4000-step run on the GPU keeps Gauss's law (charge
+    conservation of the deposit over the run)."""
+    wl = synth.cfg1_bragg_2d()
+    gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
+    R0 = gpu.residual()
+    gpu.step(wl.steps)
+    gpu.sync()
+    R = gpu.residual()
+    qw = abs(wl.species[0].w) * wl.species[0].Zb
+    assert gauss_change(R, R0, wl) < 1e-3 * qw
+    gpu.close()
+
+
+# ---------------------------------------------------------------------------
+# config 3: the 2D adjoint workload on its full grid (forward)
+
+def test_cfg3_full_forward_parity():
+    wl = synth.cfg3_adjoint_2d()
+    ora, osid, opid = oracle_from_workload(wl, probe_cap=3)
+    gpu, gsid, gpid = gpu_from_workload(wl, probe_cap=3)
+    out = []
+    done = 0
+    for s in (1, 3):
+        ora.step(s - done)
+        gpu.step(s - done)
+        gpu.sync()
+        done = s
+        out.append(field_rel_l2(gpu.fields(), ora.fields()))
+    assert out[0] < 1e-5 and out[1] < 1e-3, out
+    x1o, x2o, u1o, u2o = ora.bodies(osid[0])
+    x1g, x2g, u1g, u2g = gpu.read_particles(gsid[0], len(x1o))
+    assert np.abs(x1g - x1o).max() < 1e-5 * wl.dx[0]
+    assert rel_l2(u2g, u2o) < 1e-5
+    gpu.close()
+    ora.close()
+
+
+# ---------------------------------------------------------------------------
+# config 4: ionized crystal with 25 M free electrons, sampled
+
+def test_cfg4_full_sampled_push_and_gauss():
+    wl = synth.cfg4_ionized_crystal_2d()
+    gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
+    R0 = gpu.residual()
+    gpu.step(30)
+    gpu.sync()
+    R = gpu.residual()
+    qe = max(abs(sp.w * (sp.q if isinstance(sp, synth.Free) else sp.Zb)) for sp in wl.species)
+    assert gauss_change(R, R0, wl) < 1e-3 * qe
+    rng = np.random.default_rng(44)
+    ids = [np.unique(rng.choice(len(sp.x), min(2000, len(sp.x)), replace=False)) for sp in wl.species]
+    res = sampled_step(wl, gpu, gsid, ids)
+    check_sampled(wl, res, [isinstance(sp, synth.TwoBody) for sp in wl.species])
+    gpu.close()
