@@ -210,14 +210,32 @@ __device__ __forceinline__ long long f2ll_rn(float x) {
   return (long long)hi * 4194304LL + (long long)lo;
 }
 
-// Exact fixed-point accumulation with the GPU's native 32-bit shared
-// atomics: a node's 64-bit sum is a low word (unsigned, at lo) and a high
-// word (signed, hoff words later).  The low word takes the low 32 bits of
-// rne(v) and returns its old value; the high word takes the high 32 bits plus
-// the carry out of the low word -- usually zero, so usually one atomic.  The
-// final pair is the exact sum whatever the order of the adds.  (64-bit and
-// FP32 shared atomic adds are compare-and-swap loops on this GPU.)
+// Exact fixed-point accumulation with the GPU's native 32-bit shared atomics
+// (64-bit and FP32 shared atomic adds are compare-and-swap loops on this
+// GPU).  A node's 64-bit sum is kept as two signed 32-bit words, lo and hi
+// (hoff words later): v is split as 2^16 h + r with h = rint(v / 2^16) and
+// |r| <= 2^15, both exact in FP32 for |v| < 2^47, so rne(v) = 2^16 h + rne(r);
+// lo takes rne(r), hi takes h.  Two atomics, no branch, no returned value;
+// the node's value, 2^16 sum(h) + sum(rne(r)), is the exact sum of rne(v)
+// whatever the order, while fewer than 2^16 adds reach one node.
 __device__ __forceinline__ void fx_add(unsigned int *lo, int hoff, float v) {
+  const float h = rintf(v * 1.52587890625e-05f);
+  const float r = fmaf(-h, 65536.0f, v);
+  atomicAdd(reinterpret_cast<int *>(lo), __float2int_rn(r));
+  const int hh = __float2int_rz(h);
+  if (hh) atomicAdd(reinterpret_cast<int *>(lo + hoff), hh);
+}
+// the value of a pair (both words initialised to 0)
+__device__ __forceinline__ long long fx_value(const unsigned int *lo, int hoff) {
+  return (long long)(int)lo[hoff] * 65536LL + (long long)(int)lo[0];
+}
+
+// The same sum with one atomic per add when values are large: the low word
+// (unsigned, initialised to 2^31) takes the low 32 bits of rne(v) and returns
+// its old value; the high word takes the high 32 bits plus the carry out of
+// the low word -- usually zero.  The pair is the exact 64-bit sum (plus the
+// 2^31 bias) whatever the order.
+__device__ __forceinline__ void fx_add_carry(unsigned int *lo, int hoff, float v) {
   unsigned int l;
   int hi;
   if (fabsf(v) < 2147483648.0f) {
@@ -235,8 +253,7 @@ __device__ __forceinline__ void fx_add(unsigned int *lo, int hoff, float v) {
   (void)sum;
   if (hi) atomicAdd(reinterpret_cast<int *>(lo + hoff), hi);
 }
-// the value of a biased pair (low word initialised to 2^31, high word to 0)
-__device__ __forceinline__ long long fx_value(const unsigned int *lo, int hoff) {
+__device__ __forceinline__ long long fx_value_carry(const unsigned int *lo, int hoff) {
   return (long long)(((unsigned long long)lo[hoff] << 32) | lo[0]) - 0x80000000LL;
 }
 

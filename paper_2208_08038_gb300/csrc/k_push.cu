@@ -27,19 +27,10 @@ namespace {
 // with more general-case particles deposits the rest in place
 __host__ __device__ constexpr int push_qmax(int D) { return D == 2 ? 128 : 64; }
 
-// add v (already in fixed-point units in the sorted mode) to a current node.
-// Sorted mode: a node's 64-bit fixed-point sum (biased by 2^31, see JBIAS) is
-// kept as a low word (unsigned) and a high word (signed) in two arrays, the
-// high words 3 * JCELLS entries after the low ones, and updated with the
-// GPU's native 32-bit shared atomics: the low word takes the low 32 bits of
-// the contribution and returns its old value, and the high word takes the
-// high 32 bits plus the carry out of the low word -- usually zero, so usually
-// one atomic.  The final pair is the exact 64-bit sum whatever the order.
-// (64-bit and FP32 shared atomic adds are compare-and-swap loops on this GPU;
-// 32-bit integer adds are single instructions.)
-// Atomic mode: FP32 shared atomics.  Zero contributions are skipped.
-constexpr long long JBIAS = 0x80000000LL;
-
+// add v (already in fixed-point units in the sorted mode) to a current node:
+// sorted mode, the exact fixed-point add fx_add (low words of the box, high
+// words 3 * JCELLS entries later); atomic mode, an FP32 shared atomic.  Zero
+// contributions are skipped where SKIP0.
 template <int D, bool DET, bool SKIP0 = true, typename JT>
 __device__ __forceinline__ void jput(JT *p, float v) {
   if constexpr (DET) {
@@ -550,7 +541,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   tc[2] = t / (g.nt[0] * g.nt[1]);
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
   for (int q = tid; q < 3 * JC; q += bs) {
-    Jsm[q] = DET ? (JT)JBIAS : (JT)0;
+    Jsm[q] = (JT)0;
     if constexpr (DET) Jsm[3 * JC + q] = 0;
   }
   // stage E, B of the tile plus halo (zero outside open faces)
@@ -629,8 +620,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
       const int k = cc * JC + BX::ji(x, y, z);
       const int o = cc * JN + x + BX::J0 * (y + BX::J1 * z);
       if constexpr (DET) {
-        const long long w = (long long)(((unsigned long long)Jsm[3 * JC + k] << 32) | Jsm[k]) - JBIAS;
-        out[o] = __ll2float_rn(w) * A.jinv;  // jinv = 2^-k: one rounding
+        out[o] = __ll2float_rn(fx_value(Jsm + k, 3 * JC)) * A.jinv;  // jinv = 2^-k: one rounding
       } else {
         out[o] = Jsm[k];
       }
