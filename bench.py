@@ -335,7 +335,13 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.step(args.steps)
+    # the last `tail` steps separately (the field front has crossed most of the
+    # medium by then): their push time is reported beside the run's average
+    tail = min(50, args.steps // 5)
+    ctx.step(args.steps - tail)
+    ctx.sync()
+    push_ms_head, push_n_head = ctx.push_time()
+    ctx.step(tail)
     e1.record(stream)
     ctx.sync()
     torch.cuda.synchronize()
@@ -344,6 +350,7 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = ctx.kernel_launches() - launches0
     push_ms, push_n = ctx.push_time()
+    push_tail = (push_ms - push_ms_head) / max(push_n - push_n_head, 1)
     ctx.time_push(False)
     clocks = sampler.stop()
     if dist:
@@ -376,7 +383,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": PUSH_TRAFFIC, "traffic_unit": "bytes per launch",
                      "kernel": "k_push<3,sorted>",
-                     "peak_source": src, "push_ms_per_launch": push_avg},
+                     "peak_source": src, "push_ms_per_launch": push_avg,
+                     "push_ms_per_launch_last_steps": push_tail, "last_steps": tail},
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,

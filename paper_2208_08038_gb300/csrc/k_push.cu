@@ -319,7 +319,7 @@ __device__ __forceinline__ void window_centre(const float *f, const int *d, int 
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
                               const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax,
-                              unsigned &blo, unsigned &bhi) {
+                              unsigned &blo, unsigned &bhi, bool nofield) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   int cell = P.cell[i];
@@ -360,15 +360,25 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     atomicOr(status, ST_DOMAIN);
     return;
   }
+  // A tile whose staged E, B are all zero (ahead of the field front) gathers
+  // exact zeros, so the gather is skipped.  A neutral ion there with r = 0 and
+  // u1 = u2 also keeps its momenta exactly (no internal force at r = 0, Boris
+  // rotation by zero fields), so its kicks are skipped too.
+  bool quiet = nofield && two && sp.qw1 == -sp.qw2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) quiet &= (r[a] == 0.0f) && (u1[a] == u2[a]);
   float E1[3], B1[3], E2[3], B2[3];
-  {
+  if (nofield) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) E1[a] = B1[a] = E2[a] = B2[a] = 0.0f;
+  } else {
     Loc L1, L2;
     make_loc<D>(d, f, L1);
     make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
     gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
   }
   float v1[3], v2[3] = {0.0f, 0.0f, 0.0f};
-  if (two) {
+  if (two && !quiet) {
     // modified Coulomb field (Sec. 2): on the nucleus q2 kappa r / (r^2 + ac^2)^{3/2},
     // on the bound electron -q1 kappa r / (...), r = x1 - x2
     const int pi = P.pidx ? P.pidx[i] : 0;
@@ -382,11 +392,13 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       E2[a] = fmaf(-sp.q1 * s, r[a], E2[a]);
     }
     boris(sp.h2, E2, B2, u2);
+  }
+  if (two) {
     float g2 = rsqrtf(1.0f + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) v2[a] = u2[a] * g2;
   }
-  boris(sp.h1, E1, B1, u1);
+  if (!quiet) boris(sp.h1, E1, B1, u1);
   {
     float g1 = rsqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
 #pragma unroll
@@ -545,6 +557,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     if constexpr (DET) Jsm[3 * JC + q] = 0;
   }
   // stage E, B of the tile plus halo (zero outside open faces)
+  bool nz = false;
   for (int q = tid; q < BX::GCOMP; q += bs) {
     int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     int bidx[3] = {b0, b1, b2};
@@ -563,11 +576,13 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      Gsm[cc * GC + si] = ok ? __ldg(A.E[cc] + gi) : 0.0f;
-      Gsm[(3 + cc) * GC + si] = ok ? __ldg(A.B[cc] + gi) : 0.0f;
+      const float ev = ok ? __ldg(A.E[cc] + gi) : 0.0f, bv = ok ? __ldg(A.B[cc] + gi) : 0.0f;
+      Gsm[cc * GC + si] = ev;
+      Gsm[(3 + cc) * GC + si] = bv;
+      nz |= (ev != 0.0f) || (bv != 0.0f);
     }
   }
-  __syncthreads();
+  const bool nofield = !__syncthreads_or(nz);
   QRec *qrec = reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
   constexpr int QMAX = push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
@@ -582,7 +597,8 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     // consecutive lanes take consecutive (cell-sorted) particles: their
     // gather loads share addresses and their state loads coalesce
     for (long long i = beg + tid; i < end; i += bs)
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi);
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi,
+                                nofield);
     __syncthreads();
     // the deferred general deposits, one row per thread
     const int nitem = min(qn, QMAX) * 2 * IPB;
