@@ -174,6 +174,33 @@ int bp_read_probe(bp_ctx *ctx, int probe_id, float *dst, int64_t cap, int64_t *n
 int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, double *u1, double *u2,
                       int64_t cap, int64_t *n);
 
+/* Load a seeded lattice on the device: per_site ions at each of the n_sites
+ * sites (sites [n_sites][D], FP64, lengths in 1/k0), ion g = site * per_site
+ * + p at its site plus jitter * N(0, 1) per simulated axis (normals D g + a of
+ * the jitter stream of seed) with momentum sigma_u * N(0, 1) per component
+ * (normals 3 g + a of the momentum stream), split into the two bodies like
+ * bp_load_particles; site_param [n_sites] (may be NULL) gives every ion of a
+ * site that parameter index.  Load order = g.  The counter-based generator
+ * is SplitMix64 (uniforms (z >> 11) 2^-53, Box-Muller normals), a published
+ * definition the caller can evaluate on the host.  Synchronous;
+ * BP_ERR_STATE if the species is loaded, BP_ERR_DOMAIN for an ion off the
+ * grid. */
+int bp_set_lattice(bp_ctx *ctx, int species_id, const double *sites, int64_t n_sites, int per_site, double jitter,
+                   uint64_t seed, double sigma_u, const int32_t *site_param);
+
+/* Write the context's state to a file: the step counter, every species'
+ * a_c values and particles (load ids, positions, momenta, parameter
+ * indices, tile offsets), E and B, the status word.  bp_load reads it into a
+ * context created with the same grid description and deposit mode and with
+ * the same species added in the same order (lasers and probes are the loading
+ * context's own); its species must not be loaded yet (bp_reset clears them).
+ * Continuing from a loaded state gives the same fields as continuing the
+ * saved run (bit-identical in the sorted deposit mode).  Host-endian binary;
+ * synchronous.  BP_ERR_IO for an unreadable, truncated or foreign file,
+ * BP_ERR_ARG when the grid or the species differ. */
+int bp_save(bp_ctx *ctx, const char *path);
+int bp_load(bp_ctx *ctx, const char *path);
+
 /* Copy the states of the particles with load ids ids[0..n) (load order of
  * bp_load_particles / bp_set_medium, any order, repeats allowed) to host
  * arrays in the order of ids: x1, x2, u1, u2 [n][3] as bp_read_particles

@@ -81,6 +81,9 @@ _SIGS = {
     "bp_read_probe": (_i, [_p, _i, _p, _i64, C.POINTER(_i64)]),
     "bp_read_particles": (_i, [_p, _i, _p, _p, _p, _p, _i64, C.POINTER(_i64)]),
     "bp_read_particles_by_id": (_i, [_p, _i, _p, _i64, _p, _p, _p, _p, _p]),
+    "bp_set_lattice": (_i, [_p, _i, _p, _i64, _i, C.c_double, C.c_uint64, C.c_double, _p]),
+    "bp_save": (_i, [_p, C.c_char_p]),
+    "bp_load": (_i, [_p, C.c_char_p]),
     "bp_residual": (_i, [_p, _p, _i]),
     "bp_residual_noalloc": (_i, [_p, _p]),
     "bp_reset": (_i, [_p]),
@@ -286,6 +289,24 @@ class Context:
                                               C.byref(n)), "bp_read_particles")
         k = min(n.value, cap)
         return x1[:k], x2[:k], u1[:k], u2[:k]
+
+    def set_lattice(self, sid: int, sites, per_site: int, jitter: float, seed: int, sigma_u: float = 0.0,
+                    site_param=None):
+        """bp_set_lattice: per_site ions at every site with seeded Gaussian jitter."""
+        st = np.ascontiguousarray(sites, dtype=np.float64)
+        if st.ndim == 1:
+            st = st[:, None]
+        sp = None if site_param is None else np.ascontiguousarray(site_param, dtype=np.int32)
+        self._check(self._L.bp_set_lattice(self._h, sid, _ptr(st), st.shape[0], int(per_site), float(jitter),
+                                           int(seed), float(sigma_u), _ptr(sp)), "bp_set_lattice")
+
+    def save(self, path: str):
+        """bp_save: the run's state to a file."""
+        self._check(self._L.bp_save(self._h, os.fsencode(path)), "bp_save")
+
+    def load(self, path: str):
+        """bp_load: a saved state into this context (same grid and species)."""
+        self._check(self._L.bp_load(self._h, os.fsencode(path)), "bp_load")
 
     def read_particles_by_id(self, sid: int, ids):
         """States of the particles with the given load ids: x1, x2, u1, u2

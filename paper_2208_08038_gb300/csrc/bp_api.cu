@@ -347,6 +347,77 @@ int bp_add_species(bp_ctx *c, const bp_species_desc *d, int *id) {
   return BP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// the end of a load: wait for the conversion, check the status word, sort
+int finish_load(bp_ctx *c, Species &s, long long n, void *stage) {
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  dfree(c, stage);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load");
+  int stw = 0;
+  cudaMemcpy(&stw, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (stw & ST_NONFINITE) return fail(c, BP_ERR_NONFINITE, "non-finite position or momentum in the load");
+  if (stw & ST_DOMAIN) return fail(c, BP_ERR_DOMAIN, "a particle lies outside the grid or has a bad param_idx");
+  int rc = initial_sort(c, s, n);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load sort");
+  if (rc) return rc;
+  s.n = n;
+  s.loaded = true;
+  return BP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int bp_set_lattice(bp_ctx *c, int sid, const double *sites, int64_t n_sites, int per_site, double jitter,
+                   uint64_t seed, double sigma_u, const int32_t *site_param) {
+  if (!c || sid < 0 || sid >= (int)c->sp.size() || n_sites < 0 || per_site < 1 || (n_sites > 0 && !sites) ||
+      !(jitter >= 0.0) || !(sigma_u >= 0.0))
+    return BP_ERR_ARG;
+  Species &s = c->sp[sid];
+  if (s.loaded) return fail(c, BP_ERR_STATE, "species %d already loaded", sid);
+  const long long n = n_sites * (long long)per_site;
+  if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
+  const GridP &g = c->g;
+  const int D = g.D;
+  int rc = alloc_particles(c, s, n, site_param != nullptr);
+  if (rc) return rc;
+  s.has_pidx = site_param != nullptr;
+  s.pidx_host.assign((size_t)n, 0);
+  if (site_param)
+    for (long long q = 0; q < n; ++q) s.pidx_host[q] = site_param[q / per_site];
+  cudaStream_t st = c->stream;
+  const long long chunk = std::min<long long>(std::max<long long>(n, 1), 1LL << 25);
+  const size_t rows = (size_t)chunk * (sizeof(double) * (D + 3) + sizeof(int));
+  const size_t ns = (size_t)std::max<int64_t>(n_sites, 1);
+  char *stage = (char *)dalloc(c, rows + (sizeof(double) * D + sizeof(int)) * ns);
+  if (!stage) return fail(c, BP_ERR_OOM, "lattice staging");
+  double *sx = (double *)stage;
+  double *su = sx + (size_t)chunk * D;
+  int *sp_ = (int *)(su + (size_t)chunk * 3);
+  double *dsites = (double *)(stage + rows);
+  int *dparam = (int *)(dsites + (size_t)D * ns);
+  int zero = 0;
+  cudaMemcpyAsync(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (n_sites > 0) cudaMemcpyAsync(dsites, sites, sizeof(double) * D * n_sites, cudaMemcpyHostToDevice, st);
+  if (site_param && n_sites > 0) cudaMemcpyAsync(dparam, site_param, sizeof(int) * n_sites, cudaMemcpyHostToDevice, st);
+  for (long long b = 0; b < n; b += chunk) {
+    long long k = std::min(chunk, n - b);
+    launch_gen_lattice(D, dsites, per_site, jitter, seed, sigma_u, site_param ? dparam : nullptr, b, k, sx, su,
+                       site_param ? sp_ : nullptr, st);
+    launch_load_convert(g, s.sp, s.p, sx, su, site_param ? sp_ : nullptr, b, k, c->status, st);
+    c->launches += 2;
+  }
+  if ((rc = check_launch(c, "lattice generation"))) {
+    dfree(c, stage);
+    return rc;
+  }
+  return finish_load(c, s, n, stage);
+}
+
 int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, const int32_t *pidx, int64_t n) {
   if (!c || sid < 0 || sid >= (int)c->sp.size() || n < 0 || (n > 0 && !x)) return BP_ERR_ARG;
   Species &s = c->sp[sid];
@@ -377,21 +448,11 @@ int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, cons
     launch_load_convert(g, s.sp, s.p, sx, u ? su : nullptr, pidx ? sp_ : nullptr, b, k, c->status, st);
     c->launches++;
   }
-  if ((rc = check_launch(c, "load conversion"))) return rc;
-  cudaError_t e = cudaStreamSynchronize(st);
-  dfree(c, stage);
-  if (e != cudaSuccess) return cuda_fail(c, e, "load");
-  int stw = 0;
-  cudaMemcpy(&stw, c->status, sizeof(int), cudaMemcpyDeviceToHost);
-  if (stw & ST_NONFINITE) return fail(c, BP_ERR_NONFINITE, "non-finite position or momentum in the load");
-  if (stw & ST_DOMAIN) return fail(c, BP_ERR_DOMAIN, "a particle lies outside the grid or has a bad param_idx");
-  rc = initial_sort(c, s, n);
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(c, e, "load sort");
-  if (rc) return rc;
-  s.n = n;
-  s.loaded = true;
-  return BP_OK;
+  if ((rc = check_launch(c, "load conversion"))) {
+    dfree(c, stage);
+    return rc;
+  }
+  return finish_load(c, s, n, stage);
 }
 
 int bp_set_medium(bp_ctx *c, int sid, const int64_t lo[3], const int64_t hi[3], int ppc, uint64_t seed,
@@ -834,6 +895,168 @@ int bp_read_particles_by_id(bp_ctx *c, int sid, const int64_t *ids, int64_t n, d
     }
   }
   return BP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state files: header, per species (parameters, a_c, live particle arrays,
+// tile offsets, parameter index per load id), E and B, the status word
+
+}  // extern "C"
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, D, n[3], bc[3], L[3], det, nsp;
+  double dx[3], dt;
+  int64_t step;
+};
+struct StateSpecies {
+  int32_t kind, loaded, has_pidx, nac, dim, pad;
+  double q1, m1, q2, m2, w;
+  int64_t n, cnt, pcap;
+};
+const char kStateMagic[8] = {'B', 'P', 'S', 'T', 'A', 'T', 'E', '1'};
+
+bool wr(FILE *f, const void *p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+bool rd(FILE *f, void *p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
+bool wr_dev(FILE *f, const void *dev, size_t bytes) {
+  std::vector<char> h(bytes);
+  if (bytes && cudaMemcpy(h.data(), dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  return wr(f, h.data(), bytes);
+}
+bool rd_dev(FILE *f, void *dev, size_t bytes) {
+  std::vector<char> h(bytes);
+  if (!rd(f, h.data(), bytes)) return false;
+  return bytes == 0 || cudaMemcpy(dev, h.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+int bp_save(bp_ctx *c, const char *path) {
+  if (!c || !path) return BP_ERR_ARG;
+  const GridP &g = c->g;
+  cudaError_t e0 = cudaStreamSynchronize(c->stream);
+  if (e0 != cudaSuccess) return cuda_fail(c, e0, "save");
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(c, BP_ERR_IO, "bp_save: cannot open %s", path);
+  StateHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.D = g.D;
+  h.det = c->det;
+  h.nsp = (int)c->sp.size();
+  for (int a = 0; a < 3; ++a) {
+    h.n[a] = g.n[a];
+    h.bc[a] = g.bc[a];
+    h.L[a] = g.L[a];
+    h.dx[a] = g.dxd[a];
+  }
+  h.dt = g.dtd;
+  h.step = c->step;
+  bool ok = wr(f, &h, sizeof h);
+  const int D = g.D;
+  for (auto &s : c->sp) {
+    StateSpecies q;
+    memset(&q, 0, sizeof q);
+    q.kind = s.sp.kind;
+    q.loaded = s.loaded;
+    q.has_pidx = s.has_pidx;
+    q.nac = s.sp.nac;
+    q.dim = D;
+    q.q1 = s.sp.q1d;
+    q.m1 = s.sp.m1d;
+    q.q2 = s.sp.q2d;
+    q.m2 = s.sp.m2d;
+    q.w = s.sp.wd;
+    q.n = s.n;
+    q.pcap = s.p.cap;
+    int cnt = 0;
+    if (s.loaded) cudaMemcpy(&cnt, s.p.tstart + g.ntiles, sizeof(int), cudaMemcpyDeviceToHost);
+    q.cnt = cnt;
+    ok = ok && wr(f, &q, sizeof q);
+    if (s.sp.nac > 0 && s.ac_dev) ok = ok && wr_dev(f, s.ac_dev, sizeof(float) * s.sp.nac);
+    if (!s.loaded) continue;
+    const bool two = s.sp.kind == BP_TWO_BODY;
+    const long long pc = s.p.cap;
+    ok = ok && wr_dev(f, s.p.cell, sizeof(int) * cnt) && wr_dev(f, s.p.id, sizeof(int) * cnt);
+    for (int a = 0; a < D; ++a) ok = ok && wr_dev(f, s.p.off + a * pc, sizeof(float) * cnt);
+    for (int a = 0; a < 3; ++a) ok = ok && wr_dev(f, s.p.u1 + a * pc, sizeof(float) * cnt);
+    if (two)
+      for (int a = 0; a < 3; ++a)
+        ok = ok && wr_dev(f, s.p.r + a * pc, sizeof(float) * cnt) && wr_dev(f, s.p.u2 + a * pc, sizeof(float) * cnt);
+    if (s.p.pidx) ok = ok && wr_dev(f, s.p.pidx, sizeof(int) * cnt);
+    ok = ok && wr_dev(f, s.p.tstart, sizeof(int) * (g.ntiles + 1));
+    ok = ok && wr(f, s.pidx_host.data(), sizeof(int) * s.pidx_host.size());
+  }
+  for (int k = 0; k < 6; ++k) ok = ok && wr_dev(f, c->F[k], sizeof(float) * g.ncell);
+  ok = ok && wr_dev(f, c->status, sizeof(int));
+  ok = (fclose(f) == 0) && ok;
+  return ok ? BP_OK : fail(c, BP_ERR_IO, "bp_save: write to %s failed", path);
+}
+
+int bp_load(bp_ctx *c, const char *path) {
+  if (!c || !path) return BP_ERR_ARG;
+  const GridP &g = c->g;
+  cudaError_t e0 = cudaStreamSynchronize(c->stream);
+  if (e0 != cudaSuccess) return cuda_fail(c, e0, "load");
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(c, BP_ERR_IO, "bp_load: cannot open %s", path);
+  auto bad = [&](int code, const char *why) {
+    fclose(f);
+    return fail(c, code, "bp_load: %s (%s)", why, path);
+  };
+  StateHeader h;
+  if (!rd(f, &h, sizeof h) || memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    return bad(BP_ERR_IO, "not a state file of this library");
+  bool same = h.D == g.D && h.det == c->det && h.nsp == (int)c->sp.size() && h.dt == g.dtd;
+  for (int a = 0; a < 3; ++a)
+    same = same && h.n[a] == g.n[a] && h.bc[a] == g.bc[a] && h.L[a] == g.L[a] && h.dx[a] == g.dxd[a];
+  if (!same) return bad(BP_ERR_ARG, "grid, deposit mode or species count differ from the context's");
+  const int D = g.D;
+  for (auto &s : c->sp) {
+    StateSpecies q;
+    if (!rd(f, &q, sizeof q)) return bad(BP_ERR_IO, "truncated species record");
+    if (q.kind != s.sp.kind || q.nac != s.sp.nac || q.dim != D || q.q1 != s.sp.q1d || q.m1 != s.sp.m1d ||
+        q.q2 != s.sp.q2d || q.m2 != s.sp.m2d || q.w != s.sp.wd)
+      return bad(BP_ERR_ARG, "species differ from the context's");
+    if (q.nac > 0 && s.ac_dev && !rd_dev(f, s.ac_dev, sizeof(float) * q.nac)) return bad(BP_ERR_IO, "a_c");
+    if (!q.loaded) continue;
+    if (s.loaded) return bad(BP_ERR_STATE, "a species of the context is already loaded (bp_reset first)");
+    if (q.cnt < 0 || q.n < 0 || q.cnt > q.pcap) return bad(BP_ERR_IO, "bad particle counts");
+    const bool two = s.sp.kind == BP_TWO_BODY;
+    if (alloc_particles(c, s, std::max<long long>(q.pcap, 1), q.has_pidx != 0)) {
+      fclose(f);
+      return BP_ERR_OOM;
+    }
+    const long long pc = s.p.cap, cnt = q.cnt;
+    bool ok = rd_dev(f, s.p.cell, sizeof(int) * cnt) && rd_dev(f, s.p.id, sizeof(int) * cnt);
+    for (int a = 0; a < D; ++a) ok = ok && rd_dev(f, s.p.off + a * pc, sizeof(float) * cnt);
+    for (int a = 0; a < 3; ++a) ok = ok && rd_dev(f, s.p.u1 + a * pc, sizeof(float) * cnt);
+    if (two)
+      for (int a = 0; a < 3; ++a)
+        ok = ok && rd_dev(f, s.p.r + a * pc, sizeof(float) * cnt) && rd_dev(f, s.p.u2 + a * pc, sizeof(float) * cnt);
+    if (q.has_pidx) ok = ok && rd_dev(f, s.p.pidx, sizeof(int) * cnt);
+    ok = ok && rd_dev(f, s.p.tstart, sizeof(int) * (g.ntiles + 1));
+    s.pidx_host.assign((size_t)q.n, 0);
+    ok = ok && rd(f, s.pidx_host.data(), sizeof(int) * (size_t)q.n);
+    if (!ok) return bad(BP_ERR_IO, "truncated particle arrays");
+    s.n = q.n;
+    s.has_pidx = q.has_pidx != 0;
+    s.loaded = true;
+  }
+  bool ok = true;
+  for (int k = 0; k < 6; ++k) ok = ok && rd_dev(f, c->F[k], sizeof(float) * g.ncell);
+  ok = ok && rd_dev(f, c->status, sizeof(int));
+  fclose(f);
+  if (!ok) return fail(c, BP_ERR_IO, "bp_load: truncated fields (%s)", path);
+  for (int k = 6; k < 9; ++k) cudaMemset(c->F[k], 0, sizeof(float) * g.ncell);
+  c->step = h.step;
+  c->sort_dirty = true;
+  update_jscale(c);
+  cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "load");
 }
 
 int bp_residual(bp_ctx *c, double *dst, int on_device) {

@@ -331,6 +331,9 @@ struct SortBufs {
 };
 void launch_sort(const GridP &g, const SpecP &sp, PartP &p, SortBufs &b, int *status, cudaStream_t s);
 void launch_clear_sort_flag(int *status, cudaStream_t s);
+void launch_gen_lattice(int D, const double *sites, int per_site, double jitter, uint64_t seed, double sigma,
+                        const int *site_param, long long first, long long count, double *x, double *u, int *pidx,
+                        cudaStream_t s);
 void launch_pick(const PartP &p, int D, int two, long long count, const int *sid, const int *srow, int n,
                  int *cell_out, float *out, unsigned char *found, cudaStream_t s);
 void launch_set_sort_flag(int *status, cudaStream_t s);

@@ -489,6 +489,36 @@ void launch_pick(const PartP &p, int D, int two, long long count, const int *sid
   k_pick<<<blocks_for(count, 256), 256, 0, s>>>(p, D, two, count, sid, srow, n, cell_out, out, found);
 }
 
+// seeded lattice: ion g = site * per_site + p sits at its site plus a
+// Gaussian jitter (normals D g + a of the jitter stream) and takes momenta
+// sigma N (normals 3 g + a of the momentum stream); written as FP64 position
+// and momentum rows for the load conversion
+__device__ __forceinline__ double sm64_normal(uint64_t key, uint64_t c) {
+  const double u1 = sm64_uniform(key, 2 * c), u2 = sm64_uniform(key, 2 * c + 1);
+  return sqrt(-2.0 * log(1.0 - u1)) * cos(6.283185307179586476925 * u2);
+}
+
+__global__ void k_gen_lattice(int D, const double *sites, int per_site, double jitter, uint64_t kj, uint64_t km,
+                              double sigma, const int *site_param, long long first, long long count, double *x,
+                              double *u, int *pidx) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long gi = first + q, site = gi / per_site;
+    for (int a = 0; a < D; ++a)
+      x[q * D + a] = sites[site * D + a] + (jitter > 0.0 ? jitter * sm64_normal(kj, (uint64_t)(D * gi + a)) : 0.0);
+    for (int a = 0; a < 3; ++a) u[q * 3 + a] = sigma > 0.0 ? sigma * sm64_normal(km, (uint64_t)(3 * gi + a)) : 0.0;
+    if (pidx) pidx[q] = site_param[site];
+  }
+}
+
+void launch_gen_lattice(int D, const double *sites, int per_site, double jitter, uint64_t seed, double sigma,
+                        const int *site_param, long long first, long long count, double *x, double *u, int *pidx,
+                        cudaStream_t s) {
+  k_gen_lattice<<<blocks_for(count, 256), 256, 0, s>>>(D, sites, per_site, jitter, sm64_key(seed, 2),
+                                                        sm64_key(seed, 3), sigma, site_param, first, count, x, u,
+                                                        pidx);
+}
+
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
                        uint64_t seed, double sigma, long long first, long long count, cudaStream_t s) {
   uint64_t kpos = sm64_key(seed, 1), kmom = sm64_key(seed, 3);

@@ -1,0 +1,122 @@
+"""GPU tests of the library's lattice generator and state files:
+bp_set_lattice against the host definition of the seeded lattice, and
+bp_save / bp_load continuing a run bit for bit."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2208_08038_gb300 import synth
+from _common import field_rel_l2, gpu_from_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2208_08038_gb300 import binding
+    binding.lib()
+
+
+def bragg_small():
+    return synth.cfg1_bragg_2d(seed=5, n=256, cells_per_lambda=16, sites=(6, 6), waist_lambda=3.0,
+                               fwhm_lambda=3.0, nb=0.05, steps=60)
+
+
+def test_set_lattice_matches_host_definition():
+    """The device lattice (positions with seeded jitter, thermal momenta, one
+    parameter index per site) equals synth.lattice's, ion by ion."""
+    from paper_2208_08038_gb300 import binding as B
+    wl = bragg_small()
+    sp = wl.species[0]
+    m = wl.meta
+    sites = synth.square_lattice(m["origin"], m["d"], m["sites"])
+    per_site, jitter, sigma = 4, 0.05 * m["d"], 2e-3
+    x_h, u_h = synth.lattice(77, sites, per_site, jitter, sigma)
+    param = (np.arange(len(sites)) % 3).astype(np.int32)
+    omega = np.array([3.0, 3.5, 4.0])
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, omega)
+    ctx.set_lattice(sid, sites, per_site, jitter, 77, sigma, param)
+    x1, x2, u1, u2 = ctx.read_particles(sid, len(x_h))
+    assert len(x1) == len(x_h)
+    assert np.abs(x1[:, :2] - x_h).max() < 1e-6 * wl.dx[0]
+    assert np.array_equal(x1, x2)
+    assert np.abs(u1 - u_h).max() < 1e-6 * np.abs(u_h).max()
+    # the same run from the device lattice and from the host arrays
+    ctx2 = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    sid2 = ctx2.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, omega)
+    ctx2.load_particles(sid2, x_h, u_h, np.repeat(param, per_site))
+    for c in (ctx, ctx2):
+        for L in wl.lasers:
+            c.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+        c.step(40)
+        c.sync()
+    assert field_rel_l2(ctx.fields(), ctx2.fields(), comps=range(9)) < 1e-6
+    ctx.close()
+    ctx2.close()
+
+
+def small_periodic_3d():
+    wl = synth.cfg2_neutral_3d(seed=9, steps=30, n=(32, 16, 16), ppc=4, sigma_u=5e-2, margin=2)
+    wl.bc = (0, 0, 0)
+    wl.lasers[0].waist = 0.5 * synth.LAMBDA0
+    wl.lasers[0].a0 = 0.05
+    return wl
+
+
+def test_save_load_continues_bit_exact(tmp_path):
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    path = os.path.join(tmp_path, "state.bp")
+    a, sa, _ = gpu_from_workload(wl, deposit_mode=1)
+    a.step(12)
+    a.save(path)
+    a.step(10)
+    a.sync()
+    fa = a.fields()
+    pa = a.read_particles(sa[0], len(wl.species[0].x))
+    # a fresh context with the same grid and species, not loaded
+    sp = wl.species[0]
+    b = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    sb = b.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    for L in wl.lasers:
+        b.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    b.load(path)
+    b.step(10)
+    b.sync()
+    assert np.array_equal(fa, b.fields())
+    pb = b.read_particles(sb, len(sp.x))
+    for qa, qb in zip(pa, pb):
+        assert np.array_equal(qa, qb)
+    a.close()
+    b.close()
+
+
+def test_load_rejects_other_grids_and_foreign_files(tmp_path):
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    path = os.path.join(tmp_path, "state.bp")
+    a, _, _ = gpu_from_workload(wl, deposit_mode=1)
+    a.save(path)
+    sp = wl.species[0]
+    other = B.Context(wl.D, (64, 16, 16), wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    other.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    with pytest.raises(B.BPError) as e:
+        other.load(path)
+    assert e.value.code == B.BP_ERR_ARG
+    junk = os.path.join(tmp_path, "junk.bp")
+    with open(junk, "wb") as f:
+        f.write(b"not a state file at all" * 10)
+    same = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    same.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    with pytest.raises(B.BPError) as e:
+        same.load(junk)
+    assert e.value.code == B.BP_ERR_IO
+    with pytest.raises(B.BPError) as e:
+        same.load(os.path.join(tmp_path, "missing.bp"))
+    assert e.value.code == B.BP_ERR_IO
+    for c in (a, other, same):
+        c.close()

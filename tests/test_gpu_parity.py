@@ -203,7 +203,7 @@ def test_errors_are_status_codes():
         B.Context(1, (64,), (0.1,), 0.2, (1,))
     assert e.value.code == B.BP_ERR_CFL
     with pytest.raises(B.BPError) as e:
-        B.Context(2, (60, 64), (0.1, 0.1), 0.05, (1, 0))  # 60 is not a multiple of the 32-cell tile
+        B.Context(2, (60, 64), (0.1, 0.1), 0.05, (1, 0))  # 60 is not a multiple of the 16-cell tile
     assert e.value.code == B.BP_ERR_ARG
     with pytest.raises(B.BPError) as e:
         B.Context(1, (64,), (0.1,), 0.09, (1,), tile=(32,))  # tiles are fixed per dimension
