@@ -379,3 +379,181 @@ def test_continuity_full_step(D):
     R = s.residual()
     assert np.abs(R - R0).max() < 1e-12 * rmax
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# Pin (a'): a two-body ion driven by a uniform field E0 cos(w t).  Sec. 3.1
+# gives the steady-state displacements of nucleus and bound electron,
+#   r1 = [-qc/(mc w^2) + m2/(m1+m2) qr/(mr (wc^2 - w^2))] E,
+#   r2 = [-qc/(mc w^2) - m1/(m1+m2) qr/(mr (wc^2 - w^2))] E,
+# qr = (q1 m2 - q2 m1)/(m1+m2), mr = m1 m2/(m1+m2).  The leapfrog (x and E
+# at t_n) has the same particular solution with w replaced by
+# (2/dt) sin(w dt/2); the free oscillation at the discrete natural frequency
+# and the centre of mass's uniform drift are fitted out.
+
+@pytest.mark.parametrize("Zb,qc", [(1.0, 0.0), (10.0, 5.0)])
+def test_driven_ion_steady_state_amplitudes(Zb, qc):
+    # a light nucleus (mass 100 m_e) so that both bodies move by far more than the
+    # rounding of their positions; the formula holds for any two masses
+    dt, w, steps, wb = 0.05, 1.0, 2000, 3.0
+    s = O.Sim(1, [16], [1.0], dt, [O.PERIODIC])
+    s.set_switches(fields_on=False, deposit_on=False)
+    sid = s.add_two_body(Zb, qc, 100.0, 1.0, 12.4e-9, [wb])
+    s.load(sid, np.array([[0.5]]), np.zeros((1, 3)))
+    info = s.species_info(sid)
+    q1, m1, q2, m2 = info["q1"], info["m1"], info["q2"], info["m2"]
+    mc, qcc = m1 + m2, q1 + q2
+    mr, qr = m1 * m2 / mc, (q1 * m2 - q2 * m1) / mc
+    # relative amplitude 1e-4 a_c: the internal force stays linear to 1e-8
+    E0 = 1e-4 * s.ac(sid) * mr * (wb ** 2 - w ** 2) / abs(qr)
+    x1s, x2s = [], []
+    for n in range(steps):
+        s.field(0)[...] = E0 * math.cos(w * n * dt)   # uniform E_x at t_n
+        s.step(1)
+        a, b, _, _ = s.bodies(sid)
+        x1s.append(a[0, 0])
+        x2s.append(b[0, 0])
+    s.close()
+    t = np.arange(1, steps + 1) * dt
+    wd = 2.0 / dt * math.sin(w * dt / 2)                       # driving frequency seen by the leapfrog
+    wn = math.acos(1.0 - (wb * dt) ** 2 / 2) / dt               # discrete free frequency
+    A = np.stack([np.ones_like(t), t, np.cos(w * t), np.sin(w * t), np.cos(wn * t), np.sin(wn * t)], axis=1)
+    want1 = (-qcc / (mc * wd ** 2) + m2 / mc * qr / (mr * (wb ** 2 - wd ** 2))) * E0
+    want2 = (-qcc / (mc * wd ** 2) - m1 / mc * qr / (mr * (wb ** 2 - wd ** 2))) * E0
+    for xs, want in ((x1s, want1), (x2s, want2)):
+        coef, *_ = np.linalg.lstsq(A, np.array(xs), rcond=None)
+        assert abs(coef[2] / want - 1) < 1e-6, (coef[2], want)
+        assert abs(coef[3]) < 1e-6 * abs(want)        # in phase with the drive
+
+
+# ---------------------------------------------------------------------------
+# Pin (g): one whole step of the oracle against a second, hand-expanded FP64
+# step written here with no stencil logic: every gather and deposit sums the
+# quadratic B-spline over all nodes of a periodic 8^3 grid (minimum-image
+# distances), the running sums of the current start outside the support.
+
+def _S(xi):
+    a = np.abs(xi)
+    return np.where(a <= 0.5, 0.75 - xi * xi, np.where(a < 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+
+
+def _wrap(d, n):
+    return (d + 0.5 * n) % n - 0.5 * n
+
+
+def _weights(X, stag, n):
+    """Per-axis weight vectors over all nodes (node a-index i sits at i + stag[a])."""
+    return [_S(_wrap(X[a] - (np.arange(n[a]) + stag[a]), n[a])) for a in range(3)]
+
+
+def _gather(F, X, stag, n):
+    wx, wy, wz = _weights(X, stag, n)
+    return float(np.einsum("k,j,i,kji->", wz, wy, wx, F))
+
+
+def _curl_fwd(F, d):   # (dFz/dy - dFy/dz, ...) at the B locations, arrays [z][y][x]
+    Fx, Fy, Fz = F
+    dy = lambda A: (np.roll(A, -1, 1) - A) / d[1]
+    dz = lambda A: (np.roll(A, -1, 0) - A) / d[2]
+    dxx = lambda A: (np.roll(A, -1, 2) - A) / d[0]
+    return [dy(Fz) - dz(Fy), dz(Fx) - dxx(Fz), dxx(Fy) - dy(Fx)]
+
+
+def _curl_bwd(F, d):
+    Fx, Fy, Fz = F
+    dy = lambda A: (A - np.roll(A, 1, 1)) / d[1]
+    dz = lambda A: (A - np.roll(A, 1, 0)) / d[2]
+    dxx = lambda A: (A - np.roll(A, 1, 2)) / d[0]
+    return [dy(Fz) - dz(Fy), dz(Fx) - dxx(Fz), dxx(Fy) - dy(Fx)]
+
+
+def _boris(h, E, B, u):
+    um = u + h * E
+    g = math.sqrt(1.0 + um @ um)
+    t = h * B / g
+    s = 2.0 * t / (1.0 + t @ t)
+    up = um + np.cross(um + np.cross(um, t), s)
+    return up + h * E
+
+
+def _reference_step(E, B, bodies, sp, d, dt, n):
+    q1, m1, q2, m2, w, kappa, ac = sp
+    B = [b - 0.5 * dt * c for b, c in zip(B, _curl_fwd(E, d))]
+    stE = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5)]
+    stB = [(0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+    J = [np.zeros(E[0].shape) for _ in range(3)]
+    out = []
+    for x1, x2, u1, u2 in bodies:
+        X1, X2 = x1 / d, x2 / d
+        E1 = np.array([_gather(E[c], X1, stE[c], n) for c in range(3)])
+        B1 = np.array([_gather(B[c], X1, stB[c], n) for c in range(3)])
+        E2 = np.array([_gather(E[c], X2, stE[c], n) for c in range(3)])
+        B2 = np.array([_gather(B[c], X2, stB[c], n) for c in range(3)])
+        r = _wrap(x1 - x2, d * np.array(n))
+        f = kappa * r / (r @ r + ac * ac) ** 1.5
+        E1, E2 = E1 + q2 * f, E2 - q1 * f
+        v1n = _boris(q1 * dt / (2 * m1), E1, B1, u1)
+        v2n = _boris(q2 * dt / (2 * m2), E2, B2, u2)
+        y1 = x1 + dt * v1n / math.sqrt(1.0 + v1n @ v1n)
+        y2 = x2 + dt * v2n / math.sqrt(1.0 + v2n @ v2n)
+        for q, X0, Y in ((q1, X1, y1 / d), (q2, X2, y2 / d)):
+            S0 = _weights(X0, (0, 0, 0), n)
+            S1 = _weights(Y, (0, 0, 0), n)
+            DS = [S1[a] - S0[a] for a in range(3)]
+            for a in range(3):
+                b, c = [k for k in range(3) if k != a]
+                fac = (np.outer(S0[c], S0[b]) + 0.5 * np.outer(DS[c], S0[b]) + 0.5 * np.outer(S0[c], DS[b])
+                       + np.outer(DS[c], DS[b]) / 3.0)          # [axis c][axis b]
+                Wa = DS[a]
+                start = int((np.floor(X0[a] + 0.5) + 3) % n[a])  # a node outside the support
+                run = np.roll(np.cumsum(np.roll(Wa, -start)), start)
+                contrib = -q * w * (d[a] / dt) * run            # along axis a
+                # assemble the 3D array [z][y][x] from (a, b, c)
+                arr = np.einsum("m,cb->mcb", contrib, fac)      # [a][c][b]
+                axes = {a: 0, c: 1, b: 2}
+                J[a] += np.transpose(arr, [axes[2], axes[1], axes[0]])
+        out.append((y1, y2, v1n, v2n))
+    B = [b - 0.5 * dt * c for b, c in zip(B, _curl_fwd(E, d))]
+    E = [e + dt * (c - j) for e, c, j in zip(E, _curl_bwd(B, d), J)]
+    return E, B, J, out
+
+
+def test_whole_step_against_hand_expanded_reference():
+    n = (8, 8, 8)
+    d = np.array([0.5, 0.6, 0.7])
+    dt = 0.2
+    rng = np.random.default_rng(8)
+    s = O.Sim(3, n, d, dt, [O.PERIODIC] * 3)
+    sid = s.add_two_body(3.0, 2.0, synth.M_AU, 0.7, 12.4e-9, [3.0])
+    xs = rng.uniform(0, 1, (2, 3)) * d * np.array(n)
+    s.load(sid, xs, np.zeros((2, 3)))
+    info = s.species_info(sid)
+    ac = s.ac(sid)
+    r = rng.normal(0, 0.3, (2, 3)) * d
+    x1, x2 = xs, (xs - r) % (d * np.array(n))
+    u1 = rng.normal(0, 0.3, (2, 3))
+    u2 = rng.normal(0, 0.5, (2, 3))
+    s.set_bodies(sid, x1=x1, x2=x2, u1=u1, u2=u2)
+    for c in range(6):
+        s.field(c)[...] = rng.normal(0, 0.05, s.field(c).shape)
+    F = s.fields()
+    E, B = [F[c].copy() for c in range(3)], [F[3 + c].copy() for c in range(3)]
+    bodies = [(x1[k].copy(), x2[k].copy(), u1[k].copy(), u2[k].copy()) for k in range(2)]
+    sp = (info["q1"], info["m1"], info["q2"], info["m2"], info["w"], info["kappa"], ac)
+    L = d * np.array(n)
+    for _ in range(2):
+        E, B, J, bodies = _reference_step(E, B, bodies, sp, d, dt, n)
+        s.step(1)
+        F = s.fields()
+        scale = max(np.abs(F[c]).max() for c in range(9))
+        for c in range(3):
+            assert np.abs(F[c] - E[c]).max() <= 1e-12 * scale
+            assert np.abs(F[3 + c] - B[c]).max() <= 1e-12 * scale
+            assert np.abs(F[6 + c] - J[c]).max() <= 1e-12 * scale
+        ox1, ox2, ou1, ou2 = s.bodies(sid)
+        for k in range(2):
+            assert np.abs(_wrap(ox1[k] - bodies[k][0], L)).max() <= 1e-12 * L.max()
+            assert np.abs(_wrap(ox2[k] - bodies[k][1], L)).max() <= 1e-12 * L.max()
+            assert np.abs(ou1[k] - bodies[k][2]).max() <= 1e-12
+            assert np.abs(ou2[k] - bodies[k][3]).max() <= 1e-12
+    s.close()
