@@ -75,6 +75,15 @@ int check_launch(bp_ctx *c, const char *what) {
 // A node of a tile box then holds the exact sum of up to 2^26 such maximal
 // contributions, and a quantum is about 1e-11 of the largest one (below the
 // FP32 rounding of the contributions themselves).
+// the tile marks of the push's field-box test, recomputed from E and B
+// after they were written from outside the step (state file, caller,
+// checkpoint)
+void refresh_marks(bp_ctx *c) {
+  const float *F[6] = {c->F[0], c->F[1], c->F[2], c->F[3], c->F[4], c->F[5]};
+  launch_field_marks(c->g, F, c->stream);
+  c->launches += 1;
+}
+
 void update_jscale(bp_ctx *c) {
   if (!c->det) {
     c->jscale = c->jinv = 0.0f;
@@ -257,10 +266,12 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
   c->jbb = (uint2 *)dalloc(c, sizeof(uint2) * g.ntiles);
+  g.fnz = (unsigned char *)dalloc(c, g.ntiles);  // zero fields: no tile marked
+  c->qstate = (unsigned char *)dalloc(c, g.ntiles);
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!c->jbox || !c->occ || !c->jbb || !c->status || (nf && !c->frame)) {
+  if (!c->jbox || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
@@ -549,6 +560,7 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   A.jbox = c->jbox;
   A.occ = c->occ;
   A.jbb = c->jbb;
+  A.qstate = c->qstate;
   A.status = c->status;
   A.jscale = c->jscale;
   A.jinv = c->jinv;
@@ -696,7 +708,7 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
   launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
   launch_yee_e(g, E, cB, cJ, c->frame, st);
-  c->launches += 5 + (nopen ? 1 + nopen : 0);
+  c->launches += 6 + (nopen ? 1 + nopen : 0);  // quiet-tile pass, push, current sum, Yee (3), Mur
   c->step++;
   if (probes) {
     for (auto &p : c->pr) {
@@ -759,6 +771,7 @@ int bp_write_field(bp_ctx *c, int comp, const float *src, int on_device) {
   if (!c || comp < 0 || comp > 8 || !src) return BP_ERR_ARG;
   cudaError_t e = cudaMemcpyAsync(c->F[comp], src, sizeof(float) * c->g.ncell,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && comp < 6) refresh_marks(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "write field");
 }
@@ -1052,6 +1065,7 @@ int bp_load(bp_ctx *c, const char *path) {
   fclose(f);
   if (!ok) return fail(c, BP_ERR_IO, "bp_load: truncated fields (%s)", path);
   for (int k = 6; k < 9; ++k) cudaMemset(c->F[k], 0, sizeof(float) * g.ncell);
+  refresh_marks(c);
   c->step = h.step;
   c->sort_dirty = true;
   update_jscale(c);
@@ -1120,6 +1134,7 @@ int bp_reset(bp_ctx *c) {
   if (!c) return BP_ERR_ARG;
   cudaStream_t st = c->stream;
   for (int k = 0; k < 9; ++k) cudaMemsetAsync(c->F[k], 0, sizeof(float) * c->g.ncell, st);
+  cudaMemsetAsync(c->g.fnz, 0, (size_t)c->g.ntiles, st);
   cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st);
   c->step = 0;
   for (auto &p : c->pr) p.count = 0;
@@ -1305,6 +1320,7 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
       cl_parts(c, L, ad.ck_parts[seg][q].p, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY);
     cl_add(c, L, ad.ck_status + 4 * seg, c->status, sizeof(int) * 4);
     cl_flush(c, L);
+    refresh_marks(c);
     const long long base = (long long)seg * ad.K;
     const long long len = std::min<long long>(ad.K, ad.nsteps - base);
     c->step = ad.start + base;

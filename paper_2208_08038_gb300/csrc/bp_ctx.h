@@ -61,6 +61,7 @@ struct bp_ctx {
   float *jbox = nullptr;
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
+  unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push
   float *frame = nullptr;
   int *status = nullptr;
   std::vector<bp_species_state> sp;

@@ -30,6 +30,7 @@ struct GridP {
   int ntiles;
   int cpt;          // cells per tile
   int cb[3], cm[3]; // particle cell index: bit width and mask of each axis
+  unsigned char *fnz; // [ntiles] sticky mark: E or B in the tile has been non-zero
 };
 
 // Tile geometry per dimension (compile time): L cells per tile per simulated
@@ -116,6 +117,7 @@ struct PushArgs {
   float *jbox;             // [ntiles][3][jcells]
   unsigned char *occ;      // [ntiles] the tile's box holds a deposit
   uint2 *jbb;              // [ntiles] its bounding box: lowest / highest node, one byte per axis
+  unsigned char *qstate;   // [ntiles] what the quiet-tile pass left to the push
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
 };
@@ -195,6 +197,30 @@ inline int row_blocks(const GridP &g, int bs) {
   return (int)(rows * ((g.n[0] + bs - 1) / bs));
 }
 
+// tile of a cell (row-major over tiles, x fastest)
+__host__ __device__ __forceinline__ int tile_of(const GridP &g, const int c[3]) {
+  return c[0] / g.L[0] + g.nt[0] * (c[1] / g.L[1] + g.nt[1] * (c[2] / g.L[2]));
+}
+
+// Mark the tile of a cell whose new E or B value is non-zero.  The marks are
+// sticky (cleared only with the fields); the push stages no field box whose
+// tiles are all unmarked.  Called by every thread of a row-blocked launch that
+// is still active: a warp covers 32 consecutive x cells, and only the lowest
+// lane of each tile segment with a non-zero value reads (and, the first time,
+// writes) the mark.
+template <int D>
+__device__ __forceinline__ void mark_nonzero(const GridP &g, const int c[3], bool nz) {
+  const unsigned m = __ballot_sync(__activemask(), nz);
+  if (!nz) return;
+  constexpr int L0 = Geo<D>::L0;
+  static_assert(L0 <= 32 && (L0 & (L0 - 1)) == 0, "a tile segment lies inside one warp");
+  const int lane = (int)(threadIdx.x & 31u);
+  const int base = lane & ~(L0 - 1);
+  if (m & ((1u << lane) - 1u) & ~((1u << base) - 1u)) return;  // a lower lane of the segment marks it
+  unsigned char *f = g.fnz + tile_of(g, c);
+  if (*f == 0) *f = 1;
+}
+
 // float -> int64, rounded to nearest even, on the FP32 and integer pipes
 // (the 64-bit conversion runs on the slow FP64 unit).  Adding 1.5 * 2^23 to
 // a float of magnitude below 2^22 rounds it to an integer held in the low
@@ -214,15 +240,19 @@ __device__ __forceinline__ long long f2ll_rn(float x) {
 // (64-bit and FP32 shared atomic adds are compare-and-swap loops on this
 // GPU).  A node's 64-bit sum is kept as two signed 32-bit words, lo and hi
 // (hoff words later): v is split as 2^16 h + r with h = rint(v / 2^16) and
-// |r| <= 2^15, both exact in FP32 for |v| < 2^47, so rne(v) = 2^16 h + rne(r);
-// lo takes rne(r), hi takes h.  Two atomics, no branch, no returned value;
-// the node's value, 2^16 sum(h) + sum(rne(r)), is the exact sum of rne(v)
-// whatever the order, while fewer than 2^16 adds reach one node.
+// |r| <= 2^15, both exact in FP32, so rne(v) = 2^16 h + rne(r); lo takes
+// rne(r), hi takes h (and is skipped when h = 0).  The node's value,
+// 2^16 sum(h) + sum(rne(r)), is the exact sum of rne(v) whatever the order,
+// while fewer than 2^16 adds reach one node.  Both roundings to an integer
+// add 1.5 * 2^23 (whose ulp is 1) and read the integer off the bits, on the
+// FMA pipe; that needs |v| < 2^38 (callers scale contributions to <= 2^37).
 __device__ __forceinline__ void fx_add(unsigned int *lo, int hoff, float v) {
-  const float h = rintf(v * 1.52587890625e-05f);
-  const float r = fmaf(-h, 65536.0f, v);
-  atomicAdd(reinterpret_cast<int *>(lo), __float2int_rn(r));
-  const int hh = __float2int_rz(h);
+  constexpr float M = 12582912.0f;
+  const float hs = fmaf(v, 1.52587890625e-05f, M);  // M + rne(v / 2^16)
+  const float h = __fsub_rn(hs, M);
+  const float r = fmaf(-h, 65536.0f, v);            // exact
+  atomicAdd(reinterpret_cast<int *>(lo), __float_as_int(__fadd_rn(r, M)) - 0x4B400000);
+  const int hh = __float_as_int(hs) - 0x4B400000;
   if (hh) atomicAdd(reinterpret_cast<int *>(lo + hoff), hh);
 }
 // the value of a pair (both words initialised to 0)
@@ -314,6 +344,8 @@ size_t push_smem_bytes(const GridP &g, int det);
 int push_prepare(const GridP &g, int det);
 
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);
+// recompute the tile marks (g.fnz) from E, B (F[0..5]) after a write from outside the step
+void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s);
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3],
                   float *frame, cudaStream_t s);
 long long frame_floats(const GridP &g);

@@ -52,10 +52,12 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
   constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
   const bool same = __all_sync(__activemask(),
                                (ba[0] == bb[0]) && (D < 2 || ba[1] == bb[1]) && (D < 3 || ba[2] == bb[2]));
+  // contraction x, then y, then z: 3 + 3 + 3 weights per row, plane, box
   float sa = 0.0f, sb = 0.0f;
   if (same) {
 #pragma unroll
-    for (int k = 0; k < NK; ++k)
+    for (int k = 0; k < NK; ++k) {
+      float pa = 0.0f, pb = 0.0f;
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         const float *row = G + Box<D>::gi(ba[0], ba[1] + j, ba[2] + k);
@@ -66,12 +68,16 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
           ra = fmaf(wa[0][i], v, ra);
           rb = fmaf(wb[0][i], v, rb);
         }
-        sa = fmaf(wa[1][j] * wa[2][k], ra, sa);
-        sb = fmaf(wb[1][j] * wb[2][k], rb, sb);
+        pa = fmaf(wa[1][j], ra, pa);
+        pb = fmaf(wb[1][j], rb, pb);
       }
+      sa = fmaf(wa[2][k], pa, sa);
+      sb = fmaf(wb[2][k], pb, sb);
+    }
   } else {
 #pragma unroll
-    for (int k = 0; k < NK; ++k)
+    for (int k = 0; k < NK; ++k) {
+      float pa = 0.0f, pb = 0.0f;
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         const float *ra_ = G + Box<D>::gi(ba[0], ba[1] + j, ba[2] + k);
@@ -82,9 +88,12 @@ __device__ __forceinline__ void gather_comp(const float *__restrict__ G, const L
           ra = fmaf(wa[0][i], ra_[i], ra);
           rb = fmaf(wb[0][i], rb_[i], rb);
         }
-        sa = fmaf(wa[1][j] * wa[2][k], ra, sa);
-        sb = fmaf(wb[1][j] * wb[2][k], rb, sb);
+        pa = fmaf(wa[1][j], ra, pa);
+        pb = fmaf(wb[1][j], rb, pb);
       }
+      sa = fmaf(wa[2][k], pa, sa);
+      sb = fmaf(wb[2][k], pb, sb);
+    }
   }
   oa = sa;
   ob = sb;

@@ -38,22 +38,30 @@ __global__ void __launch_bounds__(256) k_yee_b(GridP g, float *Bx, float *By, fl
   Cell C;
   if (!row_cell<D>(g, C)) return;
   const long long q = C.q;
+  bool nz = false;
   if (!exterior_c<D>(g, 6, C.c)) {
     float d = 0.0f;
     if (D >= 2) d += (Ez[q + C.up[1]] - Ez[q]) * g.idx[1];
     if (D >= 3) d -= (Ey[q + C.up[2]] - Ey[q]) * g.idx[2];
-    Bx[q] -= h * d;
+    const float v = Bx[q] - h * d;
+    Bx[q] = v;
+    nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 5, C.c)) {
     float d = -(Ez[q + C.up[0]] - Ez[q]) * g.idx[0];
     if (D >= 3) d += (Ex[q + C.up[2]] - Ex[q]) * g.idx[2];
-    By[q] -= h * d;
+    const float v = By[q] - h * d;
+    By[q] = v;
+    nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 3, C.c)) {
     float d = (Ey[q + C.up[0]] - Ey[q]) * g.idx[0];
     if (D >= 2) d -= (Ex[q + C.up[1]] - Ex[q]) * g.idx[1];
-    Bz[q] -= h * d;
+    const float v = Bz[q] - h * d;
+    Bz[q] = v;
+    nz |= v != 0.0f;
   }
+  mark_nonzero<D>(g, C.c, nz);
 }
 
 // E <- E + dt (curl B - J) on interior nodes (backward differences)
@@ -65,22 +73,45 @@ __global__ void __launch_bounds__(256) k_yee_e(GridP g, float *Ex, float *Ey, fl
   Cell C;
   if (!row_cell<D>(g, C)) return;
   const long long q = C.q;
+  bool nz = false;
   if (!exterior_c<D>(g, 1, C.c) && !mur_node<D>(g, 1, C.c)) {
     float d = 0.0f;
     if (D >= 2) d += (Bz[q] - Bz[q + C.dn[1]]) * g.idx[1];
     if (D >= 3) d -= (By[q] - By[q + C.dn[2]]) * g.idx[2];
-    Ex[q] += g.dt * (d - Jx[q]);
+    const float v = Ex[q] + g.dt * (d - Jx[q]);
+    Ex[q] = v;
+    nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 2, C.c) && !mur_node<D>(g, 2, C.c)) {
     float d = -(Bz[q] - Bz[q + C.dn[0]]) * g.idx[0];
     if (D >= 3) d += (Bx[q] - Bx[q + C.dn[2]]) * g.idx[2];
-    Ey[q] += g.dt * (d - Jy[q]);
+    const float v = Ey[q] + g.dt * (d - Jy[q]);
+    Ey[q] = v;
+    nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 4, C.c) && !mur_node<D>(g, 4, C.c)) {
     float d = (By[q] - By[q + C.dn[0]]) * g.idx[0];
     if (D >= 2) d -= (Bx[q] - Bx[q + C.dn[1]]) * g.idx[1];
-    Ez[q] += g.dt * (d - Jz[q]);
+    const float v = Ez[q] + g.dt * (d - Jz[q]);
+    Ez[q] = v;
+    nz |= v != 0.0f;
   }
+  mark_nonzero<D>(g, C.c, nz);
+}
+
+// the marks of the fields as they are (after a write from outside the step):
+// every tile holding a non-zero E or B component (marks cleared before)
+template <int D>
+__global__ void __launch_bounds__(256) k_field_marks(GridP g, const float *__restrict__ Ex,
+                                                     const float *__restrict__ Ey, const float *__restrict__ Ez,
+                                                     const float *__restrict__ Bx, const float *__restrict__ By,
+                                                     const float *__restrict__ Bz) {
+  Cell C;
+  if (!row_cell<D>(g, C)) return;
+  const long long q = C.q;
+  const bool nz = Ex[q] != 0.0f || Ey[q] != 0.0f || Ez[q] != 0.0f || Bx[q] != 0.0f || By[q] != 0.0f ||
+                  Bz[q] != 0.0f;
+  mark_nonzero<D>(g, C.c, nz);
 }
 
 // ---------------------------------------------------------------------------
@@ -162,7 +193,12 @@ __global__ void k_mur(GridP g, float *Ex, float *Ey, float *Ez, const float *fra
     float old_b = frame[base + ((side * 2 + 0) * 2 + ci) * F + pos];
     float old_a = frame[base + ((side * 2 + 1) * 2 + ci) * F + pos];
     float km = (g.dt - g.dx[a]) / (g.dt + g.dx[a]);
-    E[comp][id] = old_a + km * (E[comp][ida] - old_b);
+    const float v = old_a + km * (E[comp][ida] - old_b);
+    E[comp][id] = v;
+    if (v != 0.0f) {
+      unsigned char *f = g.fnz + tile_of(g, c);
+      if (*f == 0) *f = 1;
+    }
   }
 }
 
@@ -305,6 +341,14 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], co
     for (int p = 1; p <= nopen; ++p)
       k_mur<<<grid_blocks(nf / 2, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf / 2, p);
   }
+}
+
+void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s) {
+  cudaMemsetAsync(g.fnz, 0, (size_t)g.ntiles, s);
+  const int nb = row_blocks(g, 256);
+  if (g.D == 1) k_field_marks<1><<<nb, 256, 0, s>>>(g, F[0], F[1], F[2], F[3], F[4], F[5]);
+  else if (g.D == 2) k_field_marks<2><<<nb, 256, 0, s>>>(g, F[0], F[1], F[2], F[3], F[4], F[5]);
+  else k_field_marks<3><<<nb, 256, 0, s>>>(g, F[0], F[1], F[2], F[3], F[4], F[5]);
 }
 
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],

@@ -316,6 +316,132 @@ __device__ __forceinline__ void window_centre(const float *f, const int *d, int 
   for (int a = 0; a < 3; ++a) n0[a] = a < D ? d[a] + Box<D>::OJ + (f[a] >= 0.5f ? 1 : 0) : 0;
 }
 
+// 1 / gamma of a momentum u = p / (m c), one fixed evaluation order (the
+// quiet pass and the full push must move a particle identically)
+__device__ __forceinline__ float inv_gamma(const float u[3]) {
+  return rsqrtf(fmaf(u[2], u[2], fmaf(u[1], u[1], fmaf(u[0], u[0], 1.0f))));
+}
+
+// body 1's offset after the drift x += dt v, in cells
+__device__ __forceinline__ float drift_offset(const GridP &g, int a, float f, float v) {
+  return fmaf(g.dt * v, g.idx[a], f);
+}
+
+// new cell of body 1 from its moved offset fn (renormalised to [0, 1)).  On
+// open axes a free particle whose cell leaves [2, n-2) is removed (after its
+// last deposit); a two-body ion leaving the grid is a domain error.
+template <int D>
+__device__ __forceinline__ void advance_cell(const GridP &g, const int T0[3], bool two, int c[3], float fn[3],
+                                             bool &bad, bool &removed, bool &need_sort) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (fn[a] >= 1.0f) {
+      fn[a] -= 1.0f;
+      c[a] += 1;
+    } else if (fn[a] < 0.0f) {
+      fn[a] += 1.0f;
+      c[a] -= 1;
+      if (fn[a] >= 1.0f) { fn[a] = 0.0f; c[a] += 1; }
+    }
+    if (g.bc[a] == BP_PERIODIC) {
+      c[a] = wrap_once(c[a], g.n[a]);
+    } else if (two) {
+      bad |= (c[a] < 0 || c[a] >= g.n[a]);
+    } else {
+      removed |= (c[a] < 2 || c[a] >= g.n[a] - 2);
+    }
+    const int dn = rel_cell<D>(g, a, c[a], T0[a]);
+    need_sort |= outside_margin<D>(a, dn);
+  }
+}
+
+// A quiet ion: a neutral two-body ion whose bodies coincide (r = 0) and move
+// together (u1 = u2, finite) in a tile whose staged fields are all zero.  The
+// full push leaves its momenta and r exactly as they are (zero internal force
+// at r = 0, zero fields) and deposits nothing (its bodies' terms cancel), so
+// only body 1's drift remains.
+__device__ __forceinline__ bool quiet_state(const float r[3], const float u1[3], const float u2[3]) {
+  bool q = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) q &= (r[a] == 0.0f) && (u1[a] == u2[a]) && isfinite(u1[a]);
+  return q;
+}
+
+// The quiet pass over QB particles of a thread (i0, i0 + bs, ...): all loads
+// first, so that many are in flight, then the drift of the quiet ones, which
+// writes only the cell and the offset.  Returns true when one of them is not
+// quiet (left for the full push).
+template <int D, int QB>
+__device__ __forceinline__ bool quiet_batch(const GridP &g, const PartP &P, long long i0, int bs, long long end,
+                                            const int T0[3], int *status) {
+  const long long cap = P.cap;
+  int cell[QB];
+  float f[QB][3], u1[QB][3], u2[QB][3], r[QB][3];
+#pragma unroll
+  for (int q = 0; q < QB; ++q) {
+    const long long i = i0 + (long long)q * bs;
+    cell[q] = i < end ? P.cell[i] : -1;
+    if (cell[q] >= 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        f[q][a] = a < D ? P.off[a * cap + i] : 0.0f;
+        u1[q][a] = P.u1[a * cap + i];
+        u2[q][a] = P.u2[a * cap + i];
+        r[q][a] = P.r[a * cap + i];
+      }
+    }
+  }
+  bool left = false;
+#pragma unroll
+  for (int q = 0; q < QB; ++q) {
+    if (cell[q] < 0) continue;
+    if (!quiet_state(r[q], u1[q], u2[q])) {
+      left = true;
+      continue;
+    }
+    const long long i = i0 + (long long)q * bs;
+    int c[3];
+    unpack_cell(g, cell[q], c);
+    bool bad = false, removed = false, need_sort = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) bad |= outside_margin<D>(a, rel_cell<D>(g, a, c[a], T0[a]));
+    if (bad) {
+      atomicOr(status, ST_DOMAIN);
+      continue;
+    }
+    const float gi = inv_gamma(u1[q]);
+    float fn[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) fn[a] = drift_offset(g, a, f[q][a], u1[q][a] * gi);
+    advance_cell<D>(g, T0, true, c, fn, bad, removed, need_sort);
+    if (bad) {
+      atomicOr(status, ST_DOMAIN);
+      P.cell[i] = -1;
+      continue;
+    }
+    if (need_sort) atomicOr(status, ST_NEED_SORT);
+    P.cell[i] = pack_cell(g, c[0], c[1], c[2]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) P.off[a * cap + i] = fn[a];
+  }
+  return left;
+}
+
+// whether the quiet pass has already moved particle i (its state is still
+// quiet after the move: r, u1, u2 unchanged)
+__device__ __forceinline__ bool quiet_done(const PartP &P, long long i) {
+  const long long cap = P.cap;
+  if (P.cell[i] < 0) return true;
+  float r[3], u1[3], u2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[a] = P.r[a * cap + i];
+    u1[a] = P.u1[a * cap + i];
+    u2[a] = P.u2[a * cap + i];
+  }
+  return quiet_state(r, u1, u2);
+}
+
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
                               const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax,
@@ -394,13 +520,13 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     boris(sp.h2, E2, B2, u2);
   }
   if (two) {
-    float g2 = rsqrtf(1.0f + u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+    const float g2 = inv_gamma(u2);
 #pragma unroll
     for (int a = 0; a < 3; ++a) v2[a] = u2[a] * g2;
   }
   if (!quiet) boris(sp.h1, E1, B1, u1);
   {
-    float g1 = rsqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    const float g1 = inv_gamma(u1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) v1[a] = u1[a] * g1;
   }
@@ -410,7 +536,7 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   float fn[3] = {0.0f, 0.0f, 0.0f}, de1[3] = {0.0f, 0.0f, 0.0f}, de2[3] = {0.0f, 0.0f, 0.0f}, rn[3];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    fn[a] = f[a] + g.dt * v1[a] * g.idx[a];
+    fn[a] = drift_offset(g, a, f[a], v1[a]);
     de1[a] = fn[a] - f[a];
   }
   if (two) {
@@ -483,30 +609,8 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       }
     }
   }
-  // new cell of body 1.  On open axes a free particle whose cell leaves
-  // [2, n-2) is removed (after its last deposit); a two-body ion leaving the
-  // grid is a domain error.
   bool need_sort = false, nonfinite = false, removed = false;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (fn[a] >= 1.0f) {
-      fn[a] -= 1.0f;
-      c[a] += 1;
-    } else if (fn[a] < 0.0f) {
-      fn[a] += 1.0f;
-      c[a] -= 1;
-      if (fn[a] >= 1.0f) { fn[a] = 0.0f; c[a] += 1; }
-    }
-    if (g.bc[a] == BP_PERIODIC) {
-      c[a] = wrap_once(c[a], g.n[a]);
-    } else if (two) {
-      bad |= (c[a] < 0 || c[a] >= g.n[a]);
-    } else {
-      removed |= (c[a] < 2 || c[a] >= g.n[a] - 2);
-    }
-    int dn = rel_cell<D>(g, a, c[a], T0[a]);
-    need_sort |= outside_margin<D>(a, dn);
-  }
+  advance_cell<D>(g, T0, two, c, fn, bad, removed, need_sort);
 #pragma unroll
   for (int a = 0; a < 3; ++a) nonfinite |= !isfinite(u1[a]) || !isfinite(u2[a]);
   if (bad) atomicOr(status, ST_DOMAIN);
@@ -530,6 +634,75 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   }
 }
 
+// clear a shared-memory current box of n nodes (and the high words in the
+// sorted mode), 16 bytes per store
+template <bool DET, typename JT>
+__device__ __forceinline__ void zero_box(JT *J, int n, int tid, int bs) {
+  constexpr int W = DET ? 2 : 1;
+  uint4 *p = reinterpret_cast<uint4 *>(J);
+  const int n4 = (W * n) / 4;
+  for (int q = tid; q < n4; q += bs) p[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (int q = 4 * n4 + tid; q < W * n; q += bs) reinterpret_cast<unsigned *>(J)[q] = 0u;
+}
+
+// A tile whose 3^D neighbouring tiles have never held a non-zero E or B has
+// an all-zero field box (the box lies inside them).  This light kernel takes
+// such tiles before the push: it moves their quiet ions (the drift alone) at
+// high occupancy and leaves a state per tile:
+//   QS_PUSH  the push kernel does the whole tile (fields may be non-zero),
+//   QS_DONE  every particle moved, nothing deposited (occ = 0),
+//   QS_REST  the quiet ions moved; the push does the others without fields.
+constexpr unsigned char QS_PUSH = 0, QS_DONE = 1, QS_REST = 2;
+
+template <int D>
+__global__ void __launch_bounds__(256, 3) k_push_quiet(GridP g, PushArgs A) {
+  static_assert(Box<D>::OG <= Geo<D>::L0 && Box<D>::G0 - Box<D>::OG <= 2 * Geo<D>::L0 &&
+                    (D < 2 || (Box<D>::OG <= Geo<D>::L1 && Box<D>::G1 - Box<D>::OG <= 2 * Geo<D>::L1)) &&
+                    (D < 3 || (Box<D>::OG <= Geo<D>::L2 && Box<D>::G2 - Box<D>::OG <= 2 * Geo<D>::L2)),
+                "field box within the neighbouring tiles");
+  constexpr int QB = 4;
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  int tc[3];
+  tc[0] = t % g.nt[0];
+  tc[1] = (t / g.nt[0]) % g.nt[1];
+  tc[2] = t / (g.nt[0] * g.nt[1]);
+  bool marked = false;
+  if (tid < 27) {
+    const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
+    bool use = true;
+    int nb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      nb[a] = tc[a] + o[a];
+      if (a >= D) use &= o[a] == 0;
+      else if (g.bc[a] == BP_PERIODIC) nb[a] = wrap_once(nb[a], g.nt[a]);
+      else use &= nb[a] >= 0 && nb[a] < g.nt[a];
+    }
+    if (use) marked = g.fnz[nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2])] != 0;
+  }
+  if (__syncthreads_or(marked)) {
+    if (tid == 0) A.qstate[t] = QS_PUSH;
+    return;
+  }
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  bool left = false;
+  for (int s = 0; s < A.nsp; ++s) {
+    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    if (A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2) {
+      for (long long i0 = beg + tid; i0 < end; i0 += (long long)QB * bs)
+        left |= quiet_batch<D, QB>(g, A.p[s], i0, bs, end, T0, A.status);
+    } else {
+      left |= end > beg;
+    }
+  }
+  left = __syncthreads_or(left);
+  if (tid == 0) {
+    A.qstate[t] = left ? QS_REST : QS_DONE;
+    if (!left) A.occ[t] = 0;
+  }
+}
+
 template <int D, bool DET>
 __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A) {
   using JT = typename std::conditional<DET, unsigned int, float>::type;
@@ -541,6 +714,8 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
   const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
+  const unsigned char qs = A.qstate[t];
+  if (qs == QS_DONE) return;
   int total = 0;
   for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
   if (total == 0) {
@@ -552,13 +727,11 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
   tc[1] = (t / g.nt[0]) % g.nt[1];
   tc[2] = t / (g.nt[0] * g.nt[1]);
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  for (int q = tid; q < 3 * JC; q += bs) {
-    Jsm[q] = (JT)0;
-    if constexpr (DET) Jsm[3 * JC + q] = 0;
-  }
-  // stage E, B of the tile plus halo (zero outside open faces)
+  zero_box<DET>(Jsm, 3 * JC, tid, bs);
+  // stage E, B of the tile plus halo (zero outside open faces); a QS_REST
+  // tile's box is all zero and is not staged
   bool nz = false;
-  for (int q = tid; q < BX::GCOMP; q += bs) {
+  for (int q = tid; qs == QS_PUSH && q < BX::GCOMP; q += bs) {
     int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     int bidx[3] = {b0, b1, b2};
     const int si = BX::gi(b0, b1, b2);
@@ -594,11 +767,15 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     if (tid == 0) qn = 0;
     __syncthreads();
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    // in a QS_REST tile the quiet ions of this species have already moved
+    const bool moved = qs == QS_REST && A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2;
     // consecutive lanes take consecutive (cell-sorted) particles: their
     // gather loads share addresses and their state loads coalesce
-    for (long long i = beg + tid; i < end; i += bs)
+    for (long long i = beg + tid; i < end; i += bs) {
+      if (moved && quiet_done(A.p[s], i)) continue;
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi,
                                 nofield);
+    }
     __syncthreads();
     // the deferred general deposits, one row per thread
     const int nitem = min(qn, QMAX) * 2 * IPB;
@@ -650,6 +827,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
 
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
+  k_push_quiet<D><<<g.ntiles, 256, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
   k_push<D, DET><<<g.ntiles, D == 3 ? 512 : 256, smem, s>>>(g, a);
 }

@@ -104,6 +104,37 @@ def small_3d(sigma=2e-2, seed=2, steps=30, n=(48, 16, 16), periodic=False):
     return wl
 
 
+def test_written_field_reaches_the_push():
+    """The push stages no field box whose neighbouring tiles never held a
+    non-zero E or B.  A field written from outside the step (here a local E_y
+    blob in a medium that has seen no field) re-marks the tiles, so the ions
+    under it are kicked and deposit exactly as in the oracle; the rest of the
+    medium stays quiet."""
+    wl = small_3d(periodic=True)
+    wl.lasers = []
+    ora, osid, _ = oracle_from_workload(wl)
+    gpu, gsid, _ = gpu_from_workload(wl)
+    ora.step(1)
+    gpu.step(1)
+    gpu.sync()
+    assert np.abs(gpu.fields()[:6]).max() == 0.0
+    f = np.zeros(ora.field(1).shape, dtype=np.float32)
+    f[5:11, 4:9, 30:37] = 2e-3  # [z][y][x]: x cells 30..36; the tiles of x cells 0..15 stay unmarked
+    gpu.write_field(1, f)
+    ora.field(1)[...] = f
+    for _ in range(3):
+        ora.step(1)
+        gpu.step(1)
+    gpu.sync()
+    assert field_rel_l2(gpu.fields(), ora.fields()) < 1e-5
+    assert rel_l2(gpu.fields()[7], ora.fields()[7]) < 1e-4  # J_y of the kicked ions
+    x1o, x2o, u1o, u2o = ora.bodies(osid[0])
+    x1g, x2g, u1g, u2g = gpu.read_particles(gsid[0], len(x1o))
+    assert np.abs(u2o).max() > 0 and rel_l2(u2g, u2o) < 1e-5
+    gpu.close()
+    ora.close()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_3d_thermal_parity(mode):
     wl = small_3d()
