@@ -29,10 +29,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/fwd ratio"
-# DRAM bytes (read + write) of one k_push<3, sorted> launch on this workload,
-# from one ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass; profiles/k_push_3d_full_traffic.md)
-PUSH_TRAFFIC = 29.0e9
+# DRAM bytes (read + write) of one push launch (k_push_quiet<3> + k_push<3,
+# sorted>) on this workload, averaged over the timed 500-step run, from an
+# ncu capture of every push launch of that run (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass per launch).  It
+# falls from 28.2 GB late in the run to 18.3 GB at its start, where most
+# ions are quiet and write only their cell and offset.
+PUSH_TRAFFIC = 23.61e9
 UNIT = "ion-pushes/s"
 
 
@@ -396,7 +399,7 @@ def main():
         "config": our_config(n_ion, args.mode, world, args.warmup, args.steps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": PUSH_TRAFFIC, "traffic_unit": "bytes per launch",
-                     "kernel": "k_push<3,sorted>",
+                     "kernel": "push: k_push_quiet<3> + k_push<3,sorted>",
                      "peak_source": src, "push_ms_per_launch": push_avg,
                      "push_ms_per_launch_last_steps": push_tail, "last_steps": tail},
         "clocks": clocks,

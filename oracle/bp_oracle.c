@@ -17,7 +17,7 @@
  *     position                                                       Sec. 2, Boris equations
  *   - current of each body q v / dV added to the total current     Sec. 2
  *   - vacuum Maxwell equations, unchanged                           Sec. 3.1
- * Discrete choices the paper leaves open (documented in the design doc):
+ * Discrete choices the paper leaves open:
  *   Yee FDTD fields, quadratic B-spline shape for gather and deposit, the
  *   Esirkepov charge-conserving current, Mur first-order open faces, a
  *   current-sheet laser antenna, normalised units (c = 1, lengths in 1/k0,

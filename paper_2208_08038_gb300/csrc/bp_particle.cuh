@@ -111,6 +111,129 @@ __device__ __forceinline__ void gather_all(const float *G, const Loc &A, const L
   gather_comp<D, 3>(G + 5 * gc, A, Bo, Ba[2], Bb[2]);
 }
 
+// ---------------------------------------------------------------------------
+// The 3D gather on packed pairs (FFMA2): the six components go in pairs
+// (E_x, B_y), (E_y, B_x), (E_z, B_z); a pair's lanes carry one component
+// each, with that component's stagger weights, so each row value pair comes
+// from two shared-memory loads and every multiply-add serves two components.
+// Per lane the arithmetic is the scalar gather's.
+
+// a body's position for the gather: offsets from the nearest node (xn) and
+// from the cell centre (xh), and the first box index of each stencil
+struct Pos {
+  float xn[3], xh[3];
+  int bn[3], bh[3];
+};
+
+template <int D>
+__device__ __forceinline__ void make_pos(const int d[3], const float f[3], Pos &P) {
+  constexpr int og = Box<D>::OG;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      const int up = f[a] >= 0.5f ? 1 : 0;
+      P.bn[a] = d[a] + og + up - 1;
+      P.xn[a] = f[a] - (float)up;
+      P.bh[a] = d[a] + og - 1;
+      P.xh[a] = f[a] - 0.5f;
+    } else {
+      P.bn[a] = P.bh[a] = 0;
+      P.xn[a] = P.xh[a] = 0.0f;
+    }
+  }
+}
+
+// qweights on a pair of offsets
+__device__ __forceinline__ void qweights2(float2 xi, float2 w[3]) {
+  const float2 H = make_float2(0.5f, 0.5f), M1 = make_float2(-1.0f, -1.0f);
+  const float2 a = __ffma2_rn(xi, M1, H), b = __fadd2_rn(xi, H);
+  w[0] = __fmul2_rn(__fmul2_rn(a, H), a);
+  w[1] = __ffma2_rn(__fmul2_rn(xi, M1), xi, make_float2(0.75f, 0.75f));
+  w[2] = __fmul2_rn(__fmul2_rn(b, H), b);
+}
+
+// components c1, c2 (stagger patterns P1, P2; boxes G1, G2) at bodies A, B
+template <int P1, int P2>
+__device__ __forceinline__ void gather_pair3(const float *__restrict__ G1, const float *__restrict__ G2, const Pos &A,
+                                             const Pos &B, float2 &oa, float2 &ob) {
+  float2 wa[3][3], wb[3][3];
+  int a1[3], a2[3], b1[3], b2[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const bool h1 = (P1 >> ax) & 1, h2 = (P2 >> ax) & 1;
+    qweights2(make_float2(h1 ? A.xh[ax] : A.xn[ax], h2 ? A.xh[ax] : A.xn[ax]), wa[ax]);
+    qweights2(make_float2(h1 ? B.xh[ax] : B.xn[ax], h2 ? B.xh[ax] : B.xn[ax]), wb[ax]);
+    a1[ax] = h1 ? A.bh[ax] : A.bn[ax];
+    a2[ax] = h2 ? A.bh[ax] : A.bn[ax];
+    b1[ax] = h1 ? B.bh[ax] : B.bn[ax];
+    b2[ax] = h2 ? B.bh[ax] : B.bn[ax];
+  }
+  const bool same = __all_sync(__activemask(), a1[0] == b1[0] && a1[1] == b1[1] && a1[2] == b1[2] &&
+                                                   a2[0] == b2[0] && a2[1] == b2[1] && a2[2] == b2[2]);
+  float2 sa = make_float2(0.0f, 0.0f), sb = sa;
+  if (same) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float2 pa = make_float2(0.0f, 0.0f), pb = pa;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float *r1 = G1 + Box<3>::gi(a1[0], a1[1] + j, a1[2] + k);
+        const float *r2 = G2 + Box<3>::gi(a2[0], a2[1] + j, a2[2] + k);
+        float2 ra = make_float2(0.0f, 0.0f), rb = ra;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float2 v = make_float2(r1[i], r2[i]);
+          ra = __ffma2_rn(wa[0][i], v, ra);
+          rb = __ffma2_rn(wb[0][i], v, rb);
+        }
+        pa = __ffma2_rn(wa[1][j], ra, pa);
+        pb = __ffma2_rn(wb[1][j], rb, pb);
+      }
+      sa = __ffma2_rn(wa[2][k], pa, sa);
+      sb = __ffma2_rn(wb[2][k], pb, sb);
+    }
+  } else {
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      float2 pa = make_float2(0.0f, 0.0f), pb = pa;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float *ra1 = G1 + Box<3>::gi(a1[0], a1[1] + j, a1[2] + k);
+        const float *ra2 = G2 + Box<3>::gi(a2[0], a2[1] + j, a2[2] + k);
+        const float *rb1 = G1 + Box<3>::gi(b1[0], b1[1] + j, b1[2] + k);
+        const float *rb2 = G2 + Box<3>::gi(b2[0], b2[1] + j, b2[2] + k);
+        float2 ra = make_float2(0.0f, 0.0f), rb = ra;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          ra = __ffma2_rn(wa[0][i], make_float2(ra1[i], ra2[i]), ra);
+          rb = __ffma2_rn(wb[0][i], make_float2(rb1[i], rb2[i]), rb);
+        }
+        pa = __ffma2_rn(wa[1][j], ra, pa);
+        pb = __ffma2_rn(wb[1][j], rb, pb);
+      }
+      // wz[k]: the weights are selected by a loop index here (rolled loop)
+      const float2 wza = k == 0 ? wa[2][0] : (k == 1 ? wa[2][1] : wa[2][2]);
+      const float2 wzb = k == 0 ? wb[2][0] : (k == 1 ? wb[2][1] : wb[2][2]);
+      sa = __ffma2_rn(wza, pa, sa);
+      sb = __ffma2_rn(wzb, pb, sb);
+    }
+  }
+  oa = sa;
+  ob = sb;
+}
+
+__device__ __forceinline__ void gather_all_p3(const float *G, const Pos &A, const Pos &Bo, float Ea[3], float Ba[3],
+                                              float Eb[3], float Bb[3]) {
+  constexpr int gc = Box<3>::GCELLS;
+  float2 a, b;
+  gather_pair3<1, 5>(G + 0 * gc, G + 4 * gc, A, Bo, a, b);  // E_x, B_y
+  Ea[0] = a.x; Ba[1] = a.y; Eb[0] = b.x; Bb[1] = b.y;
+  gather_pair3<2, 6>(G + 1 * gc, G + 3 * gc, A, Bo, a, b);  // E_y, B_x
+  Ea[1] = a.x; Ba[0] = a.y; Eb[1] = b.x; Bb[0] = b.y;
+  gather_pair3<4, 3>(G + 2 * gc, G + 5 * gc, A, Bo, a, b);  // E_z, B_z
+  Ea[2] = a.x; Ba[2] = a.y; Eb[2] = b.x; Bb[2] = b.y;
+}
+
 // relativistic Boris (Sec. 2): u- = u + hE; t = hB/gamma-; s = 2t/(1+t^2);
 // u+ = u- + (u- + u- x t) x s; u = u+ + hE
 __device__ __forceinline__ void boris(float h, const float E[3], const float B[3], float u[3]) {

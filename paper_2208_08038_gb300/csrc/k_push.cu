@@ -26,6 +26,8 @@ namespace {
 // capacity of the deferred-deposit records per tile (shared memory); a tile
 // with more general-case particles deposits the rest in place
 __host__ __device__ constexpr int push_qmax(int D) { return D == 2 ? 128 : 64; }
+// threads of a push block
+__host__ __device__ constexpr int push_threads(int D) { return D == 3 ? 512 : 256; }
 
 // add v (already in fixed-point units in the sorted mode) to a current node:
 // sorted mode, the exact fixed-point add fx_add (low words of the box, high
@@ -498,10 +500,17 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
 #pragma unroll
     for (int a = 0; a < 3; ++a) E1[a] = B1[a] = E2[a] = B2[a] = 0.0f;
   } else {
-    Loc L1, L2;
-    make_loc<D>(d, f, L1);
-    make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
-    gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
+    if constexpr (D == 3) {
+      Pos P1, P2;
+      make_pos<D>(d, f, P1);
+      make_pos<D>(two ? d2 : d, two ? f2 : f, P2);
+      gather_all_p3(Gsm, P1, P2, E1, B1, E2, B2);
+    } else {
+      Loc L1, L2;
+      make_loc<D>(d, f, L1);
+      make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
+      gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
+    }
   }
   float v1[3], v2[3] = {0.0f, 0.0f, 0.0f};
   if (two && !quiet) {
@@ -634,6 +643,26 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
   }
 }
 
+// the state of the particle a thread takes next, brought into L1 while the
+// current one is pushed (its loads would otherwise stall the warp at the
+// start of the next iteration)
+template <int D>
+__device__ __forceinline__ void prefetch_particle(const PartP &P, long long j, bool two) {
+  const long long cp = P.cap;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(P.cell + j));
+#pragma unroll
+  for (int a = 0; a < D; ++a) asm volatile("prefetch.global.L1 [%0];" ::"l"(P.off + a * cp + j));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) asm volatile("prefetch.global.L1 [%0];" ::"l"(P.u1 + a * cp + j));
+  if (two) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(P.r + a * cp + j));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(P.u2 + a * cp + j));
+    }
+  }
+}
+
 // clear a shared-memory current box of n nodes (and the high words in the
 // sorted mode), 16 bytes per store
 template <bool DET, typename JT>
@@ -704,7 +733,7 @@ __global__ void __launch_bounds__(256, 3) k_push_quiet(GridP g, PushArgs A) {
 }
 
 template <int D, bool DET>
-__global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A) {
+__global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
   using JT = typename std::conditional<DET, unsigned int, float>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   using BX = Box<D>;
@@ -773,6 +802,7 @@ __global__ void __launch_bounds__(D == 3 ? 512 : 256) k_push(GridP g, PushArgs A
     // gather loads share addresses and their state loads coalesce
     for (long long i = beg + tid; i < end; i += bs) {
       if (moved && quiet_done(A.p[s], i)) continue;
+      if (i + bs < end) prefetch_particle<D>(A.p[s], i + bs, A.sp[s].kind == BP_TWO_BODY);
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi,
                                 nofield);
     }
@@ -829,7 +859,7 @@ template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
   k_push_quiet<D><<<g.ntiles, 256, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
-  k_push<D, DET><<<g.ntiles, D == 3 ? 512 : 256, smem, s>>>(g, a);
+  k_push<D, DET><<<g.ntiles, push_threads(D), smem, s>>>(g, a);
 }
 
 template <int D, bool DET>
