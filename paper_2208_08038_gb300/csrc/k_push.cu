@@ -155,13 +155,22 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         jput<D, DET, false>(Jz + Box<D>::ji(bx + i, by + j, 0), jz);
       }
   } else {
+    // The outer loop of each pass stays rolled (its weights picked by
+    // selects): the fully unrolled 54-node form is about three times the
+    // code, and the kernel's hot path then outgrows the instruction caches.
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      float azk[NB], dzk[NB];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+      for (int b = 0; b < NB; ++b) {
+        azk[b] = k == 0 ? A[b][2][0] : (k == 1 ? A[b][2][1] : A[b][2][2]);
+        dzk[b] = k == 0 ? DS[b][2][0] : (k == 1 ? DS[b][2][1] : DS[b][2][2]);
+      }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][1][j], A[b][2][k], DK[b][1][j] * DS[b][2][k]);
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][1][j], azk[b], DK[b][1][j] * dzk[b]);
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
           float jx = __fmul_rn(cP[0][0][f], F[0]);
@@ -170,12 +179,10 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
         }
       }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
       for (int i = 0; i < 3; ++i) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], A[b][2][k], DK[b][0][i] * DS[b][2][k]);
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], azk[b], DK[b][0][i] * dzk[b]);
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           float jy = __fmul_rn(cP[0][1][g], F[0]);
@@ -183,13 +190,20 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
           jput<D, DET, false>(Jy + Box<D>::ji(bx + i, by + g, bz + k), jy);
         }
       }
+    }
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+      float ayj[NB], dyj[NB];
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
+      for (int b = 0; b < NB; ++b) {
+        ayj[b] = j == 0 ? A[b][1][0] : (j == 1 ? A[b][1][1] : A[b][1][2]);
+        dyj[b] = j == 0 ? DS[b][1][0] : (j == 1 ? DS[b][1][1] : DS[b][1][2]);
+      }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         float F[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], A[b][1][j], DK[b][0][i] * DS[b][1][j]);
+        for (int b = 0; b < NB; ++b) F[b] = fmaf(A[b][0][i], ayj[b], DK[b][0][i] * dyj[b]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float jz = __fmul_rn(cP[0][2][h], F[0]);
@@ -197,6 +211,7 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
           jput<D, DET, false>(Jz + Box<D>::ji(bx + i, by + j, bz + h), jz);
         }
       }
+    }
   }
 }
 
