@@ -33,9 +33,9 @@ METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/
 # sorted>) on this workload, averaged over the timed 500-step run, from an
 # ncu capture of every push launch of that run (dram__bytes_read.sum +
 # dram__bytes_write.sum, 1 pass per launch).  It
-# falls from 28.2 GB late in the run to 18.3 GB at its start, where most
+# falls from 27.5 GB late in the run to 18.3 GB at its start, where most
 # ions are quiet and write only their cell and offset.
-PUSH_TRAFFIC = 23.61e9
+PUSH_TRAFFIC = 23.22e9
 UNIT = "ion-pushes/s"
 
 

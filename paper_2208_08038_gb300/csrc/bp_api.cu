@@ -263,7 +263,13 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
       return BP_ERR_OOM;
     }
   }
-  c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
+  // sorted deposit: the tiles add their current to a global 64-bit fixed-point
+  // array; atomic deposit: per-tile FP32 boxes summed by the current-sum kernel
+  if (c->det) {
+    c->jfx = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 3 * (size_t)ncell);
+    c->ant = (double *)dalloc(c, sizeof(double) * BP_MAX_LASER * (size_t)(ncell / g.n[0]));
+  }
+  else c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
   c->jbb = (uint2 *)dalloc(c, sizeof(uint2) * g.ntiles);
   g.fnz = (unsigned char *)dalloc(c, g.ntiles);  // zero fields: no tile marked
@@ -271,7 +277,8 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!c->jbox || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status || (nf && !c->frame)) {
+  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && !c->ant) || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
+      (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
@@ -558,6 +565,7 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
     A.B[k] = c->F[3 + k];
   }
   A.jbox = c->jbox;
+  A.jfx = c->jfx;
   A.occ = c->occ;
   A.jbb = c->jbb;
   A.qstate = c->qstate;
@@ -705,10 +713,13 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
     cudaEventRecord(c->ev[c->ev_used + 1], st);
     c->ev_used += 2;
   }
-  launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), ((double)c->step + 0.5) * g.dtd, st);
+  const double th = ((double)c->step + 0.5) * g.dtd;  // the current's time level
+  if (!c->det) launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), th, st);
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
-  launch_yee_e(g, E, cB, cJ, c->frame, st);
-  c->launches += 6 + (nopen ? 1 + nopen : 0);  // quiet-tile pass, push, current sum, Yee (3), Mur
+  launch_yee_e(g, E, cB, J, c->frame, c->det ? c->jfx : nullptr, c->jinv, c->las.data(), (int)c->las.size(), th,
+               c->ant, st);
+  // quiet-tile pass, push, current sum (atomic deposit) or antenna (sorted deposit, with lasers), Yee (3), Mur
+  c->launches += (c->det ? 5 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0);
   c->step++;
   if (probes) {
     for (auto &p : c->pr) {
@@ -1065,6 +1076,7 @@ int bp_load(bp_ctx *c, const char *path) {
   fclose(f);
   if (!ok) return fail(c, BP_ERR_IO, "bp_load: truncated fields (%s)", path);
   for (int k = 6; k < 9; ++k) cudaMemset(c->F[k], 0, sizeof(float) * g.ncell);
+  if (c->jfx) cudaMemset(c->jfx, 0, sizeof(unsigned long long) * 3 * (size_t)g.ncell);
   refresh_marks(c);
   c->step = h.step;
   c->sort_dirty = true;
@@ -1135,6 +1147,7 @@ int bp_reset(bp_ctx *c) {
   cudaStream_t st = c->stream;
   for (int k = 0; k < 9; ++k) cudaMemsetAsync(c->F[k], 0, sizeof(float) * c->g.ncell, st);
   cudaMemsetAsync(c->g.fnz, 0, (size_t)c->g.ntiles, st);
+  if (c->jfx) cudaMemsetAsync(c->jfx, 0, sizeof(unsigned long long) * 3 * (size_t)c->g.ncell, st);
   cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st);
   c->step = 0;
   for (auto &p : c->pr) p.count = 0;

@@ -58,7 +58,9 @@ struct bp_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   float *F[9] = {};
-  float *jbox = nullptr;
+  float *jbox = nullptr;             // atomic deposit: per-tile FP32 current boxes
+  unsigned long long *jfx = nullptr; // sorted deposit: [3][ncell] current in 64-bit fixed point
+  double *ant = nullptr;             // sorted deposit: antenna sheet values of a step, [laser][ncell / n0]
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push

@@ -118,6 +118,7 @@ struct PushArgs {
   unsigned char *occ;      // [ntiles] the tile's box holds a deposit
   uint2 *jbb;              // [ntiles] its bounding box: lowest / highest node, one byte per axis
   unsigned char *qstate;   // [ntiles] what the quiet-tile pass left to the push
+  unsigned long long *jfx; // [3][ncell] sorted deposit: the current in 64-bit fixed point (two's complement)
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
 };
@@ -346,8 +347,14 @@ int push_prepare(const GridP &g, int det);
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);
 // recompute the tile marks (g.fnz) from E, B (F[0..5]) after a write from outside the step
 void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s);
-void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3],
-                  float *frame, cudaStream_t s);
+// E <- E + dt (curl B - J).  With jfx (sorted deposit) the current is first
+// formed per cell from the 64-bit fixed-point accumulator (times jinv) plus
+// the antenna sheets at time t (evaluated into ant, [nlas][ncell / n0] FP64),
+// written to J, and the accumulator cleared;
+// without it J is read as the current sum left it.
+void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
+                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, double t, double *ant,
+                  cudaStream_t s);
 long long frame_floats(const GridP &g);
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
                  const LaserP *las, int nlas, double t, cudaStream_t s);

@@ -64,35 +64,145 @@ __global__ void __launch_bounds__(256) k_yee_b(GridP g, float *Bx, float *By, fl
   mark_nonzero<D>(g, C.c, nz);
 }
 
-// E <- E + dt (curl B - J) on interior nodes (backward differences)
+__device__ double laser_value(const LaserP &L, double t, double y, double z) {
+  double ty = y - L.yc, tz = z - L.zc;
+  double tau = t - ty * sin(L.theta);
+  double env;
+  if (L.fwhm > 0) {
+    double d = tau - L.t0;
+    env = exp(-2.0 * 0.69314718055994530942 * d * d / (L.fwhm * L.fwhm));
+  } else if (tau <= 0) {
+    env = 0.0;
+  } else if (tau < L.ramp) {
+    double s = sin(0.5 * 3.14159265358979323846 * tau / L.ramp);
+    env = s * s;
+  } else {
+    env = 1.0;
+  }
+  double prof = 1.0;
+  if (L.waist > 0) {
+    double ey = ty * cos(L.theta);
+    prof = exp(-(ey * ey + tz * tz) / (L.waist * L.waist));
+  }
+  return L.a0 * env * prof * sin(L.omega * tau + L.phase);
+}
+
+struct LaserSet {
+  int n;
+  int lo, hi;  // lowest and highest antenna plane
+  LaserP l[BP_MAX_LASER];
+};
+
+LaserSet make_laser_set(const LaserP *las, int nlas) {
+  LaserSet ls;
+  ls.n = nlas;
+  ls.lo = 1 << 30;
+  ls.hi = -1;
+  for (int i = 0; i < nlas; ++i) {
+    ls.l[i] = las[i];
+    ls.lo = las[i].ia < ls.lo ? las[i].ia : ls.lo;
+    ls.hi = las[i].ia > ls.hi ? las[i].ia : ls.hi;
+  }
+  return ls;
+}
+
+// v * s for a 64-bit fixed-point value v and a power-of-two scale s, rounded
+// once: v = a 2^24 + b with 0 <= b < 2^24, both exact in FP32 while
+// |v| < 2^48, so the fma rounds the exact product (the 64-bit integer
+// conversion would run on the slow FP64 path)
+__device__ __forceinline__ float fx_to_float(long long v, float s) {
+  const float a = (float)(int)(v >> 24);
+  const float b = (float)(int)(v & 0xFFFFFFLL);
+  return fmaf(a, 16777216.0f * s, b * s);
+}
+
+// the antenna sheets' current at time t on their planes, FP64: ant[s][y + ny z]
+// for laser s (the value the current sum adds at cell (L.ia, y, z))
 template <int D>
+__global__ void k_antenna(GridP g, LaserSet las, double t, double *ant) {
+  const long long nyz = g.ncell / g.n[0];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < las.n * nyz;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(q / nyz);
+    const long long yz = q - s * nyz;
+    const int cy = (int)(yz % g.n[1]), cz = (int)(yz / g.n[1]);
+    const LaserP &L = las.l[s];
+    double y = D >= 2 ? (cy + (L.comp == 1 ? 0.5 : 0.0)) * g.dxd[1] : 0.0;
+    double z = D >= 3 ? (cz + (L.comp == 2 ? 0.5 : 0.0)) * g.dxd[2] : 0.0;
+    double amp = -2.0 / g.dxd[0] * (L.comp == 2 ? cos(L.theta) : 1.0);
+    ant[q] = amp * laser_value(L, t, y, z);
+  }
+}
+
+// the antenna part of the sheets covering cell c: only which laser sits on
+// which plane and component is needed here
+struct AntSet {
+  int n, lo, hi;
+  int ia[BP_MAX_LASER], comp[BP_MAX_LASER];
+};
+
+// E <- E + dt (curl B - J) on interior nodes (backward differences).  FX:
+// J^{n+1/2} is formed here from the 64-bit fixed-point accumulator (one
+// rounding: the scale jinv is a power of two) plus the antenna (added in
+// FP64 before the rounding) and stored in J; the launcher then clears the
+// accumulator for the next deposit with one memset (clearing it here, after
+// the loads, ran the kernel at a third of the bandwidth).
+template <int D, bool FX>
 __global__ void __launch_bounds__(256) k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
-                                               const float *__restrict__ By, const float *__restrict__ Bz,
-                                               const float *__restrict__ Jx, const float *__restrict__ Jy,
-                                               const float *__restrict__ Jz) {
+                                               const float *__restrict__ By, const float *__restrict__ Bz, float *Jx,
+                                               float *Jy, float *Jz, unsigned long long *jfx, float jinv,
+                                               AntSet as, const double *__restrict__ ant) {
   Cell C;
   if (!row_cell<D>(g, C)) return;
   const long long q = C.q;
+  float jx, jy, jz;
+  if constexpr (FX) {
+    const long long nc = g.ncell;
+    const long long fx = (long long)jfx[q], fy = (long long)jfx[nc + q], fz = (long long)jfx[2 * nc + q];
+    jx = fx_to_float(fx, jinv);
+    if (as.n > 0 && C.c[0] >= as.lo && C.c[0] <= as.hi) {
+      double ay = 0.0, az = 0.0;
+      const long long yz = q / g.n[0], nyz = g.ncell / g.n[0];
+#pragma unroll
+      for (int k = 0; k < BP_MAX_LASER; ++k) {
+        if (k >= as.n || C.c[0] != as.ia[k]) continue;
+        if (as.comp[k] == 1) ay += ant[k * nyz + yz];
+        else az += ant[k * nyz + yz];
+      }
+      jy = (float)((double)fy * (double)jinv + ay);
+      jz = (float)((double)fz * (double)jinv + az);
+    } else {
+      jy = fx_to_float(fy, jinv);
+      jz = fx_to_float(fz, jinv);
+    }
+    Jx[q] = jx;
+    Jy[q] = jy;
+    Jz[q] = jz;
+  } else {
+    jx = Jx[q];
+    jy = Jy[q];
+    jz = Jz[q];
+  }
   bool nz = false;
   if (!exterior_c<D>(g, 1, C.c) && !mur_node<D>(g, 1, C.c)) {
     float d = 0.0f;
     if (D >= 2) d += (Bz[q] - Bz[q + C.dn[1]]) * g.idx[1];
     if (D >= 3) d -= (By[q] - By[q + C.dn[2]]) * g.idx[2];
-    const float v = Ex[q] + g.dt * (d - Jx[q]);
+    const float v = Ex[q] + g.dt * (d - jx);
     Ex[q] = v;
     nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 2, C.c) && !mur_node<D>(g, 2, C.c)) {
     float d = -(Bz[q] - Bz[q + C.dn[0]]) * g.idx[0];
     if (D >= 3) d += (Bx[q] - Bx[q + C.dn[2]]) * g.idx[2];
-    const float v = Ey[q] + g.dt * (d - Jy[q]);
+    const float v = Ey[q] + g.dt * (d - jy);
     Ey[q] = v;
     nz |= v != 0.0f;
   }
   if (!exterior_c<D>(g, 4, C.c) && !mur_node<D>(g, 4, C.c)) {
     float d = (By[q] - By[q + C.dn[0]]) * g.idx[0];
     if (D >= 2) d -= (Bx[q] - Bx[q + C.dn[1]]) * g.idx[1];
-    const float v = Ez[q] + g.dt * (d - Jz[q]);
+    const float v = Ez[q] + g.dt * (d - jz);
     Ez[q] = v;
     nz |= v != 0.0f;
   }
@@ -206,34 +316,6 @@ __global__ void k_mur(GridP g, float *Ex, float *Ey, float *Ez, const float *fra
 // current: J(cell) = sum of the boxes of the tiles covering the cell, in a
 // fixed order (z, y, x candidates ascending), plus the antenna sheets
 
-__device__ double laser_value(const LaserP &L, double t, double y, double z) {
-  double ty = y - L.yc, tz = z - L.zc;
-  double tau = t - ty * sin(L.theta);
-  double env;
-  if (L.fwhm > 0) {
-    double d = tau - L.t0;
-    env = exp(-2.0 * 0.69314718055994530942 * d * d / (L.fwhm * L.fwhm));
-  } else if (tau <= 0) {
-    env = 0.0;
-  } else if (tau < L.ramp) {
-    double s = sin(0.5 * 3.14159265358979323846 * tau / L.ramp);
-    env = s * s;
-  } else {
-    env = 1.0;
-  }
-  double prof = 1.0;
-  if (L.waist > 0) {
-    double ey = ty * cos(L.theta);
-    prof = exp(-(ey * ey + tz * tz) / (L.waist * L.waist));
-  }
-  return L.a0 * env * prof * sin(L.omega * tau + L.phase);
-}
-
-struct LaserSet {
-  int n;
-  LaserP l[BP_MAX_LASER];
-};
-
 template <int D>
 __global__ void __launch_bounds__(256) k_jsum(GridP g, const float *__restrict__ jbox,
                                               const unsigned char *__restrict__ occ, const uint2 *__restrict__ jbb,
@@ -300,6 +382,77 @@ __global__ void __launch_bounds__(256) k_jsum(GridP g, const float *__restrict__
   Jz[C.q] = sz;
 }
 
+// The same sum with one block per destination tile (2D, 3D): the block's
+// cells are covered only by the boxes of the tile's 3^D neighbours, whose
+// occupancy and bounding boxes are read once into shared memory; each cell
+// adds the covering boxes in the same order as k_jsum (source tiles by
+// ascending z, y, x offset), so the result is the same.
+template <int D>
+__global__ void __launch_bounds__(Geo<D>::L0 * Geo<D>::L1 * Geo<D>::L2)
+    k_jsum_tile(GridP g, const float *__restrict__ jbox, const unsigned char *__restrict__ occ,
+                const uint2 *__restrict__ jbb, float *Jx, float *Jy, float *Jz, LaserSet las, double t) {
+  static_assert(D >= 2, "tile form for 2D and 3D");
+  constexpr int L0 = Geo<D>::L0, L1 = Geo<D>::L1, L2 = Geo<D>::L2;
+  constexpr int NC = D == 3 ? 27 : 9;
+  __shared__ int ctile[NC], corg[NC][3];
+  __shared__ uint2 cbb[NC];
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int tc[3] = {tile % g.nt[0], (tile / g.nt[0]) % g.nt[1], tile / (g.nt[0] * g.nt[1])};
+  if (tid < NC) {
+    const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, D == 3 ? tid / 9 - 1 : 0};
+    bool use = true;
+    int nb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int tu = tc[a] + o[a];
+      // first box cell of the source tile, in the (unwrapped) coordinates of this tile's cells
+      corg[tid][a] = a < D ? tu * g.L[a] - g.oj[a] : 0;
+      nb[a] = tu;
+      if (a < D) {
+        if (g.bc[a] == BP_PERIODIC) nb[a] = wrap_once(tu, g.nt[a]);
+        else use &= tu >= 0 && tu < g.nt[a];
+      }
+    }
+    const int src = nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2]);
+    ctile[tid] = use && occ[src] ? src : -1;
+    cbb[tid] = use ? jbb[src] : make_uint2(0u, 0u);
+  }
+  __syncthreads();
+  const int c[3] = {tc[0] * L0 + tid % L0, tc[1] * L1 + (tid / L0) % L1, tc[2] * L2 + tid / (L0 * L1)};
+  float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+  // unrolled: every covering box's loads are issued before the in-order adds
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int src = ctile[k];
+    if (src < 0) continue;
+    const uint2 bb = cbb[k];
+    const int l0 = c[0] - corg[k][0], l1 = c[1] - corg[k][1], l2 = c[2] - corg[k][2];
+    // outside the tile's deposit box every entry is zero (and unwritten)
+    if (l0 < (int)(bb.x & 255u) || l0 > (int)(bb.y & 255u) || l1 < (int)((bb.x >> 8) & 255u) ||
+        l1 > (int)((bb.y >> 8) & 255u) || l2 < (int)((bb.x >> 16) & 255u) || l2 > (int)((bb.y >> 16) & 255u))
+      continue;
+    const long long l = l0 + (long long)g.jb[0] * (l1 + (long long)g.jb[1] * l2);
+    const float *b = jbox + (size_t)src * 3 * g.jcells;
+    sx += b[l];
+    sy += b[g.jcells + l];
+    sz += b[2 * g.jcells + l];
+  }
+  for (int s = 0; s < las.n; ++s) {
+    const LaserP &L = las.l[s];
+    if (c[0] != L.ia) continue;
+    double y = (c[1] + (L.comp == 1 ? 0.5 : 0.0)) * g.dxd[1];
+    double z = D >= 3 ? (c[2] + (L.comp == 2 ? 0.5 : 0.0)) * g.dxd[2] : 0.0;
+    double amp = -2.0 / g.dxd[0] * (L.comp == 2 ? cos(L.theta) : 1.0);
+    double v = amp * laser_value(L, t, y, z);
+    if (L.comp == 1) sy = (float)((double)sy + v);
+    else sz = (float)((double)sz + v);
+  }
+  const long long q = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+  Jx[q] = sx;
+  Jy[q] = sy;
+  Jz[q] = sz;
+}
+
 __global__ void k_probe(const float *F, const long long *nodes, long long npts, float *buf) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
     buf[q] = F[nodes[q]];
@@ -327,14 +480,42 @@ void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], fl
   else k_yee_b<3><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
 }
 
-void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], const float *const J[3], float *frame,
+void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
+                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, double t, double *ant,
                   cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
   const int nb = row_blocks(g, 256);
-  if (g.D == 1) k_yee_e<1><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
-  else if (g.D == 2) k_yee_e<2><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
-  else k_yee_e<3><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2]);
+  AntSet as;
+  as.n = jfx ? nlas : 0;
+  as.lo = 1 << 30;
+  as.hi = -1;
+  for (int i = 0; i < as.n; ++i) {
+    as.ia[i] = las[i].ia;
+    as.comp[i] = las[i].comp;
+    as.lo = las[i].ia < as.lo ? las[i].ia : as.lo;
+    as.hi = las[i].ia > as.hi ? las[i].ia : as.hi;
+  }
+  if (as.n > 0) {
+    const LaserSet ls = make_laser_set(las, nlas);
+    const long long nant = (long long)nlas * (g.ncell / g.n[0]);
+    if (g.D == 1) k_antenna<1><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
+    else if (g.D == 2) k_antenna<2><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
+    else k_antenna<3><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
+  }
+#define YEE_E(DD, FF) \
+  k_yee_e<DD, FF><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
+  if (jfx) {
+    if (g.D == 1) YEE_E(1, true);
+    else if (g.D == 2) YEE_E(2, true);
+    else YEE_E(3, true);
+  } else {
+    if (g.D == 1) YEE_E(1, false);
+    else if (g.D == 2) YEE_E(2, false);
+    else YEE_E(3, false);
+  }
+#undef YEE_E
+  if (jfx) cudaMemsetAsync(jfx, 0, sizeof(unsigned long long) * 3 * (size_t)g.ncell, s);
   if (nf) {
     int nopen = 0;
     for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
@@ -353,13 +534,16 @@ void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s)
 
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
                  const LaserP *las, int nlas, double t, cudaStream_t s) {
-  LaserSet ls;
-  ls.n = nlas;
-  for (int i = 0; i < nlas; ++i) ls.l[i] = las[i];
-  const int nb = row_blocks(g, 256);
-  if (g.D == 1) k_jsum<1><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
-  else if (g.D == 2) k_jsum<2><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
-  else k_jsum<3><<<nb, 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  const LaserSet ls = make_laser_set(las, nlas);
+  if (g.D == 1) {
+    k_jsum<1><<<row_blocks(g, 256), 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  } else if (g.D == 2) {
+    constexpr int nt = Geo<2>::L0 * Geo<2>::L1 * Geo<2>::L2;
+    k_jsum_tile<2><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  } else {
+    constexpr int nt = Geo<3>::L0 * Geo<3>::L1 * Geo<3>::L2;
+    k_jsum_tile<3><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+  }
 }
 
 // one block row per copy; 16-byte moves when both ends allow, then the tail

@@ -845,9 +845,12 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
   }
   __syncthreads();
   const bool any = sbb[0] != 0xFFFFFFFFu;
-  // the box's occupied part to global memory (compact per-tile layout)
+  // the box's occupied part to global memory.  Sorted mode: each non-zero
+  // node, an exact 64-bit fixed-point sum, is added into the global
+  // fixed-point current (integer adds: the same result in any order; nodes
+  // beyond an open face hold no deposit the field sees).  Atomic mode: the
+  // FP32 box to the tile's slot (compact layout) for the current-sum kernel.
   constexpr int JN = BX::JCOMP;
-  float *out = A.jbox + (size_t)t * 3 * JN;
   if (any) {
     const int lo0 = sbb[0], lo1 = sbb[1], lo2 = sbb[2];
     const int nx = sbb[3] - lo0 + 1, ny = sbb[4] - lo1 + 1, nz = sbb[5] - lo2 + 1;
@@ -856,11 +859,25 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
       const int cc = q / nbox, r = q - cc * nbox;
       const int x = lo0 + r % nx, y = lo1 + (r / nx) % ny, z = lo2 + r / (nx * ny);
       const int k = cc * JC + BX::ji(x, y, z);
-      const int o = cc * JN + x + BX::J0 * (y + BX::J1 * z);
       if constexpr (DET) {
-        out[o] = __ll2float_rn(fx_value(Jsm + k, 3 * JC)) * A.jinv;  // jinv = 2^-k: one rounding
+        const long long v = fx_value(Jsm + k, 3 * JC);
+        if (v == 0) continue;
+        const int bidx[3] = {x, y, z};
+        long long gidx = 0, stride = 1;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          int c = T0[a] - (a < D ? BX::OJ : 0) + bidx[a];
+          if (a < D) {
+            if (g.bc[a] == BP_PERIODIC) c = wrap_once(c, g.n[a]);
+            else ok &= (c >= 0 && c < g.n[a]);
+          }
+          gidx += (long long)c * stride;
+          stride *= g.n[a];
+        }
+        if (ok) atomicAdd(A.jfx + (size_t)cc * g.ncell + gidx, (unsigned long long)v);
       } else {
-        out[o] = Jsm[k];
+        A.jbox[(size_t)t * 3 * JN + cc * JN + x + BX::J0 * (y + BX::J1 * z)] = Jsm[k];
       }
     }
   }
