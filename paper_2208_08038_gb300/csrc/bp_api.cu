@@ -268,6 +268,7 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   if (c->det) {
     c->jfx = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 3 * (size_t)ncell);
     c->ant = (double *)dalloc(c, sizeof(double) * BP_MAX_LASER * (size_t)(ncell / g.n[0]));
+    c->grec_n = (int *)dalloc(c, sizeof(int));
   }
   else c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
@@ -277,7 +278,7 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && !c->ant) || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
+  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n)) || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
       (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
@@ -549,7 +550,22 @@ int bp_add_probe(bp_ctx *c, int comp, const int64_t *nodes, int64_t npts, int64_
 
 namespace {
 
+// sorted mode: room for the general-case records of a step, 1 in 256
+// particles (at least 65,536); a step with more deposits the rest in place
+void ensure_records(bp_ctx *c) {
+  if (!c->det) return;
+  long long n = 0;
+  for (auto &s : c->sp)
+    if (s.loaded) n += s.p.cap;
+  const long long want = std::min<long long>(1LL << 30, std::max<long long>(65536, n / 256));
+  if (c->grec && c->grec_cap >= want) return;
+  if (c->grec) dfree(c, c->grec);
+  c->grec = dalloc(c, push_record_bytes() * (size_t)want);
+  c->grec_cap = c->grec ? want : 0;
+}
+
 PushArgs push_args(bp_ctx *c, int *nsp_out) {
+  ensure_records(c);
   PushArgs A;
   memset(&A, 0, sizeof A);
   int nsp = 0;
@@ -566,6 +582,9 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   }
   A.jbox = c->jbox;
   A.jfx = c->jfx;
+  A.grec = c->grec;
+  A.grec_n = c->grec_n;
+  A.grec_cap = (int)c->grec_cap;
   A.occ = c->occ;
   A.jbb = c->jbb;
   A.qstate = c->qstate;
@@ -719,7 +738,8 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
   launch_yee_e(g, E, cB, J, c->frame, c->det ? c->jfx : nullptr, c->jinv, c->las.data(), (int)c->las.size(), th,
                c->ant, st);
   // quiet-tile pass, push, current sum (atomic deposit) or antenna (sorted deposit, with lasers), Yee (3), Mur
-  c->launches += (c->det ? 5 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0);
+  // (sorted: quiet pass, push, records, antenna if any, Yee (3); atomic: quiet pass, push, current sum, Yee (3))
+  c->launches += (c->det ? 6 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0);
   c->step++;
   if (probes) {
     for (auto &p : c->pr) {

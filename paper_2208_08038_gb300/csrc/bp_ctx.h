@@ -61,6 +61,9 @@ struct bp_ctx {
   float *jbox = nullptr;             // atomic deposit: per-tile FP32 current boxes
   unsigned long long *jfx = nullptr; // sorted deposit: [3][ncell] current in 64-bit fixed point
   double *ant = nullptr;             // sorted deposit: antenna sheet values of a step, [laser][ncell / n0]
+  void *grec = nullptr;              // sorted deposit: general-case deposit records of a step
+  int *grec_n = nullptr;             // their count (device, cleared after each step)
+  long long grec_cap = 0;
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push

@@ -119,6 +119,9 @@ struct PushArgs {
   uint2 *jbb;              // [ntiles] its bounding box: lowest / highest node, one byte per axis
   unsigned char *qstate;   // [ntiles] what the quiet-tile pass left to the push
   unsigned long long *jfx; // [3][ncell] sorted deposit: the current in 64-bit fixed point (two's complement)
+  void *grec;              // sorted deposit: general-case deposit records (grec_cap of them)
+  int *grec_n;             // their count this step (device)
+  int grec_cap;
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
 };
@@ -342,6 +345,7 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t k
 
 void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s);
 size_t push_smem_bytes(const GridP &g, int det);
+size_t push_record_bytes();  // one general-case deposit record
 int push_prepare(const GridP &g, int det);
 
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);

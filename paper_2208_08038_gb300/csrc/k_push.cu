@@ -216,16 +216,19 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
 }
 
 // Deferred general deposits.  A thread whose particle leaves the fast path
-// finishes the push and stores the particle's five-node windows in a
-// shared-memory record; after the main pass the whole block deposits the
-// records row by row (one row: one current component along one line of the
-// window), so the rare general case does not leave most of the block idle.
+// finishes the push and stores the particle's five-node windows in a record,
+// deposited row by row (one row: one current component along one line of the
+// window) by many threads, so the rare general case does not leave most of a
+// block idle.  Sorted mode: the records go to a global buffer and a separate
+// kernel adds their rows to the fixed-point current; atomic mode: a
+// shared-memory queue the block deposits after its pass.
 struct QRec {
   float S0[2][3][5];
   float DS[2][3][5];
   float cq[2][3];  // component along a simulated axis: -qw dx/dt; otherwise qw v
-  int n0[2][3];
+  int n0[2][3];    // window centre, box coordinates
   int nb;
+  int org[3];      // grid coordinates of box node 0 (unwrapped)
 };
 
 // a general-case particle's deposit inputs, gathered into one object inside
@@ -267,9 +270,10 @@ __host__ __device__ constexpr int qrows(int c) {
   return (((c == 0 ? 1 : 0) < D) ? 5 : 1) * (((c == 2 ? 1 : 2) < D) ? 5 : 1);
 }
 
-template <int D, bool DET, typename JT>
-__device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, int row, float scale) {
-  constexpr int jcells = Box<D>::JCELLS;
+// the contributions of one row: sink(c, x, y, z, v) per node, box
+// coordinates, v in the deposit's units before the fixed-point scale
+template <int D, typename Sink>
+__device__ __forceinline__ void record_row(const QRec &R, int b, int c, int row, Sink &&sink) {
   const int p = c == 0 ? 1 : 0, q = c == 2 ? 1 : 2;  // the other two axes, p < q
   const int ip = p < D ? row % 5 : 2, iq = q < D ? row / 5 : 2;
   const float sp = R.S0[b][p][ip], dp = R.DS[b][p][ip], sq = R.S0[b][q][iq], dq = R.DS[b][q][iq];
@@ -281,20 +285,24 @@ __device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, i
   if (p < D) node[p] = R.n0[b][p] - 2 + ip;
   if (q < D) node[q] = R.n0[b][q] - 2 + iq;
   const float cq = R.cq[b][c];
-  JT *Jc = J + c * jcells;
   if (c < D) {
-    const int b0 = R.n0[b][c] - 2;
-    const int stride = c == 0 ? 1 : (c == 1 ? Box<D>::J0 : Box<D>::JP);
-    const int lin0 = Box<D>::ji(c == 0 ? 0 : node[0], c == 1 ? 0 : node[1], c == 2 ? 0 : node[2]);
     float run = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       run += R.DS[b][c][i];
-      jadd<D, DET>(Jc + lin0 + (b0 + i) * stride, cq * run * fac, scale);
+      node[c] = R.n0[b][c] - 2 + i;
+      sink(c, node[0], node[1], node[2], cq * run * fac);
     }
   } else {
-    jadd<D, DET>(Jc + Box<D>::ji(node[0], node[1], node[2]), cq * fac, scale);
+    sink(c, node[0], node[1], node[2], cq * fac);
   }
+}
+
+template <int D, bool DET, typename JT>
+__device__ __forceinline__ void queued_row(JT *J, const QRec &R, int b, int c, int row, float scale) {
+  record_row<D>(R, b, c, row, [&](int cc, int x, int y, int z, float v) {
+    jadd<D, DET>(J + cc * Box<D>::JCELLS + Box<D>::ji(x, y, z), v, scale);
+  });
 }
 
 // a general-case particle when the record queue is full: the same rows, in
@@ -621,15 +629,25 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
       in.qw1 = sp.qw1;
       in.qw2 = sp.qw2;
       in.two = two;
+      // sorted mode: qrec, qn, qmax are the global record buffer, its counter
+      // and capacity; atomic mode: the block's shared-memory queue
       const int slot = atomicAdd(qn, 1);
-      if (slot < qmax) queue_record<D>(qrec[slot], in);
-      else deposit_in_place<D, DET, JT>(Jsm, in, scale);
-      int n0[3];
-      window_centre<D>(f, d, n0);
-      bb_add<D>(blo, bhi, n0, 2, 2);
-      if (two) {
-        window_centre<D>(f2, d2, n0);
+      const bool queued = slot < qmax;
+      if (queued) {
+        queue_record<D>(qrec[slot], in);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qrec[slot].org[a] = T0[a] - (a < D ? Box<D>::OJ : 0);
+      } else {
+        deposit_in_place<D, DET, JT>(Jsm, in, scale);
+      }
+      if (!DET || !queued) {
+        int n0[3];
+        window_centre<D>(f, d, n0);
         bb_add<D>(blo, bhi, n0, 2, 2);
+        if (two) {
+          window_centre<D>(f2, d2, n0);
+          bb_add<D>(blo, bhi, n0, 2, 2);
+        }
       }
     }
   }
@@ -800,8 +818,10 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
     }
   }
   const bool nofield = !__syncthreads_or(nz);
-  QRec *qrec = reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
-  constexpr int QMAX = push_qmax(D);
+  QRec *qrec = DET ? reinterpret_cast<QRec *>(A.grec)
+                   : reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
+  int *const qcount = DET ? A.grec_n : nullptr;
+  const int qmax = DET ? A.grec_cap : push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
   __shared__ int qn;
   __shared__ unsigned sbb[6];
@@ -818,12 +838,13 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
     for (long long i = beg + tid; i < end; i += bs) {
       if (moved && quiet_done(A.p[s], i)) continue;
       if (i + bs < end) prefetch_particle<D>(A.p[s], i + bs, A.sp[s].kind == BP_TWO_BODY);
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec, &qn, QMAX, blo, bhi,
-                                nofield);
+      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec,
+                                DET ? qcount : &qn, qmax, blo, bhi, nofield);
     }
     __syncthreads();
+    if constexpr (DET) continue;  // the records are deposited by k_records
     // the deferred general deposits, one row per thread
-    const int nitem = min(qn, QMAX) * 2 * IPB;
+    const int nitem = min(qn, qmax) * 2 * IPB;
     for (int k = tid; k < nitem; k += bs) {
       const int e = k / (2 * IPB), rem = k - e * (2 * IPB), b = rem / IPB, it = rem - b * IPB;
       if (b >= qrec[e].nb) continue;
@@ -887,11 +908,52 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
   }
 }
 
+// Sorted mode: the records' rows added to the fixed-point current.  Each
+// contribution is rounded to the fixed-point unit as the shared-memory path
+// rounds it (the same value, so the current does not depend on which path a
+// particle took); nodes beyond an open face are dropped as the push drops them.
+template <int D>
+__global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict__ rec, const int *__restrict__ count,
+                                                 int cap, unsigned long long *jfx, float scale) {
+  constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
+  const long long n = (long long)min(*count, cap) * 2 * IPB;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(k / (2 * IPB)), rem = (int)(k - (long long)e * 2 * IPB), b = rem / IPB, it = rem - b * IPB;
+    const QRec &R = rec[e];
+    if (b >= R.nb) continue;
+    const int c = it < NR0 ? 0 : (it < NR0 + NR1 ? 1 : 2);
+    const int row = it - (c == 0 ? 0 : (c == 1 ? NR0 : NR0 + NR1));
+    record_row<D>(R, b, c, row, [&](int cc, int x, int y, int z, float v) {
+      const float vs = v * scale;
+      if (fabsf(vs) <= 0.5f) return;  // rounds to zero
+      const int bx[3] = {x, y, z};
+      long long gidx = 0, stride = 1;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int cg = R.org[a] + bx[a];
+        if (a < D) {
+          if (g.bc[a] == BP_PERIODIC) cg = wrap_once(cg, g.n[a]);
+          else ok &= (cg >= 0 && cg < g.n[a]);
+        }
+        gidx += (long long)cg * stride;
+        stride *= g.n[a];
+      }
+      if (ok) atomicAdd(jfx + (size_t)cc * g.ncell + gidx, (unsigned long long)f2ll_rn(vs));
+    });
+  }
+}
+
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
   k_push_quiet<D><<<g.ntiles, 256, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
   k_push<D, DET><<<g.ntiles, push_threads(D), smem, s>>>(g, a);
+  if constexpr (DET) {
+    k_records<D><<<152 * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
+                                        a.jscale);
+    cudaMemsetAsync(a.grec_n, 0, sizeof(int), s);
+  }
 }
 
 template <int D, bool DET>
@@ -908,8 +970,11 @@ size_t push_smem_bytes(const GridP &g, int det) {
   if (g.D == 1) { jc = Box<1>::JCELLS; gc = Box<1>::GCELLS; }
   if (g.D == 2) { jc = Box<2>::JCELLS; gc = Box<2>::GCELLS; }
   if (g.D == 3) { jc = Box<3>::JCELLS; gc = Box<3>::GCELLS; }
-  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc + sizeof(QRec) * (size_t)push_qmax(g.D);
+  // the sorted mode keeps its records in global memory
+  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc + (det ? 0 : sizeof(QRec) * (size_t)push_qmax(g.D));
 }
+
+size_t push_record_bytes() { return sizeof(QRec); }
 
 int push_prepare(const GridP &g, int det) {
   switch (g.D * 2 + (det ? 1 : 0)) {
