@@ -280,6 +280,18 @@ int64_t bp_kernel_launches(const bp_ctx *ctx);
 int bp_time_push(bp_ctx *ctx, int enable);
 int bp_push_time(bp_ctx *ctx, double *ms, int64_t *launches);
 
+/* Capacity of the sorted deposit's general-case record buffer, in records
+ * (BP_DEPOSIT_SORTED only).  A particle whose positions change their nearest
+ * node in a step (Esirkepov's five-node case) leaves a record that a
+ * separate kernel adds to the fixed-point current; when a step has more
+ * such particles than the capacity, the rest deposit in place.  Both paths
+ * add the same integers, so the fields do not depend on the capacity.
+ * n > 0 fixes the capacity (at least 1); n = 0 restores the default (one
+ * record per 256 particles, at least 65,536).  Takes effect at the next
+ * bp_step; returns BP_ERR_ARG for n < 0 or a context in atomic mode,
+ * BP_ERR_OOM if the buffer cannot be allocated then. */
+int bp_set_record_capacity(bp_ctx *ctx, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

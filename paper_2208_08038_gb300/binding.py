@@ -92,6 +92,7 @@ _SIGS = {
     "bp_backward": (_i, [_p, _i, _p, _i, _p, _p, _i64, _p]),
     "bp_kernel_launches": (_i64, [_p]),
     "bp_time_push": (_i, [_p, _i]),
+    "bp_set_record_capacity": (_i, [_p, C.c_int64]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
 }
 
@@ -354,6 +355,9 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self._L.bp_kernel_launches(self._h))
+
+    def set_record_capacity(self, n: int):
+        self._check(self._L.bp_set_record_capacity(self._h, int(n)), "bp_set_record_capacity")
 
     def time_push(self, enable: bool):
         self._check(self._L.bp_time_push(self._h, int(enable)), "bp_time_push")

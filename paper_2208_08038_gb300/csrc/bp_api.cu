@@ -557,8 +557,9 @@ void ensure_records(bp_ctx *c) {
   long long n = 0;
   for (auto &s : c->sp)
     if (s.loaded) n += s.p.cap;
-  const long long want = std::min<long long>(1LL << 30, std::max<long long>(65536, n / 256));
-  if (c->grec && c->grec_cap >= want) return;
+  const long long want =
+      c->grec_fixed > 0 ? c->grec_fixed : std::min<long long>(1LL << 30, std::max<long long>(65536, n / 256));
+  if (c->grec && (c->grec_fixed > 0 ? c->grec_cap == want : c->grec_cap >= want)) return;
   if (c->grec) dfree(c, c->grec);
   c->grec = dalloc(c, push_record_bytes() * (size_t)want);
   c->grec_cap = c->grec ? want : 0;
@@ -1136,6 +1137,14 @@ int64_t bp_kernel_launches(const bp_ctx *c) {
   // re-sorts run inside the step graph are counted on the device
   const long long runs = c->sort_runs ? *(volatile int *)c->sort_runs : 0;
   return c->launches + runs * ((long long)c->sort_nsp * sort_launches() + 1);
+}
+
+int bp_set_record_capacity(bp_ctx *c, int64_t n) {
+  if (!c || n < 0 || !c->det) return BP_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  c->grec_fixed = std::min<long long>(n, 1LL << 30);
+  ensure_records(c);
+  return (c->grec || c->sp.empty()) ? BP_OK : fail(c, BP_ERR_OOM, "record buffer");
 }
 
 int bp_time_push(bp_ctx *c, int enable) {

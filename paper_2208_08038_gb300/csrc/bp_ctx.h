@@ -64,6 +64,7 @@ struct bp_ctx {
   void *grec = nullptr;              // sorted deposit: general-case deposit records of a step
   int *grec_n = nullptr;             // their count (device, cleared after each step)
   long long grec_cap = 0;
+  long long grec_fixed = 0;          // capacity set by the caller (0: default)
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push

@@ -710,19 +710,19 @@ __device__ __forceinline__ void zero_box(JT *J, int n, int tid, int bs) {
 // A tile whose 3^D neighbouring tiles have never held a non-zero E or B has
 // an all-zero field box (the box lies inside them).  This light kernel takes
 // such tiles before the push: it moves their quiet ions (the drift alone) at
-// high occupancy and leaves a state per tile:
+// high occupancy (eight 128-thread blocks per SM) and leaves a state per tile:
 //   QS_PUSH  the push kernel does the whole tile (fields may be non-zero),
 //   QS_DONE  every particle moved, nothing deposited (occ = 0),
 //   QS_REST  the quiet ions moved; the push does the others without fields.
 constexpr unsigned char QS_PUSH = 0, QS_DONE = 1, QS_REST = 2;
 
 template <int D>
-__global__ void __launch_bounds__(256, 3) k_push_quiet(GridP g, PushArgs A) {
+__global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
   static_assert(Box<D>::OG <= Geo<D>::L0 && Box<D>::G0 - Box<D>::OG <= 2 * Geo<D>::L0 &&
                     (D < 2 || (Box<D>::OG <= Geo<D>::L1 && Box<D>::G1 - Box<D>::OG <= 2 * Geo<D>::L1)) &&
                     (D < 3 || (Box<D>::OG <= Geo<D>::L2 && Box<D>::G2 - Box<D>::OG <= 2 * Geo<D>::L2)),
                 "field box within the neighbouring tiles");
-  constexpr int QB = 4;
+  constexpr int QB = 2;  // particles in flight per thread (measured best of 1, 2, 4, 8)
   const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
   int tc[3];
@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict
 
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
-  k_push_quiet<D><<<g.ntiles, 256, 0, s>>>(g, a);
+  k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
   k_push<D, DET><<<g.ntiles, push_threads(D), smem, s>>>(g, a);
   if constexpr (DET) {

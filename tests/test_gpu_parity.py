@@ -135,6 +135,26 @@ def test_written_field_reaches_the_push():
     ora.close()
 
 
+def test_record_capacity_does_not_change_the_fields():
+    """Sorted mode: a particle whose nearest node changes in a step leaves a
+    five-node record that a separate kernel adds to the fixed-point current,
+    or deposits in place when the record buffer is full.  Both add the same
+    integers, so with room for a single record (nearly every such particle
+    deposited in place) the fields are bit-identical to the default."""
+    wl = small_3d(sigma=0.2, periodic=True)  # hot ions: many nearest-node changes per step
+    outs = []
+    for cap in (0, 1):
+        gpu, _, _ = gpu_from_workload(wl)
+        if cap:
+            gpu.set_record_capacity(cap)
+        gpu.step(10)
+        gpu.sync()
+        outs.append(gpu.fields())
+        gpu.close()
+    assert np.abs(outs[0][6:9]).max() > 0
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_3d_thermal_parity(mode):
     wl = small_3d()
