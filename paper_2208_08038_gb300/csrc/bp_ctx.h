@@ -68,6 +68,7 @@ struct bp_ctx {
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push
+  int *tile_ctr = nullptr;           // the push's tile counter
   float *frame = nullptr;
   int *status = nullptr;
   std::vector<bp_species_state> sp;

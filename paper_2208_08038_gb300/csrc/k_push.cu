@@ -765,8 +765,9 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
   }
 }
 
+// one tile of the push (the block's work for tile t)
 template <int D, bool DET>
-__global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
+__device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, const int t) {
   using JT = typename std::conditional<DET, unsigned int, float>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   using BX = Box<D>;
@@ -774,7 +775,6 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
   constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * JC;  // low (and high) words
   JT *Jsm = reinterpret_cast<JT *>(smem);
   float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
-  const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
   const unsigned char qs = A.qstate[t];
   if (qs == QS_DONE) return;
@@ -908,6 +908,22 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
   }
 }
 
+// The push: persistent blocks (as many as fit on the GPU at once) take tiles
+// in order from a counter, so a block's shared memory and setup are reused
+// from tile to tile instead of a block being launched per tile.
+template <int D, bool DET>
+__global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
+  __shared__ int next;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with the shared memory
+    if (threadIdx.x == 0) next = atomicAdd(A.tile_ctr, 1);
+    __syncthreads();
+    const int t = next;
+    if (t >= g.ntiles) return;
+    push_tile<D, DET>(g, A, t);
+  }
+}
+
 // Sorted mode: the records' rows added to the fixed-point current.  Each
 // contribution is rounded to the fixed-point unit as the shared-memory path
 // rounds it (the same value, so the current does not depend on which path a
@@ -948,7 +964,17 @@ template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
   k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
-  k_push<D, DET><<<g.ntiles, push_threads(D), smem, s>>>(g, a);
+  // resident blocks of the GPU (queried once per instantiation)
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push<D, DET>, push_threads(D), smem);
+    blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), s);
+  k_push<D, DET><<<blocks < g.ntiles ? blocks : g.ntiles, push_threads(D), smem, s>>>(g, a);
   if constexpr (DET) {
     k_records<D><<<152 * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
                                         a.jscale);
