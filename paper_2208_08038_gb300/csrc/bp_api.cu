@@ -276,10 +276,12 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   g.fnz = (unsigned char *)dalloc(c, g.ntiles);  // zero fields: no tile marked
   c->qstate = (unsigned char *)dalloc(c, g.ntiles);
   c->tile_ctr = (int *)dalloc(c, sizeof(int));
+  c->tile_list = (int *)dalloc(c, sizeof(int) * g.ntiles);
+  c->tile_n = (int *)dalloc(c, sizeof(int));
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n)) || !c->tile_ctr || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
+  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
       (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
@@ -591,6 +593,8 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   A.jbb = c->jbb;
   A.qstate = c->qstate;
   A.tile_ctr = c->tile_ctr;
+  A.tile_list = c->tile_list;
+  A.tile_n = c->tile_n;
   A.status = c->status;
   A.jscale = c->jscale;
   A.jinv = c->jinv;

@@ -69,6 +69,8 @@ struct bp_ctx {
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push
   int *tile_ctr = nullptr;           // the push's tile counter
+  int *tile_list = nullptr;          // tiles left for the push by the quiet-tile pass, and their number
+  int *tile_n = nullptr;
   float *frame = nullptr;
   int *status = nullptr;
   std::vector<bp_species_state> sp;

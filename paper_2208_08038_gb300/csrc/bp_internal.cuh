@@ -119,7 +119,9 @@ struct PushArgs {
   uint2 *jbb;              // [ntiles] its bounding box: lowest / highest node, one byte per axis
   unsigned char *qstate;   // [ntiles] what the quiet-tile pass left to the push
   unsigned long long *jfx; // [3][ncell] sorted deposit: the current in 64-bit fixed point (two's complement)
-  int *tile_ctr;           // the push's next tile (cleared before each launch)
+  int *tile_list;          // [ntiles] tiles the quiet-tile pass left for the push
+  int *tile_n;             // their number (cleared before the quiet-tile pass)
+  int *tile_ctr;           // the push's next list entry (cleared before each launch)
   void *grec;              // sorted deposit: general-case deposit records (grec_cap of them)
   int *grec_n;             // their count this step (device)
   int grec_cap;

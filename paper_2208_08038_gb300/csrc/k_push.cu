@@ -744,7 +744,10 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
     if (use) marked = g.fnz[nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2])] != 0;
   }
   if (__syncthreads_or(marked)) {
-    if (tid == 0) A.qstate[t] = QS_PUSH;
+    if (tid == 0) {
+      A.qstate[t] = QS_PUSH;
+      A.tile_list[atomicAdd(A.tile_n, 1)] = t;
+    }
     return;
   }
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
@@ -762,40 +765,25 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
   if (tid == 0) {
     A.qstate[t] = left ? QS_REST : QS_DONE;
     if (!left) A.occ[t] = 0;
+    else A.tile_list[atomicAdd(A.tile_n, 1)] = t;
   }
 }
 
-// one tile of the push (the block's work for tile t)
-template <int D, bool DET>
-__device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, const int t) {
-  using JT = typename std::conditional<DET, unsigned int, float>::type;
-  extern __shared__ __align__(16) unsigned char smem[];
+// Staging of a tile's field box (E, B of the tile plus halo; zero outside
+// open faces) by asynchronous copies into shared memory: no registers held,
+// so the copies can run while the block finishes the previous tile.  A
+// QS_REST tile's box is all zero and is not staged.
+template <int D>
+__device__ __forceinline__ void stage_issue(const GridP &g, const PushArgs &A, int t, float *Gsm) {
   using BX = Box<D>;
-  constexpr int JC = BX::JCELLS, GC = BX::GCELLS;
-  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * JC;  // low (and high) words
-  JT *Jsm = reinterpret_cast<JT *>(smem);
-  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
-  const int tid = threadIdx.x, bs = blockDim.x;
-  const unsigned char qs = A.qstate[t];
-  if (qs == QS_DONE) return;
-  int total = 0;
-  for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
-  if (total == 0) {
-    if (tid == 0) A.occ[t] = 0;
-    return;
-  }
-  int tc[3];
-  tc[0] = t % g.nt[0];
-  tc[1] = (t / g.nt[0]) % g.nt[1];
-  tc[2] = t / (g.nt[0] * g.nt[1]);
+  constexpr int GC = BX::GCELLS;
+  if (A.qstate[t] != QS_PUSH) return;
+  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  zero_box<DET>(Jsm, 3 * JC, tid, bs);
-  // stage E, B of the tile plus halo (zero outside open faces); a QS_REST
-  // tile's box is all zero and is not staged
-  bool nz = false;
-  for (int q = tid; qs == QS_PUSH && q < BX::GCOMP; q += bs) {
-    int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
-    int bidx[3] = {b0, b1, b2};
+  const unsigned gbase = (unsigned)__cvta_generic_to_shared(Gsm);
+  for (int q = threadIdx.x; q < BX::GCOMP; q += blockDim.x) {
+    const int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
+    const int bidx[3] = {b0, b1, b2};
     const int si = BX::gi(b0, b1, b2);
     long long gi = 0, stride = 1;
     bool ok = true;
@@ -809,14 +797,65 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
       gi += (long long)x * stride;
       stride *= g.n[a];
     }
+    if (!ok) gi = 0;  // a zero fill: nothing is read
+    const unsigned src = ok ? 4u : 0u;
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      const float ev = ok ? __ldg(A.E[cc] + gi) : 0.0f, bv = ok ? __ldg(A.B[cc] + gi) : 0.0f;
-      Gsm[cc * GC + si] = ev;
-      Gsm[(3 + cc) * GC + si] = bv;
-      nz |= (ev != 0.0f) || (bv != 0.0f);
+    for (int cc = 0; cc < 6; ++cc) {
+      const float *gp = (cc < 3 ? A.E[cc] : A.B[cc - 3]) + gi;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(gbase + 4u * (unsigned)(cc * GC + si)),
+                   "l"(gp), "r"(src)
+                   : "memory");
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// wait for this thread's copies; whether any of them is non-zero
+template <int D>
+__device__ __forceinline__ bool stage_done(const PushArgs &A, int t, const float *Gsm) {
+  using BX = Box<D>;
+  constexpr int GC = BX::GCELLS;
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  bool nz = false;
+  if (A.qstate[t] != QS_PUSH) return nz;
+  for (int q = threadIdx.x; q < BX::GCOMP; q += blockDim.x) {
+    const int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
+    const int si = BX::gi(b0, b1, b2);
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) nz |= Gsm[cc * GC + si] != 0.0f;
+  }
+  return nz;
+}
+
+// one tile of the push (the block's work for tile t)
+template <int D, bool DET, typename AfterLoop>
+__device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, const int t, AfterLoop &&after_loop) {
+  using JT = typename std::conditional<DET, unsigned int, float>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  using BX = Box<D>;
+  constexpr int JC = BX::JCELLS, GC = BX::GCELLS;
+  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * JC;  // low (and high) words
+  JT *Jsm = reinterpret_cast<JT *>(smem);
+  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const unsigned char qs = A.qstate[t];
+  int total = 0;
+  for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
+  if (qs == QS_DONE || total == 0) {
+    stage_done<D>(A, t, Gsm);  // this tile's copies land before the next tile's are issued
+    __syncthreads();
+    if (tid == 0 && qs != QS_DONE) A.occ[t] = 0;
+    after_loop();
+    return;
+  }
+  int tc[3];
+  tc[0] = t % g.nt[0];
+  tc[1] = (t / g.nt[0]) % g.nt[1];
+  tc[2] = t / (g.nt[0] * g.nt[1]);
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  zero_box<DET>(Jsm, 3 * JC, tid, bs);
+  // the field box was staged asynchronously (stage_issue) by the caller
+  const bool nz = stage_done<D>(A, t, Gsm);
   const bool nofield = !__syncthreads_or(nz);
   QRec *qrec = DET ? reinterpret_cast<QRec *>(A.grec)
                    : reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
@@ -854,6 +893,8 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
     }
     __syncthreads();
   }
+  // the field box is no longer needed: the caller may start staging the next tile
+  after_loop();
   // the deposits' bounding box over the block
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -908,19 +949,29 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
   }
 }
 
-// The push: persistent blocks (as many as fit on the GPU at once) take tiles
-// in order from a counter, so a block's shared memory and setup are reused
-// from tile to tile instead of a block being launched per tile.
+// The push: persistent blocks (as many as fit on the GPU at once) take the
+// tiles the quiet-tile pass left (its list) in order from a counter, so a
+// block's shared memory and setup are reused from tile to tile, and the next
+// tile's field box is staged while the block finishes the current one.
 template <int D, bool DET>
 __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * Box<D>::JCELLS;
+  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
   __shared__ int next;
-  for (;;) {
-    __syncthreads();  // the previous tile is done with the shared memory
-    if (threadIdx.x == 0) next = atomicAdd(A.tile_ctr, 1);
+  const int nlist = *A.tile_n;
+  auto grab = [&]() {
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(A.tile_ctr, 1);
+      next = k < nlist ? A.tile_list[k] : -1;
+    }
     __syncthreads();
-    const int t = next;
-    if (t >= g.ntiles) return;
-    push_tile<D, DET>(g, A, t);
+    if (next >= 0) stage_issue<D>(g, A, next, Gsm);
+  };
+  grab();
+  for (int t = next; t >= 0; t = next) {
+    push_tile<D, DET>(g, A, t, grab);
+    __syncthreads();  // every thread has read `next` before it changes
   }
 }
 
@@ -962,6 +1013,7 @@ __global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict
 
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
+  cudaMemsetAsync(a.tile_n, 0, sizeof(int), s);
   k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
   size_t smem = push_smem_bytes(g, DET);
   // resident blocks of the GPU (queried once per instantiation)
