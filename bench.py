@@ -35,7 +35,7 @@ METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/
 # dram__bytes_write.sum, 1 pass per launch).  It
 # falls from 27.5 GB late in the run to 18.3 GB at its start, where most
 # ions are quiet and write only their cell and offset.
-PUSH_TRAFFIC = 23.22e9
+PUSH_TRAFFIC = 23.23e9
 UNIT = "ion-pushes/s"
 
 
