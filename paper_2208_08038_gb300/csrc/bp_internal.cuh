@@ -262,6 +262,22 @@ __device__ __forceinline__ void fx_add(unsigned int *lo, int hoff, float v) {
   const int hh = __float_as_int(hs) - 0x4B400000;
   if (hh) atomicAdd(reinterpret_cast<int *>(lo + hoff), hh);
 }
+// fx_add of two values at two nodes (lo0, lo1; high words hoff later), the
+// FP32 part on packed pairs: each lane rounds exactly as fx_add does
+__device__ __forceinline__ void fx_add2(unsigned int *lo0, unsigned int *lo1, int hoff, float2 v) {
+  constexpr float M = 12582912.0f;
+  const float2 hs = __ffma2_rn(v, make_float2(1.52587890625e-05f, 1.52587890625e-05f), make_float2(M, M));
+  const float2 h = __fadd2_rn(hs, make_float2(-M, -M));
+  const float2 r = __ffma2_rn(h, make_float2(-65536.0f, -65536.0f), v);
+  const float2 rm = __fadd2_rn(r, make_float2(M, M));
+  const int l0 = __float_as_int(rm.x) - 0x4B400000, l1 = __float_as_int(rm.y) - 0x4B400000;
+  const int h0 = __float_as_int(hs.x) - 0x4B400000, h1 = __float_as_int(hs.y) - 0x4B400000;
+  atomicAdd(reinterpret_cast<int *>(lo0), l0);
+  atomicAdd(reinterpret_cast<int *>(lo1), l1);
+  if (h0) atomicAdd(reinterpret_cast<int *>(lo0 + hoff), h0);
+  if (h1) atomicAdd(reinterpret_cast<int *>(lo1 + hoff), h1);
+}
+
 // the value of a pair (both words initialised to 0)
 __device__ __forceinline__ long long fx_value(const unsigned int *lo, int hoff) {
   return (long long)(int)lo[hoff] * 65536LL + (long long)(int)lo[0];

@@ -215,6 +215,75 @@ __device__ __forceinline__ void esirkepov3(JT *__restrict__ J, const int n[3], c
   }
 }
 
+__device__ __forceinline__ float2 sel3(int k, const float2 *a) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); }
+
+// esirkepov3 for a two-body ion in 3D, sorted mode, on Blackwell's packed
+// FP32 pairs (FFMA2): the two bodies in the lanes of every setup term and of
+// each row's transverse factor F; a node's value is the bodies' two products
+// (one packed multiply) added, and a row's two nodes go through one packed
+// fixed-point split (fx_add2).  The outer loops stay rolled as in the scalar
+// form (code size).
+__device__ __forceinline__ void esirkepov3_p3(unsigned int *__restrict__ J, const int n[3], const float (*xi)[3],
+                                              const float (*de)[3], const float *qw, const float dxdt[3],
+                                              float scale) {
+  constexpr int jcells = Box<3>::JCELLS;
+  constexpr int hoff = 3 * jcells;
+  const float2 K12 = make_float2(1.0f / 12.0f, 1.0f / 12.0f), H = make_float2(0.5f, 0.5f);
+  const float2 M1 = make_float2(-1.0f, -1.0f), ONE = make_float2(1.0f, 1.0f);
+  float2 A[3][3], DS[3][3], DK[3][3], cP[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 x = make_float2(xi[0][a], xi[1][a]), d = make_float2(de[0][a], de[1][a]);
+    float2 S0[3];
+    qweights2(x, S0);
+    const float2 u = __fadd2_rn(__fadd2_rn(x, x), d);
+    float2 dd[3];
+    dd[0] = __fmul2_rn(__fmul2_rn(d, make_float2(-0.5f, -0.5f)), __ffma2_rn(u, M1, ONE));
+    dd[1] = __fmul2_rn(__fmul2_rn(d, M1), u);
+    dd[2] = __fmul2_rn(__fmul2_rn(d, H), __fadd2_rn(u, ONE));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      A[a][i] = __ffma2_rn(H, dd[i], S0[i]);
+      DS[a][i] = dd[i];
+      DK[a][i] = __fmul2_rn(K12, dd[i]);
+    }
+    const float2 c = make_float2(-qw[0] * dxdt[a] * scale, -qw[1] * dxdt[a] * scale);
+    cP[a][0] = __fmul2_rn(c, dd[0]);
+    cP[a][1] = __fmul2_rn(__fmul2_rn(c, M1), dd[2]);
+  }
+  unsigned int *Jx = J, *Jy = J + jcells, *Jz = J + 2 * jcells;
+  const int bx = n[0] - 1, by = n[1] - 1, bz = n[2] - 1;
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    const float2 az = sel3(k, A[2]), dz = sel3(k, DS[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float2 F = __ffma2_rn(A[1][j], az, __fmul2_rn(DK[1][j], dz));
+      const float2 t0 = __fmul2_rn(cP[0][0], F), t1 = __fmul2_rn(cP[0][1], F);
+      unsigned int *p = Jx + Box<3>::ji(bx, by + j, bz + k);
+      fx_add2(p, p + 1, hoff, make_float2(__fadd_rn(t0.x, t0.y), __fadd_rn(t1.x, t1.y)));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float2 F = __ffma2_rn(A[0][i], az, __fmul2_rn(DK[0][i], dz));
+      const float2 t0 = __fmul2_rn(cP[1][0], F), t1 = __fmul2_rn(cP[1][1], F);
+      unsigned int *p = Jy + Box<3>::ji(bx + i, by, bz + k);
+      fx_add2(p, p + Box<3>::J0, hoff, make_float2(__fadd_rn(t0.x, t0.y), __fadd_rn(t1.x, t1.y)));
+    }
+  }
+#pragma unroll 1
+  for (int j = 0; j < 3; ++j) {
+    const float2 ay = sel3(j, A[1]), dy = sel3(j, DS[1]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float2 F = __ffma2_rn(A[0][i], ay, __fmul2_rn(DK[0][i], dy));
+      const float2 t0 = __fmul2_rn(cP[2][0], F), t1 = __fmul2_rn(cP[2][1], F);
+      unsigned int *p = Jz + Box<3>::ji(bx + i, by + j, bz);
+      fx_add2(p, p + Box<3>::JP, hoff, make_float2(__fadd_rn(t0.x, t0.y), __fadd_rn(t1.x, t1.y)));
+    }
+  }
+}
+
 // Deferred general deposits.  A thread whose particle leaves the fast path
 // finishes the push and stores the particle's five-node windows in a record,
 // deposited row by row (one row: one current component along one line of the
@@ -616,7 +685,10 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
         dd[0][a] = de1[a];
         dd[1][a] = de2[a];
       }
-      if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+      if constexpr (D == 3 && DET) {
+        if (two) esirkepov3_p3(Jsm, nn, xi, dd, qw, dxdt, scale);
+        else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
+      } else if (two) esirkepov3<D, DET, 2>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
       else esirkepov3<D, DET, 1>(Jsm, nn, xi, dd, qw, vv, dxdt, scale);
       bb_add<D>(blo, bhi, nn, 1, 1);
     } else {
