@@ -1,8 +1,10 @@
 // k_fields.cu -- Yee FDTD for the vacuum Maxwell equations (the medium's
 // response comes only from the particles' current, arXiv 2208.08038 Sec. 3.1),
-// first-order Mur open faces, the fixed-order sum of the per-tile current
-// boxes plus the laser antenna, and probes.  All FP32, memory bound: one
-// thread per cell, coalesced along x.
+// first-order Mur open faces, the laser antenna, the current (sorted deposit:
+// formed in the E update from the 64-bit fixed-point accumulator; atomic
+// deposit: the fixed-order sum of the per-tile boxes), the tile marks of
+// non-zero fields, and probes.  All FP32, memory bound: one thread per cell,
+// coalesced along x.
 #include "bp_internal.cuh"
 
 namespace {

@@ -1,21 +1,30 @@
-// k_push.cu -- the per-tile particle kernel: gather at both bodies, internal
+// k_push.cu -- the particle step: gather at both bodies, internal
 // modified-Coulomb field, relativistic Boris push of both bodies, drift and
-// Esirkepov (quadratic shape) current deposit into a shared-memory tile.
+// Esirkepov (quadratic shape) current deposit.
 //
 // Method: arXiv 2208.08038 Sec. 2 (two-body macro-ion, Boris equations,
-// modified Coulomb force, body currents q v / dV).  One CTA per tile:
-//   1. stage E and B of the tile plus halo in shared memory (FP32),
-//   2. push every particle of the tile (all species), accumulating the
-//      current of both bodies in a shared-memory box (tile + halo).  A
-//      particle whose bodies keep their nearest nodes deposits on the spot
-//      (three-node windows); the others leave a five-node record that the
-//      whole block deposits after the pass.  The box holds
-//        BP_DEPOSIT_SORTED: 64-bit fixed point (integer adds are associative,
-//                           so the box is bit-identical whatever the order),
-//        BP_DEPOSIT_ATOMIC: FP32 shared atomics,
-//   3. write the box to the tile's slot of the global box array; the
-//      current-sum kernel adds the overlapping boxes of neighbouring tiles
-//      in a fixed order.
+// modified Coulomb force, body currents q v / dV).  Per step:
+//   k_push_quiet  tiles whose neighbourhood never held a field (the field
+//                 kernels' tile marks): their co-moving neutral ions only
+//                 drift; the other tiles go on a list for the push,
+//   k_push        persistent blocks walk that list; per tile:
+//     1. stage E and B of the tile plus halo in shared memory (FP32, by
+//        asynchronous copies issued while the block finishes the previous
+//        tile),
+//     2. push every particle of the tile (all species), accumulating the
+//        current of both bodies in a shared-memory box (tile + halo).  A
+//        particle whose bodies keep their nearest nodes deposits on the spot
+//        (three-node windows); the others leave a five-node record.  The box
+//        holds
+//          BP_DEPOSIT_SORTED: 64-bit fixed point (integer adds are
+//                             associative: the same sums in any order),
+//          BP_DEPOSIT_ATOMIC: FP32 shared atomics,
+//     3. sorted mode: add every non-zero node of the box to the global 64-bit
+//        fixed-point current; atomic mode: write the box to the tile's slot
+//        for the current-sum kernel (and deposit the records from a
+//        shared-memory queue before that),
+//   k_records     sorted mode: the records' rows added to the fixed-point
+//                 current.
 #include <type_traits>
 
 #include "bp_internal.cuh"
