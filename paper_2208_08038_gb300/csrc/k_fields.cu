@@ -35,7 +35,7 @@ __device__ __forceinline__ int pat_e(int comp) { return 1 << comp; }
 
 // B <- B - h curl E (forward differences to the B locations)
 template <int D>
-__global__ void __launch_bounds__(256) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
+__global__ void __launch_bounds__(128) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
                                                const float *__restrict__ Ey, const float *__restrict__ Ez, float h) {
   Cell C;
   if (!row_cell<D>(g, C)) return;
@@ -150,7 +150,7 @@ struct AntSet {
 // accumulator for the next deposit with one memset (clearing it here, after
 // the loads, ran the kernel at a third of the bandwidth).
 template <int D, bool FX>
-__global__ void __launch_bounds__(256) k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
+__global__ void __launch_bounds__(128) k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
                                                const float *__restrict__ By, const float *__restrict__ Bz, float *Jx,
                                                float *Jy, float *Jz, unsigned long long *jfx, float jinv,
                                                AntSet as, const double *__restrict__ ant) {
@@ -476,10 +476,10 @@ long long frame_floats(const GridP &g) {
 }
 
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s) {
-  const int nb = row_blocks(g, 256);
-  if (g.D == 1) k_yee_b<1><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
-  else if (g.D == 2) k_yee_b<2><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
-  else k_yee_b<3><<<nb, 256, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  const int nb = row_blocks(g, 128);
+  if (g.D == 1) k_yee_b<1><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  else if (g.D == 2) k_yee_b<2><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  else k_yee_b<3><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
 }
 
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
@@ -487,7 +487,7 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
                   cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
-  const int nb = row_blocks(g, 256);
+  const int nb = row_blocks(g, 128);
   AntSet as;
   as.n = jfx ? nlas : 0;
   as.lo = 1 << 30;
@@ -506,7 +506,7 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
     else k_antenna<3><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
   }
 #define YEE_E(DD, FF) \
-  k_yee_e<DD, FF><<<nb, 256, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
+  k_yee_e<DD, FF><<<nb, 128, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
   if (jfx) {
     if (g.D == 1) YEE_E(1, true);
     else if (g.D == 2) YEE_E(2, true);
