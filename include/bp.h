@@ -159,6 +159,17 @@ int bp_sync(bp_ctx *ctx);
  * pointer when on_device != 0, else a host pointer.  Synchronous. */
 int bp_read_field(bp_ctx *ctx, int comp, float *dst, int on_device);
 
+/* Enqueue a read of field component comp, as it stands after the steps
+ * enqueued so far, into caller-owned host memory dst (nz*ny*nx floats; page-
+ * locked memory for the copy to run asynchronously).  Returns at once: the
+ * field is first copied to one of two device snapshot buffers on the
+ * context's stream, and the snapshot goes to dst on a side stream, so the
+ * steps that follow overlap the transfer.  dst is valid after the next
+ * bp_sync (which waits for every enqueued read).  The snapshot buffers
+ * (2 * nz*ny*nx floats) are allocated at the first call; BP_ERR_OOM if they
+ * cannot be. */
+int bp_read_field_async(bp_ctx *ctx, int comp, float *dst);
+
 /* Overwrite field component comp from src (nz*ny*nx floats; device pointer
  * when on_device != 0).  Synchronous.  Used to start from given fields. */
 int bp_write_field(bp_ctx *ctx, int comp, const float *src, int on_device);

@@ -93,6 +93,7 @@ _SIGS = {
     "bp_kernel_launches": (_i64, [_p]),
     "bp_time_push": (_i, [_p, _i]),
     "bp_set_record_capacity": (_i, [_p, C.c_int64]),
+    "bp_read_field_async": (_i, [_p, _i, _p]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
 }
 
@@ -355,6 +356,11 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self._L.bp_kernel_launches(self._h))
+
+    def read_field_async(self, comp: int, dst) -> None:
+        """Enqueue a read of field comp into dst (a contiguous float32 array
+        of the grid's size, ideally page-locked); valid after sync()."""
+        self._check(self._L.bp_read_field_async(self._h, comp, _ptr(dst)), "bp_read_field_async")
 
     def set_record_capacity(self, n: int):
         self._check(self._L.bp_set_record_capacity(self._h, int(n)), "bp_set_record_capacity")

@@ -304,6 +304,14 @@ void bp_destroy(bp_ctx *c) {
   for (auto e : c->ev) cudaEventDestroy(e);
   if (c->sort_exec) cudaGraphExecDestroy(c->sort_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->read_stream) {
+    cudaStreamSynchronize(c->read_stream);
+    cudaStreamDestroy(c->read_stream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (c->snap_ready[k]) cudaEventDestroy(c->snap_ready[k]);
+    if (c->snap_done[k]) cudaEventDestroy(c->snap_done[k]);
+  }
   if (c->sort_runs) cudaFreeHost(c->sort_runs);
   std::vector<void *> all = c->owned;
   for (void *p : all) dfree(c, p);
@@ -778,6 +786,7 @@ int bp_step(bp_ctx *c, int64_t nsteps) {
 int bp_sync(bp_ctx *c) {
   if (!c) return BP_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && c->read_stream) e = cudaStreamSynchronize(c->read_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "sync");
   if (c->timing && c->ev_used) {
     for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
@@ -803,6 +812,35 @@ int bp_read_field(bp_ctx *c, int comp, float *dst, int on_device) {
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "read field");
+}
+
+int bp_read_field_async(bp_ctx *c, int comp, float *dst) {
+  if (!c || comp < 0 || comp > 8 || !dst) return BP_ERR_ARG;
+  const size_t bytes = sizeof(float) * c->g.ncell;
+  if (!c->snap[0]) {
+    c->snap[0] = (float *)dalloc(c, bytes);
+    c->snap[1] = (float *)dalloc(c, bytes);
+    if (!c->snap[0] || !c->snap[1]) return fail(c, BP_ERR_OOM, "read snapshots");
+    if (cudaStreamCreateWithFlags(&c->read_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->read_stream = nullptr;
+      return cuda_fail(c, cudaGetLastError(), "read stream");
+    }
+    for (int k = 0; k < 2; ++k) {
+      cudaEventCreateWithFlags(&c->snap_ready[k], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&c->snap_done[k], cudaEventDisableTiming);
+      cudaEventRecord(c->snap_done[k], c->read_stream);
+    }
+  }
+  const int k = c->snap_next;
+  c->snap_next ^= 1;
+  // snapshot k may be overwritten once its previous copy to the host is done
+  cudaStreamWaitEvent(c->stream, c->snap_done[k], 0);
+  cudaError_t e = cudaMemcpyAsync(c->snap[k], c->F[comp], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->snap_ready[k], c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->read_stream, c->snap_ready[k], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, c->snap[k], bytes, cudaMemcpyDeviceToHost, c->read_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->snap_done[k], c->read_stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "read field async");
 }
 
 int bp_write_field(bp_ctx *c, int comp, const float *src, int on_device) {

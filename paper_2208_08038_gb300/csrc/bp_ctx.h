@@ -71,6 +71,12 @@ struct bp_ctx {
   int *tile_ctr = nullptr;           // the push's tile counter
   int *tile_list = nullptr;          // tiles left for the push by the quiet-tile pass, and their number
   int *tile_n = nullptr;
+  // asynchronous field reads: two device snapshots, copied to the host on a
+  // side stream; ready[k] marks snapshot k written, done[k] its copy finished
+  float *snap[2] = {nullptr, nullptr};
+  cudaStream_t read_stream = nullptr;
+  cudaEvent_t snap_ready[2] = {nullptr, nullptr}, snap_done[2] = {nullptr, nullptr};
+  int snap_next = 0;
   float *frame = nullptr;
   int *status = nullptr;
   std::vector<bp_species_state> sp;

@@ -1,6 +1,7 @@
-"""GPU tests of the library's lattice generator and state files:
-bp_set_lattice against the host definition of the seeded lattice, and
-bp_save / bp_load continuing a run bit for bit."""
+"""GPU tests of the library's lattice generator, state files and
+asynchronous field reads: bp_set_lattice against the host definition of the
+seeded lattice, bp_save / bp_load continuing a run bit for bit, and
+bp_read_field_async returning each step's field as the synchronous read does."""
 import os
 
 import numpy as np
@@ -120,3 +121,28 @@ def test_load_rejects_other_grids_and_foreign_files(tmp_path):
     assert e.value.code == B.BP_ERR_IO
     for c in (a, other, same):
         c.close()
+
+
+def test_async_field_reads_match_synchronous_reads():
+    """bp_read_field_async snapshots the field on the device and copies it to
+    the host on a side stream while the next steps run (two snapshot buffers
+    alternate): each step's E_y, read that way, equals the synchronous read of
+    the same step in an identical run."""
+    import torch
+    wl = small_periodic_3d()
+    nsteps = 5
+    a, _, _ = gpu_from_workload(wl, deposit_mode=1)
+    bufs = [torch.empty(int(np.prod(wl.n)), dtype=torch.float32, pin_memory=True) for _ in range(nsteps)]
+    for k in range(nsteps):
+        a.step(1)
+        a.read_field_async(1, bufs[k].data_ptr())
+    a.sync()
+    b, _, _ = gpu_from_workload(wl, deposit_mode=1)
+    for k in range(nsteps):
+        b.step(1)
+        b.sync()
+        ref = b.read_field(1).ravel()
+        assert np.array_equal(bufs[k].numpy(), ref), k
+    assert np.abs(bufs[-1].numpy()).max() > 0
+    a.close()
+    b.close()
