@@ -53,10 +53,10 @@ def whole_job(ms_local, units_local, dist=None, device="cpu"):
     return float(m.item()), float(u.item())
 
 
-def workload_cfg2(size="full"):
+def workload_neutral_3d(size="full"):
     from paper_2208_08038_gb300 import synth
     n = (512, 256, 256) if size == "full" else (128, 64, 64)
-    wl = synth.cfg2_neutral_3d(n=n, build_particles=False)
+    wl = synth.neutral_3d(n=n, build_particles=False)
     m = wl.meta
     n_ion = m["ppc"] * (m["hi"][0] - m["lo"][0]) * (m["hi"][1] - m["lo"][1]) * (m["hi"][2] - m["lo"][2])
     return wl, n_ion
@@ -123,14 +123,14 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_cfg2(seconds_target: float = 10.0):
+def cpu_baseline_neutral_3d(seconds_target: float = 10.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: a
     32^3-cell periodic box with the workload's dx, dt, ppc, momenta and
     omega_b (262,144 ions), timed over whole steps."""
     import oracle as O
     from paper_2208_08038_gb300 import synth
     n = (32, 32, 32)
-    wl = synth.cfg2_neutral_3d(n=n, margin=0)
+    wl = synth.neutral_3d(n=n, margin=0)
     wl.bc = (0, 0, 0)
     sp = wl.species[0]
     s = O.Sim(3, n, wl.dx, wl.dt, wl.bc)
@@ -199,7 +199,7 @@ def run_adjoint_ratio(steps=400, K=20):
     from paper_2208_08038_gb300 import binding as B
     from paper_2208_08038_gb300 import synth
     from paper_2208_08038_gb300.adjoint import SiteProblem
-    wl = synth.cfg3_adjoint_2d(steps=steps)
+    wl = synth.adjoint_2d(steps=steps)
     sp = wl.species[0]
     m = wl.meta
     ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=B.BP_DEPOSIT_SORTED)
@@ -236,7 +236,7 @@ def run_adjoint_ratio(steps=400, K=20):
     t_fwd = timed(lambda: prob.run(sp.omega_b, sites))
     t_bwd = timed(lambda: prob.gradients(dl, len(sp.omega_b)))
     ctx.close()
-    return {"workload": "cfg3_adjoint_2d: 1024x1024 cells, dx=lambda/32, 524288 ions on 4096 sites, "
+    return {"workload": "adjoint_2d: 1024x1024 cells, dx=lambda/32, 524288 ions on 4096 sites, "
                         "1024 per-column omega_b, 400 steps, checkpoint every 20",
             "plain_forward_ms": t_plain, "ckpt_forward_ms": t_fwd, "backward_ms": t_bwd,
             "ratio": (t_fwd + t_bwd) / t_plain,
@@ -246,7 +246,7 @@ def run_adjoint_ratio(steps=400, K=20):
 
 
 def our_config(n_ion, mode, world, warmup=3, steps=500):
-    return {"workload": "cfg2_neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
+    return {"workload": "neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
                         f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, {mode} deposit",
             "timed": f"steps {warmup}..{warmup + steps} of the run from t=0 (the field front crosses the "
                      "medium during the run; an ion it has not reached is a co-moving neutral pair and "
@@ -267,7 +267,7 @@ def run_reference(args, rank, world):
     # oracle's ~1.7e5 ion-pushes/s
     side = int(max(8, min(16, round((60.0 * 1.7e5 / max(args.steps, 1) / 8) ** (1.0 / 3.0)))))
     n = (side, side, side)
-    wl = synth.cfg2_neutral_3d(n=n, margin=0)
+    wl = synth.neutral_3d(n=n, margin=0)
     wl.bc = (0, 0, 0)
     sp = wl.species[0]
     s = O.Sim(3, n, wl.dx, wl.dt, wl.bc)
@@ -279,7 +279,7 @@ def run_reference(args, rank, world):
     el = time.perf_counter() - t0
     s.close()
     value = len(sp.x) * args.steps / el
-    wl_full, n_ion = workload_cfg2()
+    wl_full, n_ion = workload_neutral_3d()
     sample = f"{side}^3-cell periodic box of the 3D workload ({len(sp.x)} ions, 8/cell), FP64, {args.steps} timed steps"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
@@ -334,7 +334,7 @@ def main():
     if not os.path.exists(B.LIB_PATH):
         build_lib.build()
 
-    wl, n_ion = workload_cfg2(args.size)
+    wl, n_ion = workload_neutral_3d(args.size)
     mode = B.BP_DEPOSIT_SORTED if args.mode == "sorted" else B.BP_DEPOSIT_ATOMIC
     stream = torch.cuda.current_stream()
     ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=mode, tile=wl.tile)
@@ -410,7 +410,7 @@ def main():
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_cfg2()
+        line["cpu_baseline"] = cpu_baseline_neutral_3d()
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = run_adjoint_ratio()
     if rank == 0:

@@ -205,7 +205,7 @@ def _lin(n, i, j=0, k=0):
     return i + n[0] * (j + n[1] * k)
 
 
-def cfg0_neutral_1d(ppc: int = 16, seed: int = 0, steps: int = 3000, nb: float = 0.01,
+def neutral_1d(ppc: int = 16, seed: int = 0, steps: int = 3000, nb: float = 0.01,
                     Zb: float = 1.0, omega_b: float = 3.0, slab=(8.0, 24.0), probe_x: float = 26.0,
                     vacuum: bool = False, nx: int = 2048, cells_per_lambda: int = 64) -> Workload:
     """1D neutral-medium propagation: 2048 cells, dx = lambda/64, dt = 0.95 dx,
@@ -222,12 +222,12 @@ def cfg0_neutral_1d(ppc: int = 16, seed: int = 0, steps: int = 3000, nb: float =
     las = [Laser(comp=1, a0=1e-3, fwhm=fwhm, t0=1.5 * fwhm, ia=8)]
     n = (nx, 1, 1)
     probe = np.array([_lin(n, int(probe_x * cells_per_lambda))], dtype=np.int64)
-    return Workload("cfg0_neutral_1d", 1, (nx,), (dx,), 0.95 * dx, (1,), steps, sp, las,
+    return Workload("neutral_1d", 1, (nx,), (dx,), 0.95 * dx, (1,), steps, sp, las,
                     tile=(16,), probe_comp=1, probe_nodes=probe,
                     meta=dict(slab=(lo, hi), ppc=ppc, nb=nb, omega_b=omega_b, Zb=Zb))
 
 
-def cfg1_bragg_2d(seed: int = 1, steps: int = 4000, n: int = 2048, cells_per_lambda: int = 32,
+def bragg_2d(seed: int = 1, steps: int = 4000, n: int = 2048, cells_per_lambda: int = 32,
                   sites=(40, 40), theta_deg: float = 30.0, waist_lambda: float = 8.0,
                   fwhm_lambda: float = 19.0, nb: float = 0.01, omega_b: float = 4.0,
                   lattice_angle_deg: float = 0.0) -> Workload:
@@ -256,11 +256,11 @@ def cfg1_bragg_2d(seed: int = 1, steps: int = 4000, n: int = 2048, cells_per_lam
     las = [Laser(comp=1, a0=1e-3, theta=th, waist=waist_lambda * LAMBDA0, fwhm=fwhm, t0=1.5 * fwhm,
                  ia=ia, yc=yc)]
     dt = 0.95 * dx / math.sqrt(2.0)
-    return Workload("cfg1_bragg_2d", 2, (n, n), (dx, dx), dt, (1, 1), steps, sp, las, tile=(16, 16),
+    return Workload("bragg_2d", 2, (n, n), (dx, dx), dt, (1, 1), steps, sp, las, tile=(16, 16),
                     meta=dict(d=d, sites=sites, theta=th, origin=origin))
 
 
-def cfg2_neutral_3d(seed: int = 2, steps: int = 500, n=(512, 256, 256), cells_per_lambda: int = 16,
+def neutral_3d(seed: int = 2, steps: int = 500, n=(512, 256, 256), cells_per_lambda: int = 16,
                     ppc: int = 8, nb: float = 0.02, omega_b: float = 3.0, sigma_u: float = 1e-3,
                     margin: int = 4, build_particles: bool = True) -> Workload:
     """3D neutral medium: 512x256x256 cells, dx = lambda/16, 8 ions per cell at
@@ -279,12 +279,12 @@ def cfg2_neutral_3d(seed: int = 2, steps: int = 500, n=(512, 256, 256), cells_pe
     las = [Laser(comp=1, a0=1e-3, waist=6 * LAMBDA0, fwhm=fwhm, t0=1.5 * fwhm, ia=2,
                  yc=0.5 * n[1] * dx, zc=0.5 * n[2] * dx)]
     dt = 0.95 * dx / math.sqrt(3.0)
-    return Workload("cfg2_neutral_3d", 3, tuple(n), (dx, dx, dx), dt, (1, 0, 0), steps, sp, las,
+    return Workload("neutral_3d", 3, tuple(n), (dx, dx, dx), dt, (1, 0, 0), steps, sp, las,
                     tile=(8, 8, 8), meta=dict(seed=seed, lo=lo, hi=hi, ppc=ppc, sigma_u=sigma_u,
                                               nb=nb, omega_b=omega_b))
 
 
-def cfg3_adjoint_2d(seed: int = 3, target_seed: int = 33, steps: int = 400, n=(1024, 1024),
+def adjoint_2d(seed: int = 3, target_seed: int = 33, steps: int = 400, n=(1024, 1024),
                     cells_per_lambda: int = 32, ppc: int = 8, nb: float = 0.01, slab=(2.0, 4.0),
                     sites_x: int = 4, probe_x: float = 6.0, target: bool = False) -> Workload:
     """2D adjoint workload: 1024^2 cells, dx = lambda/32, bound slab x in [2, 4)
@@ -314,13 +314,13 @@ def cfg3_adjoint_2d(seed: int = 3, target_seed: int = 33, steps: int = 400, n=(1
     dt = 0.95 * dx / math.sqrt(2.0)
     ip = int(probe_x * cells_per_lambda)
     probe = np.array([_lin((nx, ny, 1), ip, j) for j in range(ny)], dtype=np.int64)
-    return Workload("cfg3_adjoint_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
+    return Workload("adjoint_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
                     tile=(16, 16), probe_comp=2, probe_nodes=probe,
                     meta=dict(sites=sites, off=off, site_of_ion=site_of_ion, column=column,
                               per_site=per_site, omega=omega))
 
 
-def cfg4_ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), cells_per_lambda: int = 32,
+def ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), cells_per_lambda: int = 32,
                             period_lambda: float = 0.6, span=(16.0, 112.0), e_ppc: int = 4,
                             ne: float = 0.1, Te_eV: float = 10.0, a0: float = 0.3,
                             build_particles: bool = True) -> Workload:
@@ -351,6 +351,6 @@ def cfg4_ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), ce
     fwhm = 10 * T0
     las = [Laser(comp=1, a0=a0, fwhm=fwhm, t0=1.5 * fwhm, ia=8)]
     dt = 0.95 * dx / math.sqrt(2.0)
-    return Workload("cfg4_ionized_crystal_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
+    return Workload("ionized_crystal_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
                     tile=(16, 16), free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
                     meta=dict(sites=st, lo=lo, hi=hi, sigma=sigma))

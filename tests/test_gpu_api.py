@@ -22,7 +22,7 @@ def _cuda():
 
 
 def bragg_small():
-    return synth.cfg1_bragg_2d(seed=5, n=256, cells_per_lambda=16, sites=(6, 6), waist_lambda=3.0,
+    return synth.bragg_2d(seed=5, n=256, cells_per_lambda=16, sites=(6, 6), waist_lambda=3.0,
                                fwhm_lambda=3.0, nb=0.05, steps=60)
 
 
@@ -61,7 +61,7 @@ def test_set_lattice_matches_host_definition():
 
 
 def small_periodic_3d():
-    wl = synth.cfg2_neutral_3d(seed=9, steps=30, n=(32, 16, 16), ppc=4, sigma_u=5e-2, margin=2)
+    wl = synth.neutral_3d(seed=9, steps=30, n=(32, 16, 16), ppc=4, sigma_u=5e-2, margin=2)
     wl.bc = (0, 0, 0)
     wl.lasers[0].waist = 0.5 * synth.LAMBDA0
     wl.lasers[0].a0 = 0.05

@@ -30,7 +30,7 @@ def _cuda():
     binding.lib()
 
 
-def cfg2_context(wl, mode=1):
+def neutral_3d_context(wl, mode=1):
     """The 3D medium exactly as the benchmark builds it (device generator)."""
     from paper_2208_08038_gb300 import binding as B
     ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=mode, tile=wl.tile)
@@ -119,12 +119,12 @@ def check_sampled(wl, res, two_body):
 
 
 # ---------------------------------------------------------------------------
-# config 2: the 3D medium of the benchmark (264,241,152 ions), sampled
+# the 3D neutral medium of the benchmark (264,241,152 ions), sampled
 
-def test_cfg2_full_medium_matches_definition_and_sampled_push():
-    wl = synth.cfg2_neutral_3d(build_particles=False)
+def test_neutral_3d_full_medium_matches_definition_and_sampled_push():
+    wl = synth.neutral_3d(build_particles=False)
     m = wl.meta
-    ctx, sid, n_ion = cfg2_context(wl)
+    ctx, sid, n_ion = neutral_3d_context(wl)
     rng = np.random.default_rng(12)
     # ions of the first 40 x cells (reached by the field within 40 steps) and random ones
     ext = [m["hi"][a] - m["lo"][a] for a in range(3)]
@@ -151,14 +151,14 @@ def test_cfg2_full_medium_matches_definition_and_sampled_push():
     ctx.close()
 
 
-def test_cfg2_full_gauss_and_bit_exact_rerun():
+def test_neutral_3d_full_gauss_and_bit_exact_rerun():
     """Charge conservation and bit-identical reruns of the benchmark's own
     launch configuration over its first steps."""
-    wl = synth.cfg2_neutral_3d(build_particles=False)
+    wl = synth.neutral_3d(build_particles=False)
     wl.lasers[0].a0 = 0.05  # a stronger pulse: ions near the antenna deposit within the first steps
     outs = []
     for rep in range(2):
-        ctx, sid, _ = cfg2_context(wl)
+        ctx, sid, _ = neutral_3d_context(wl)
         if rep == 0:
             R0 = ctx.residual()
         ctx.step(12)
@@ -173,10 +173,10 @@ def test_cfg2_full_gauss_and_bit_exact_rerun():
 
 
 # ---------------------------------------------------------------------------
-# config 1: the 2D Bragg crystal on its full 2048^2 grid
+# the 2D Bragg crystal on its full 2048^2 grid
 
-def test_cfg1_full_grid_parity():
-    wl = synth.cfg1_bragg_2d()
+def test_bragg_2d_full_grid_parity():
+    wl = synth.bragg_2d()
     ora, osid, _ = oracle_from_workload(wl, probe_cap=1)
     gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
     out = []
@@ -195,10 +195,10 @@ def test_cfg1_full_grid_parity():
     ora.close()
 
 
-def test_cfg1_full_run_gauss():
+def test_bragg_2d_full_run_gauss():
     """The whole 4000-step run on the GPU keeps Gauss's law (charge
     conservation of the deposit over the run)."""
-    wl = synth.cfg1_bragg_2d()
+    wl = synth.bragg_2d()
     gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
     R0 = gpu.residual()
     gpu.step(wl.steps)
@@ -210,10 +210,10 @@ def test_cfg1_full_run_gauss():
 
 
 # ---------------------------------------------------------------------------
-# config 3: the 2D adjoint workload on its full grid (forward)
+# the 2D adjoint workload on its full 1024^2 grid (forward)
 
-def test_cfg3_full_forward_parity():
-    wl = synth.cfg3_adjoint_2d()
+def test_adjoint_2d_full_forward_parity():
+    wl = synth.adjoint_2d()
     ora, osid, opid = oracle_from_workload(wl, probe_cap=3)
     gpu, gsid, gpid = gpu_from_workload(wl, probe_cap=3)
     out = []
@@ -234,10 +234,10 @@ def test_cfg3_full_forward_parity():
 
 
 # ---------------------------------------------------------------------------
-# config 4: ionized crystal with 25 M free electrons, sampled
+# the ionized crystal with 25 M free electrons, sampled
 
-def test_cfg4_full_sampled_push_and_gauss():
-    wl = synth.cfg4_ionized_crystal_2d()
+def test_ionized_crystal_full_sampled_push_and_gauss():
+    wl = synth.ionized_crystal_2d()
     gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
     R0 = gpu.residual()
     gpu.step(30)

@@ -67,10 +67,10 @@ def test_vacuum_yee_parity(D):
 
 
 # ---------------------------------------------------------------------------
-# config 0 geometry (1D neutral medium)
+# the 1D neutral medium (2048 cells)
 
-def test_cfg0_one_step_and_short_run():
-    wl = synth.cfg0_neutral_1d(ppc=16, steps=400)
+def test_neutral_1d_one_step_and_short_run():
+    wl = synth.neutral_1d(ppc=16, steps=400)
     ora, gpu, osid, gsid, opid, gpid, out = run_both(wl, 400, check_steps=(1,))
     (s1, f1, j1), (s2, f2, j2) = out
     assert f1 < 1e-5, out
@@ -83,10 +83,10 @@ def test_cfg0_one_step_and_short_run():
 
 
 @pytest.mark.slow
-def test_cfg0_full_run():
-    """Config 0 at full size and length (16 ions/cell, 3000 steps): relative
+def test_neutral_1d_full_run():
+    """The 1D neutral medium at full size and length (16 ions/cell, 3000 steps): relative
     field L2 <= 1e-5 after one step and <= 1e-3 at the end; probe trace too."""
-    wl = synth.cfg0_neutral_1d()
+    wl = synth.neutral_1d()
     ora, gpu, osid, gsid, opid, gpid, out = run_both(wl, wl.steps, check_steps=(1,))
     assert out[0][1] < 1e-5, out
     assert out[-1][1] < 1e-3, out
@@ -97,7 +97,7 @@ def test_cfg0_full_run():
 # 3D thermal medium, several tiles, ragged occupancy, re-sorting
 
 def small_3d(sigma=2e-2, seed=2, steps=30, n=(48, 16, 16), periodic=False):
-    wl = synth.cfg2_neutral_3d(seed=seed, steps=steps, n=n, ppc=4, sigma_u=sigma, margin=3)
+    wl = synth.neutral_3d(seed=seed, steps=steps, n=n, ppc=4, sigma_u=sigma, margin=3)
     wl.lasers[0].waist = 0.5 * synth.LAMBDA0
     if periodic:  # fast ions would otherwise leave through the open x faces
         wl.bc = (0, 0, 0)
@@ -224,7 +224,7 @@ def test_gauss_residual_conserved_gpu():
 # 2D: reduced Bragg crystal; charged ions with free electrons
 
 def test_2d_bragg_small_parity():
-    wl = synth.cfg1_bragg_2d(seed=1, n=256, cells_per_lambda=16, sites=(6, 6), waist_lambda=3.0,
+    wl = synth.bragg_2d(seed=1, n=256, cells_per_lambda=16, sites=(6, 6), waist_lambda=3.0,
                              fwhm_lambda=3.0, nb=0.05, steps=300)
     ora, gpu, *_ , out = run_both(wl, 300, check_steps=(1,))
     assert out[0][1] < 1e-5, out
@@ -232,7 +232,7 @@ def test_2d_bragg_small_parity():
 
 
 def test_2d_free_electrons_and_charged_ions():
-    wl = synth.cfg4_ionized_crystal_2d(n=(256, 64), span=(2.0, 6.0), steps=60, a0=0.3)
+    wl = synth.ionized_crystal_2d(n=(256, 64), span=(2.0, 6.0), steps=60, a0=0.3)
     wl.lasers[0].fwhm = 2 * synth.T0
     wl.lasers[0].t0 = 1.5 * wl.lasers[0].fwhm
     ora, gpu, osid, gsid, opid, gpid, out = run_both(wl, 60, check_steps=(1,))
@@ -241,7 +241,7 @@ def test_2d_free_electrons_and_charged_ions():
 
 
 def test_empty_species_and_vacuum_laser():
-    wl = synth.cfg0_neutral_1d(ppc=1, steps=200, vacuum=True)
+    wl = synth.neutral_1d(ppc=1, steps=200, vacuum=True)
     wl.species = [synth.TwoBody(Zb=1.0, qc=0.0, mc=synth.M_AU, w=0.01, lambda0_m=12.4e-9,
                                 omega_b=np.array([3.0]), x=np.zeros((0, 1)), u=np.zeros((0, 3)))]
     ora, gpu, *_ , out = run_both(wl, 200, check_steps=(1,))

@@ -4,7 +4,7 @@ Each reverse operator is checked against the forward operator it
 transposes: linear operators by dot-product identities <A x, y> = <x, A^T y>,
 non-linear ones (Boris, internal force, gather, Esirkepov) by central finite
 differences of the forward function; the whole reverse pass by FP64 central
-finite differences of the probe loss on a config-0-size grid.
+finite differences of the probe loss on the 1D neutral medium's grid (2048 cells).
 """
 import math
 
@@ -147,16 +147,16 @@ def test_yee_adjoint_dot_products(D, bc):
 # whole reverse pass against finite differences of the loss
 
 def fd_problem(D=1):
-    """Config-0-size 1D grid (2048 cells, lambda/64), a short bound slab with
+    """The 1D neutral medium's grid (2048 cells, lambda/64), a short bound slab with
     8 parameter groups (per-group omega_b; the ions of a group form one
     'site' that moves rigidly), a short pulse and a probe behind the slab."""
     if D == 1:
-        wl = synth.cfg0_neutral_1d(ppc=2, slab=(6.0, 7.0), probe_x=8.0, nb=0.05)
+        wl = synth.neutral_1d(ppc=2, slab=(6.0, 7.0), probe_x=8.0, nb=0.05)
         wl.lasers[0].fwhm = 2 * synth.T0
         wl.lasers[0].t0 = 2.0 * wl.lasers[0].fwhm
         steps = 900
     else:
-        wl = synth.cfg3_adjoint_2d(n=(128, 32), slab=(1.0, 1.5), probe_x=2.0, sites_x=2, nb=0.05)
+        wl = synth.adjoint_2d(n=(128, 32), slab=(1.0, 1.5), probe_x=2.0, sites_x=2, nb=0.05)
         wl.lasers[0].ia = 8
         steps = 260
     sp = wl.species[0]

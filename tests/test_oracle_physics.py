@@ -84,14 +84,14 @@ STEPS_B = 4500  # the whole 10-cycle pulse passes the probe at 26 lambda
 
 @pytest.fixture(scope="module")
 def vacuum_trace():
-    wl = synth.cfg0_neutral_1d(ppc=1, vacuum=True)
+    wl = synth.neutral_1d(ppc=1, vacuum=True)
     return run_1d(wl, STEPS_B)
 
 
 def test_lorentz_index_phase_delay(vacuum_trace):
-    """Pin (b): config-0 geometry (16 lambda slab, n_b = 0.01, w_b = 3).
+    """Pin (b): the 1D neutral medium's geometry (16 lambda slab, n_b = 0.01, w_b = 3).
     n - 1 = 6.248e-4, so the delay is k0 L (n - 1) ~ 0.0628 rad."""
-    wl = synth.cfg0_neutral_1d(ppc=1)
+    wl = synth.neutral_1d(ppc=1)
     sp = wl.species[0]
     tr = run_1d(wl, STEPS_B)
     meas = measured_delay(tr, vacuum_trace, wl.dt)
@@ -109,7 +109,7 @@ def test_drude_plus_bound_index(vacuum_trace):
     """Pin (b'): free electrons (Drude term -n_e e^2/(m_e w^2), Sec. 3.1) plus
     charged two-body ions (q_c = +1, Z_b = 1) at the same positions, so the
     slab starts neutral; the phase advances by k0 L (n - 1) < 0."""
-    base = synth.cfg0_neutral_1d(ppc=1)
+    base = synth.neutral_1d(ppc=1)
     sp = base.species[0]
     n_ion = 0.01
     ion = synth.TwoBody(Zb=1.0, qc=1.0, mc=sp.mc, w=n_ion, lambda0_m=sp.lambda0_m,
@@ -133,7 +133,7 @@ def test_zb_invariance(vacuum_trace):
     for Z_b = 1, 20, 78 to 1e-3."""
     vals = []
     for Zb in (1.0, 20.0, 78.0):
-        wl = synth.cfg0_neutral_1d(ppc=1, Zb=Zb)
+        wl = synth.neutral_1d(ppc=1, Zb=Zb)
         tr = run_1d(wl, STEPS_B)
         vals.append(measured_delay(tr, vacuum_trace, wl.dt))
     vals = np.array(vals)
@@ -144,7 +144,7 @@ def _bragg_run(theta_deg, steps=620):
     n = 384
     cpl = 16
     dx = synth.LAMBDA0 / cpl
-    wl = synth.cfg1_bragg_2d(seed=1, n=n, cells_per_lambda=cpl, sites=(8, 8), theta_deg=theta_deg,
+    wl = synth.bragg_2d(seed=1, n=n, cells_per_lambda=cpl, sites=(8, 8), theta_deg=theta_deg,
                              waist_lambda=4.0, fwhm_lambda=4.0, nb=0.05)
     s = O.Sim(2, wl.n, wl.dx, wl.dt, wl.bc)
     sp = wl.species[0]

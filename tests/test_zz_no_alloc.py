@@ -19,7 +19,7 @@ def _context():
     import sys, os
     sys.path.insert(0, os.path.dirname(__file__))
     from _common import gpu_from_workload
-    wl = synth.cfg4_ionized_crystal_2d(n=(256, 64), span=(2.0, 6.0), steps=10, a0=0.3)
+    wl = synth.ionized_crystal_2d(n=(256, 64), span=(2.0, 6.0), steps=10, a0=0.3)
     return gpu_from_workload(wl, deposit_mode=1)[0]
 
 
