@@ -501,9 +501,10 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
   if (as.n > 0) {
     const LaserSet ls = make_laser_set(las, nlas);
     const long long nant = (long long)nlas * (g.ncell / g.n[0]);
-    if (g.D == 1) k_antenna<1><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
-    else if (g.D == 2) k_antenna<2><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
-    else k_antenna<3><<<grid_blocks(nant, 256), 256, 0, s>>>(g, ls, t, ant);
+    // small blocks: the FP64 exp / sin of the antenna planes spread over many SMs
+    if (g.D == 1) k_antenna<1><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
+    else if (g.D == 2) k_antenna<2><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
+    else k_antenna<3><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
   }
 #define YEE_E(DD, FF) \
   k_yee_e<DD, FF><<<nb, 128, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
