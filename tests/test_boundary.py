@@ -1,5 +1,6 @@
-"""The C-ABI library loads and exports every symbol include/bp.h declares
-(no compute calls: runs without a GPU)."""
+"""The C-ABI library loads, exports every symbol include/bp.h declares and
+rejects a null context at every entry point (no compute calls: runs without a
+GPU)."""
 import ctypes
 import os
 import subprocess
@@ -49,3 +50,27 @@ def test_oracle_not_imported_by_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(root, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "bp_oracle" not in txt, f
+
+
+def test_entry_points_reject_a_null_context(libpath):
+    """Every entry point that takes a context checks it before any CUDA call:
+    a null context gives BP_ERR_ARG (and no crash), so this runs without a GPU."""
+    L = binding.lib()
+    err_arg = -1
+    zero = {ctypes.c_int: 0, ctypes.c_int64: 0, ctypes.c_uint64: 0, ctypes.c_double: 0.0}
+    checked = 0
+    for name, (res, args) in binding._SIGS.items():
+        f = getattr(L, name)
+        vals = [zero.get(a, None) for a in args]
+        if name == "bp_destroy":
+            f(None)
+            continue
+        out = f(*vals)
+        if name == "bp_last_error":
+            assert out == b"null context"
+        elif name == "bp_kernel_launches":
+            assert out == 0
+        else:
+            assert out == err_arg, name
+            checked += 1
+    assert checked >= 25
