@@ -3,13 +3,15 @@ finite differences in test_oracle_adjoint.py), on the same small problems:
 gradients of a probe loss with respect to per-group omega_b and rigid
 group ('site') positions.  Both adjoints get the same loss gradient dL/dp
 (from the oracle's probe), so the comparison measures the reverse pass, not
-the FP32 forward's effect on a small residual p - target.  Gradients are
-end-of-run quantities of a run of hundreds of FP32 steps, compared at the
-end-of-run FP32 tolerance, 1e-3 relative to the largest component (FP32
-forward and adjoint, FP64 reductions).  The probe itself is compared at
-1e-5.  Reruns give bit-identical gradients."""
+the FP32 forward's effect on a small residual p - target.  Gradients are compared at
+1e-4 relative to the largest component (FP32 forward and adjoint, FP64
+reductions; the order of every cross-particle sum is fixed, so the
+difference is FP32 rounding of a few hundred steps: measured on a GB300,
+at most 5.3e-5 for the 1D site gradient, 1.8e-6 for the 1D omega_b
+gradient, below 4e-7 in 2D).  The probe itself is compared at 1e-5.
+Reruns give bit-identical gradients."""
 
-GRAD_TOL = 1e-3
+GRAD_TOL = 1e-4
 import numpy as np
 import pytest
 
