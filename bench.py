@@ -29,13 +29,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "two-body ion pushes/s (gather+push+deposit+Yee) FP32 vs FP64; adjoint/fwd ratio"
-# DRAM bytes (read + write) of one push launch (k_push_quiet<3> + k_push<3,
-# sorted>) on this workload, averaged over the timed 500-step run, from an
-# ncu capture of every push launch of that run (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass per launch).  It
-# falls from 27.5 GB late in the run to 18.3 GB at its start, where most
-# ions are quiet and write only their cell and offset.
-PUSH_TRAFFIC = 23.23e9
+# Algorithmic bytes of the push per unit (3D two-body ion, FP32 state: cell,
+# 3 offsets, r, u1, u2 = 52 B): a fully pushed ion reads and writes its whole
+# state; a quiet ion (moved by the quiet-tile pass: a co-moving neutral pair
+# ahead of the field, which carries no current) reads it and writes its cell
+# and offsets; per cell, E and B are read once and J written once.
+BYTES_FULL_ION = 104
+BYTES_QUIET_ION = 68
+BYTES_CELL = 36
+# FP32 operations of one fully pushed 3D two-body ion (gather of six
+# components at both bodies, internal field, two Boris rotations, drift,
+# three-node Esirkepov deposit of both bodies in fixed point), counted by
+# ncu's executed-instruction classes on the small 3D case with a field in
+# every tile: FFMA2 x 4 + FMUL2 x 2 + FADD2 x 2 + FFMA x 2 + FMUL + FADD.
+FLOPS_FULL_ION = 2371
+# DRAM bytes (read + write) per ion of the push launch, from ncu on the small
+# 3D case (one launch each; profiles/): None until captured for the current
+# kernels.
+TRAFFIC_FULL_ION = None
+TRAFFIC_QUIET_ION = None
+# the late window starts here: the field has crossed most of the medium
+LATE_START = 450
 UNIT = "ion-pushes/s"
 
 
@@ -245,13 +259,43 @@ def run_adjoint_ratio(steps=400, K=20):
                            "backward (segment recompute + reverse steps) / plain forward"}
 
 
-def our_config(n_ion, mode, world, warmup=3, steps=500):
+def our_config(n_ion, mode, world, warmup, steps):
     return {"workload": "neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
                         f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, {mode} deposit",
-            "timed": f"steps {warmup}..{warmup + steps} of the run from t=0 (the field front crosses the "
-                     "medium during the run; an ion it has not reached is a co-moving neutral pair and "
-                     "deposits nothing)",
+            "timed": f"steps {warmup}..{warmup + steps} of the 500-step run from t=0: the quiet start (the "
+                     "field has reached only the tiles near the antenna; the co-moving neutral ions ahead of "
+                     "it are drifted by the quiet-tile pass without gather or deposit); the field-covered "
+                     f"regime is timed separately from step {LATE_START} (key 'late')",
             "l2": "inputs larger than L2 (particles 13.7 GB)", "parallelism": f"replicas x{world}"}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 non-tensor peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def timed_window(ctx, steps, stream):
+    """CUDA-event time of `steps` steps, with the push launches timed and
+    their work counted on the device."""
+    import torch
+    ctx.time_push(True)
+    launches0 = ctx.kernel_launches()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(steps)
+    e1.record(stream)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    push_ms, push_n = ctx.push_time()
+    full, quiet = ctx.push_work()
+    launches = ctx.kernel_launches() - launches0
+    ctx.time_push(False)
+    return ms, push_ms, push_n, full, quiet, launches
 
 
 def run_reference(args, rank, world):
@@ -284,7 +328,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(our_config(n_ion, "oracle", world), sample=sample),
+            "data": "synthetic", "config": dict(our_config(n_ion, "oracle", world, args.warmup, args.steps), sample=sample),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -293,9 +337,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500,
-                    help="timed steps (default: the workload's whole 500-step run)")
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20, help="timed steps from t = 0 (after the warm-up)")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="sorted", choices=["sorted", "atomic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -303,6 +346,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only the adjoint/forward ratio of the 2D adjoint workload over STEPS steps")
+    ap.add_argument("--late-start", type=int, default=LATE_START,
+                    help="step at which the late (field-covered) window starts")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the 3D workload on 128x64x64 cells (profiling)")
     args = ap.parse_args()
@@ -350,34 +395,24 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ctx.time_push(True)
-    launches0 = ctx.kernel_launches()
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    # the last `tail` steps separately (the field front has crossed most of the
-    # medium by then): their push time is reported beside the run's average
-    tail = min(50, args.steps // 5)
-    ctx.step(args.steps - tail)
-    ctx.sync()
-    push_ms_head, push_n_head = ctx.push_time()
-    ctx.step(tail)
-    e1.record(stream)
-    ctx.sync()
-    torch.cuda.synchronize()
+    # the driver's window: K steps right after the warm-up, from t = 0
+    ms, push_ms, push_n, full0, quiet0, launches = timed_window(ctx, args.steps, stream)
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    launches = ctx.kernel_launches() - launches0
-    push_ms, push_n = ctx.push_time()
-    push_tail = (push_ms - push_ms_head) / max(push_n - push_n_head, 1)
-    ctx.time_push(False)
-    clocks = sampler.stop()
     ms, units = whole_job(ms, n_ion * args.steps, dist, "cuda")
-
+    # the field-covered regime: advance (untimed) to LATE_START, then time a
+    # second window there; the roofline describes this window
+    done = args.warmup + args.steps
+    if done < args.late_start:
+        ctx.step(args.late_start - done)
+        ctx.sync()
+        done = args.late_start
+    late_steps = max(args.steps, 20)
+    lms, lpush_ms, lpush_n, lfull, lquiet, llaunch = timed_window(ctx, late_steps, stream)
+    clocks = sampler.stop()
+    lms_job, lunits = whole_job(lms, n_ion * late_steps, dist, "cuda")
     ctx.close()
     # end to end through the C ABI with host buffers: a fresh context loads
     # the ions' FP64 positions and momenta from pinned host memory
@@ -388,23 +423,42 @@ def main():
     if e2e_steps > 0:
         e2e = run_e2e(wl, n_ion, mode, e2e_steps, rank, world, dist)
     hbm, src = peaks()
-    # algorithmic bytes of one push launch: every ion's state read and written
-    # (2 x 52 B: cell, 3 offsets, r, u1, u2), E and B read once (24 B/cell),
-    # J written once (12 B/cell)
-    alg = n_ion * 104 + (wl.n[0] * wl.n[1] * wl.n[2]) * 36
-    push_avg = push_ms / max(push_n, 1)
-    achieved = alg / (push_avg * 1e-3) / 1e9
+    ncell = wl.n[0] * wl.n[1] * wl.n[2]
+    # per push launch of the late window: algorithmic bytes from the work the
+    # device counted (full pushes and quiet drifts), FP32 operations of the
+    # full pushes
+    per = max(lpush_n, 1)
+    lpush_avg = lpush_ms / per
+    alg = (lfull * BYTES_FULL_ION + lquiet * BYTES_QUIET_ION) / per + ncell * BYTES_CELL
+    flops = lfull * FLOPS_FULL_ION / per
+    achieved_gbs = alg / (lpush_avg * 1e-3) / 1e9
+    achieved_tf = flops / (lpush_avg * 1e-3) / 1e12
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak, sms = fp32_peak_tflops(sm_max)
+    traffic = None
+    if TRAFFIC_FULL_ION is not None and TRAFFIC_QUIET_ION is not None:
+        traffic = (lfull * TRAFFIC_FULL_ION + lquiet * TRAFFIC_QUIET_ION) / per
+    push_avg0 = push_ms / max(push_n, 1)
     value = units / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": our_config(n_ion, args.mode, world, args.warmup, args.steps),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": PUSH_TRAFFIC, "traffic_unit": "bytes per launch",
-                     "kernel": "push: k_push_quiet<3> + k_push<3,sorted>",
-                     "peak_source": src, "push_ms_per_launch": push_avg,
-                     "push_ms_per_launch_last_steps": push_tail, "last_steps": tail},
+        "push_ms_per_launch": push_avg0,
+        "push_work_per_launch": {"full": full0 / max(push_n, 1), "quiet": quiet0 / max(push_n, 1)},
+        "late": {"steps": f"{done}..{done + late_steps}", "ms_per_step": lms_job / late_steps,
+                 "value": lunits / (lms_job * 1e-3), "unit": UNIT, "push_ms_per_launch": lpush_avg,
+                 "full_pushes_per_launch": lfull / per, "quiet_per_launch": lquiet / per,
+                 "full_fraction": lfull / max(lfull + lquiet, 1), "gpu_launches": llaunch},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp32_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                     "window": "late", "kernel": "push launch: k_push_quiet<3> + k_push<3,sorted> + k_records<3>",
+                     "peak_source": f"FP32 lanes: {sms} SMs x 128 x 2 flops x {sm_max:.0f} MHz (max SM clock)",
+                     "flops_per_full_push": FLOPS_FULL_ION,
+                     "limiter": "instruction issue (ncu on the small 3D case with a field in every tile)",
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                             "bytes_per_launch": alg, "peak_source": src}},
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,

@@ -95,6 +95,7 @@ _SIGS = {
     "bp_set_record_capacity": (_i, [_p, C.c_int64]),
     "bp_read_field_async": (_i, [_p, _i, _p]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
+    "bp_push_work": (_i, [_p, C.POINTER(_i64), C.POINTER(_i64)]),
 }
 
 
@@ -184,6 +185,9 @@ class Context:
             if allocator == "torch":
                 self._alloc = _TorchAllocator(dev)
                 ap = C.pointer(self._alloc.struct)
+        if hasattr(allocator, "struct"):  # a caller-built bp_allocator (kept alive by the context)
+            self._alloc = allocator
+            ap = C.pointer(allocator.struct)
         self.stream = stream
         h = C.c_void_p()
         rc = L.bp_create(C.byref(g), ap, C.c_void_p(stream), C.byref(h))
@@ -373,3 +377,10 @@ class Context:
         n = C.c_int64()
         self._check(self._L.bp_push_time(self._h, C.byref(ms), C.byref(n)), "bp_push_time")
         return ms.value, n.value
+
+    def push_work(self):
+        """(full pushes, quiet drifts) of the timed push launches (bp_push_work)."""
+        full = C.c_int64()
+        quiet = C.c_int64()
+        self._check(self._L.bp_push_work(self._h, C.byref(full), C.byref(quiet)), "bp_push_work")
+        return full.value, quiet.value

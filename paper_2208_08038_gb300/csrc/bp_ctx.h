@@ -79,6 +79,9 @@ struct bp_ctx {
   int snap_next = 0;
   float *frame = nullptr;
   int *status = nullptr;
+  unsigned long long *work = nullptr;  // [2] push work counters (see PushArgs::work)
+  int push_blocks[2] = {1, 1};         // resident push blocks per deposit mode (atomic, sorted)
+  int sms = 1;                         // multiprocessors of the context's device
   std::vector<bp_species_state> sp;
   std::vector<LaserP> las;
   std::vector<bp_probe_state> pr;

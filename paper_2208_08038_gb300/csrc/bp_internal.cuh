@@ -127,6 +127,9 @@ struct PushArgs {
   int grec_cap;
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
+  unsigned long long *work; // [2] ions given the full push, ions moved by the quiet-tile pass (cumulative)
+  int push_blocks;          // persistent push blocks for this grid on this device
+  int sms;                  // multiprocessors of the device
 };
 
 struct LaserP {
@@ -365,7 +368,9 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t k
 void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s);
 size_t push_smem_bytes(const GridP &g, int det);
 size_t push_record_bytes();  // one general-case deposit record
-int push_prepare(const GridP &g, int det);
+// set the push kernel's shared-memory limit for this grid and return, in
+// *blocks, the number of push blocks resident on the current device at once
+int push_prepare(const GridP &g, int det, int *blocks);
 
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);
 // recompute the tile marks (g.fnz) from E, B (F[0..5]) after a write from outside the step

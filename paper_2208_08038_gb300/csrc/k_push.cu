@@ -476,7 +476,7 @@ __device__ __forceinline__ bool quiet_state(const float r[3], const float u1[3],
 // quiet (left for the full push).
 template <int D, int QB>
 __device__ __forceinline__ bool quiet_batch(const GridP &g, const PartP &P, long long i0, int bs, long long end,
-                                            const int T0[3], int *status) {
+                                            const int T0[3], int *status, unsigned &moved) {
   const long long cap = P.cap;
   int cell[QB];
   float f[QB][3], u1[QB][3], u2[QB][3], r[QB][3];
@@ -526,8 +526,15 @@ __device__ __forceinline__ bool quiet_batch(const GridP &g, const PartP &P, long
     P.cell[i] = pack_cell(g, c[0], c[1], c[2]);
 #pragma unroll
     for (int a = 0; a < D; ++a) P.off[a * cap + i] = fn[a];
+    ++moved;
   }
   return left;
+}
+
+// add a per-thread count to a global work counter: one atomic per warp
+__device__ __forceinline__ void count_work(unsigned long long *ctr, unsigned n) {
+  const unsigned s = __reduce_add_sync(0xFFFFFFFFu, n);
+  if ((threadIdx.x & 31u) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
 // whether the quiet pass has already moved particle i (its state is still
@@ -833,15 +840,17 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
   }
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
   bool left = false;
+  unsigned moved = 0;
   for (int s = 0; s < A.nsp; ++s) {
     const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
     if (A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2) {
       for (long long i0 = beg + tid; i0 < end; i0 += (long long)QB * bs)
-        left |= quiet_batch<D, QB>(g, A.p[s], i0, bs, end, T0, A.status);
+        left |= quiet_batch<D, QB>(g, A.p[s], i0, bs, end, T0, A.status, moved);
     } else {
       left |= end > beg;
     }
   }
+  if (A.work) count_work(A.work + 1, moved);
   left = __syncthreads_or(left);
   if (tid == 0) {
     A.qstate[t] = left ? QS_REST : QS_DONE;
@@ -947,6 +956,7 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
   __shared__ unsigned sbb[6];
   if (tid < 6) sbb[tid] = tid < 3 ? 0xFFFFFFFFu : 0u;
   unsigned blo = 0xFFFFFFFFu, bhi = 0u;
+  unsigned pushed = 0;
   for (int s = 0; s < A.nsp; ++s) {
     if (tid == 0) qn = 0;
     __syncthreads();
@@ -960,6 +970,7 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
       if (i + bs < end) prefetch_particle<D>(A.p[s], i + bs, A.sp[s].kind == BP_TWO_BODY);
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec,
                                 DET ? qcount : &qn, qmax, blo, bhi, nofield);
+      ++pushed;
     }
     __syncthreads();
     if constexpr (DET) continue;  // the records are deposited by k_records
@@ -974,6 +985,7 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
     }
     __syncthreads();
   }
+  if (A.work) count_work(A.work, pushed);
   // the field box is no longer needed: the caller may start staging the next tile
   after_loop();
   // the deposits' bounding box over the block
@@ -1096,30 +1108,31 @@ template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
   cudaMemsetAsync(a.tile_n, 0, sizeof(int), s);
   k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
-  size_t smem = push_smem_bytes(g, DET);
-  // resident blocks of the GPU (queried once per instantiation)
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push<D, DET>, push_threads(D), smem);
-    blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }
+  const size_t smem = push_smem_bytes(g, DET);
+  // as many persistent blocks as the device holds at once (worked out per
+  // context for its grid and device when it was created)
+  const int blocks = a.push_blocks > 0 ? a.push_blocks : 1;
   cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), s);
   k_push<D, DET><<<blocks < g.ntiles ? blocks : g.ntiles, push_threads(D), smem, s>>>(g, a);
   if constexpr (DET) {
-    k_records<D><<<152 * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
-                                        a.jscale);
+    k_records<D><<<a.sms * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
+                                          a.jscale);
     cudaMemsetAsync(a.grec_n, 0, sizeof(int), s);
   }
 }
 
 template <int D, bool DET>
-int prepare_one(const GridP &g) {
-  size_t smem = push_smem_bytes(g, DET);
+int prepare_one(const GridP &g, int *blocks) {
+  const size_t smem = push_smem_bytes(g, DET);
   cudaError_t e = cudaFuncSetAttribute(k_push<D, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return e == cudaSuccess ? 0 : -1;
+  if (e != cudaSuccess) return -1;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push<D, DET>, push_threads(D), smem);
+  if (e != cudaSuccess) return -1;
+  *blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  return 0;
 }
 
 }  // namespace
@@ -1135,14 +1148,14 @@ size_t push_smem_bytes(const GridP &g, int det) {
 
 size_t push_record_bytes() { return sizeof(QRec); }
 
-int push_prepare(const GridP &g, int det) {
+int push_prepare(const GridP &g, int det, int *blocks) {
   switch (g.D * 2 + (det ? 1 : 0)) {
-    case 2: return prepare_one<1, false>(g);
-    case 3: return prepare_one<1, true>(g);
-    case 4: return prepare_one<2, false>(g);
-    case 5: return prepare_one<2, true>(g);
-    case 6: return prepare_one<3, false>(g);
-    default: return prepare_one<3, true>(g);
+    case 2: return prepare_one<1, false>(g, blocks);
+    case 3: return prepare_one<1, true>(g, blocks);
+    case 4: return prepare_one<2, false>(g, blocks);
+    case 5: return prepare_one<2, true>(g, blocks);
+    case 6: return prepare_one<3, false>(g, blocks);
+    default: return prepare_one<3, true>(g, blocks);
   }
 }
 
