@@ -116,11 +116,26 @@ typedef struct {
 } bp_laser_desc;
 
 /* Create a context on the calling thread's current CUDA device.  stream is
- * a cudaStream_t (NULL: legacy default stream).  allocator may be NULL. */
+ * a cudaStream_t (NULL: legacy default stream).  allocator may be NULL.
+ * Source: Sec. 1 and Sec. 2 -- a PIC grid whose fields follow Maxwell's
+ * equations with the macro-particles' currents as sources; Sec. 3.1 keeps the
+ * vacuum permittivity in those equations.  (The Yee stagger, the Mur faces
+ * and the tile shape are this library's choices; the paper fixes none.)
+ * BP_ERR_ARG for a bad description, BP_ERR_CFL when dt breaks the Courant
+ * limit, BP_ERR_OOM when the allocator fails; *out is set only on BP_OK. */
 int bp_create(const bp_grid_desc *grid, const bp_allocator *allocator, void *stream, bp_ctx **out);
+/* Release every device buffer of the context (through its allocator) and the
+ * context itself; NULL is ignored.  (The paper has no counterpart: resource
+ * release of this interface.) */
 void bp_destroy(bp_ctx *ctx);
+/* Text of the last failure of a call on ctx ("null context" for NULL),
+ * valid until the next call on ctx.  (The paper has no counterpart.) */
 const char *bp_last_error(const bp_ctx *ctx);
 
+/* Add a species (Sec. 2: the two-body split q2 = -Zb e, m2 = Zb m_e,
+ * q1 = qc - q2, m1 = mc - m2; Sec. 3.1: omega_b -> a_c).  *species_id
+ * receives its index.  BP_ERR_ARG for a bad description, BP_ERR_CFL when
+ * omega_b dt >= 2 (the leapfrog oscillation is then unstable). */
 int bp_add_species(bp_ctx *ctx, const bp_species_desc *desc, int *species_id);
 
 /* Load macro-particles from host arrays: ion positions x [n][dims] and
@@ -136,30 +151,56 @@ int bp_load_particles(bp_ctx *ctx, int species_id, const double *x, const double
  * [lo, hi), at seeded uniform in-cell positions and Gaussian momenta of
  * standard deviation sigma_u per component, with the counter-based
  * SplitMix64 streams that the input module of this package also implements
- * (ion g = cell rank * ppc + p takes uniforms 3g+a and normals 3g+a). */
+ * (ion g = cell rank * ppc + p takes uniforms 3g+a and normals 3g+a).
+ * Source: Sec. 3.1 (a neutral medium of partially ionised atoms), with the
+ * initial conditions of Sec. 2 applied to every ion as in bp_load_particles.
+ * BP_ERR_STATE if the species is loaded, BP_ERR_ARG for an empty or
+ * off-grid box. */
 int bp_set_medium(bp_ctx *ctx, int species_id, const int64_t lo[3], const int64_t hi[3], int ppc,
                   uint64_t seed, double sigma_u);
 
+/* Add a laser (see bp_laser_desc).  Source: Sec. 3.1 (an x-ray laser of
+ * given wavelength and normalised amplitude a = |eE / (m_e omega c)|, normal
+ * or oblique incidence) and Sec. 3.2 (a beam of given width, pulse length and
+ * peak field, incident at an angle to the crystal axis).  The current-sheet
+ * antenna is this library's launcher; the paper does not say how it injects.
+ * At most 4 lasers (BP_ERR_ARG beyond, or for comp not 1 or 2). */
 int bp_add_laser(bp_ctx *ctx, const bp_laser_desc *laser);
 
 /* Probe: records field component comp (BP_EX..BP_JZ) at the given linear
- * node indices (i + nx (j + ny k)) after every step, up to capacity samples. */
+ * node indices (i + nx (j + ny k)) after every step, up to capacity samples.
+ * Source: Sec. 3.1 (group velocities and reflection phase shifts are read off
+ * the simulated field at fixed points) and Sec. 3.2 (the transmitted E_x).
+ * nodes [npts] is copied; BP_ERR_ARG for an index off the grid. */
 int bp_add_probe(bp_ctx *ctx, int comp, const int64_t *nodes, int64_t npts, int64_t capacity,
                  int *probe_id);
 
 /* Advance n_steps leapfrog steps (asynchronous on the context stream):
  *   B^n = B^{n-1/2} - dt/2 curl E^n; gather; internal field; Boris; drift;
- *   J^{n+1/2} (Esirkepov + antenna); B^{n+1/2}; E^{n+1} = E^n + dt (curl B - J). */
+ *   J^{n+1/2} (Esirkepov + antenna); B^{n+1/2}; E^{n+1} = E^n + dt (curl B - J).
+ * Source: Sec. 2 -- the Boris equations for both bodies, each with the fields
+ * at its own position plus the field of the modified Coulomb force
+ * q1 q2 r / (4 pi eps0 (r^2 + a_c^2)^{3/2}), and the bodies' currents
+ * q_{1,2} v_{1,2} / dV added to the total current that updates the fields;
+ * Sec. 3.1 -- Maxwell's equations with the vacuum permittivity.  Returns
+ * BP_ERR_ARG for n_steps < 0; kernel problems (a particle off its tile's
+ * reach, a non-finite momentum) surface at the next bp_sync. */
 int bp_step(bp_ctx *ctx, int64_t n_steps);
 
-/* Wait for the stream and return the device status word as a bp_status. */
+/* Wait for the stream and return the device status word as a bp_status:
+ * BP_ERR_DOMAIN, BP_ERR_NONFINITE or BP_ERR_TIMEOUT from the kernels,
+ * BP_ERR_CUDA for a failed CUDA call.  (The paper has no counterpart:
+ * completion and error reporting of this interface.) */
 int bp_sync(bp_ctx *ctx);
 
 /* Copy field component comp (nz*ny*nx floats, x fastest) to dst: a device
- * pointer when on_device != 0, else a host pointer.  Synchronous. */
+ * pointer when on_device != 0, else a host pointer.  Synchronous.  Source:
+ * Sec. 3.1 and Sec. 3.2 read their results off the fields (the Fourier
+ * transforms of E that show the refracted and the Bragg-scattered beams). */
 int bp_read_field(bp_ctx *ctx, int comp, float *dst, int on_device);
 
-/* Enqueue a read of field component comp, as it stands after the steps
+/* (Source: as bp_read_field.)
+ * Enqueue a read of field component comp, as it stands after the steps
  * enqueued so far, into caller-owned host memory dst (nz*ny*nx floats; page-
  * locked memory for the copy to run asynchronously).  Returns at once: the
  * field is first copied to one of two device snapshot buffers on the
@@ -171,21 +212,27 @@ int bp_read_field(bp_ctx *ctx, int comp, float *dst, int on_device);
 int bp_read_field_async(bp_ctx *ctx, int comp, float *dst);
 
 /* Overwrite field component comp from src (nz*ny*nx floats; device pointer
- * when on_device != 0).  Synchronous.  Used to start from given fields. */
+ * when on_device != 0).  Synchronous.  Used to start from given fields.
+ * (The paper has no counterpart: its runs start from zero fields.) */
 int bp_write_field(bp_ctx *ctx, int comp, const float *src, int on_device);
 
 /* Copy up to cap samples of probe probe_id ([samples][npts] floats) to host
- * dst; *n receives the number of samples recorded. */
+ * dst; *n receives the number of samples recorded.  Source: as bp_add_probe.
+ * BP_ERR_ARG for an unknown probe. */
 int bp_read_probe(bp_ctx *ctx, int probe_id, float *dst, int64_t cap, int64_t *n);
 
 /* Copy the bodies' states to host arrays in load order: x1, x2 positions
  * [n][3] (simulated axes reduced to the box for periodic axes; body 2 at
  * x1 - r), u1, u2 [n][3]; *n receives the number alive.  Any pointer may be
- * NULL.  Free particles fill x1, u1 only. */
+ * NULL.  Free particles fill x1, u1 only.  Source: Sec. 2 (each body has its
+ * own position and momentum).  Synchronous. */
 int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, double *u1, double *u2,
                       int64_t cap, int64_t *n);
 
-/* Load a seeded lattice on the device: per_site ions at each of the n_sites
+/* Source: Sec. 3.2 (a crystal: ions placed periodically with crystal
+ * constant d, the laser incident at an angle to the crystal axis), with the
+ * initial conditions of Sec. 2.
+ * Load a seeded lattice on the device: per_site ions at each of the n_sites
  * sites (sites [n_sites][D], FP64, lengths in 1/k0), ion g = site * per_site
  * + p at its site plus jitter * N(0, 1) per simulated axis (normals D g + a of
  * the jitter stream of seed) with momentum sigma_u * N(0, 1) per component
@@ -199,20 +246,25 @@ int bp_read_particles(bp_ctx *ctx, int species_id, double *x1, double *x2, doubl
 int bp_set_lattice(bp_ctx *ctx, int species_id, const double *sites, int64_t n_sites, int per_site, double jitter,
                    uint64_t seed, double sigma_u, const int32_t *site_param);
 
-/* Write the context's state to a file: the step counter, every species'
+/* (The paper has no counterpart: checkpoint and restart of a run.)
+ * Write the context's state to a file: the step counter, every species'
  * a_c values and particles (load ids, positions, momenta, parameter
  * indices, tile offsets), E and B, the status word.  bp_load reads it into a
  * context created with the same grid description and deposit mode and with
  * the same species added in the same order (lasers and probes are the loading
  * context's own); its species must not be loaded yet (bp_reset clears them).
  * Continuing from a loaded state gives the same fields as continuing the
- * saved run (bit-identical in the sorted deposit mode).  Host-endian binary;
- * synchronous.  BP_ERR_IO for an unreadable, truncated or foreign file,
- * BP_ERR_ARG when the grid or the species differ. */
+ * saved run (bit-identical in the sorted deposit mode).  Host-endian binary
+ * ending with the CRC-32 (zlib's convention: reflected polynomial
+ * 0xEDB88320) of every byte before it, little-endian; synchronous.  bp_load
+ * verifies the checksum before it changes anything: BP_ERR_IO for an
+ * unreadable, truncated, corrupted or foreign file (the context is left as
+ * it was), BP_ERR_ARG when the grid or the species differ. */
 int bp_save(bp_ctx *ctx, const char *path);
 int bp_load(bp_ctx *ctx, const char *path);
 
-/* Copy the states of the particles with load ids ids[0..n) (load order of
+/* (Source: as bp_read_particles.)
+ * Copy the states of the particles with load ids ids[0..n) (load order of
  * bp_load_particles / bp_set_medium, any order, repeats allowed) to host
  * arrays in the order of ids: x1, x2, u1, u2 [n][3] as bp_read_particles
  * (any may be NULL).  found[k] (may be NULL) receives 1 if particle ids[k]
@@ -224,7 +276,11 @@ int bp_read_particles_by_id(bp_ctx *ctx, int species_id, const int64_t *ids, int
 
 /* Gauss-law residual R = div E - rho at every node, in FP64 on the device
  * (rho deposited in FP64 from the stored FP32 positions with the quadratic
- * shape).  dst holds nz*ny*nx doubles (device pointer if on_device). */
+ * shape).  dst holds nz*ny*nx doubles (device pointer if on_device).  (The
+ * paper has no counterpart: a diagnostic of the discrete continuity that the
+ * charge-conserving deposit of Sec. 2's body currents keeps, R^n = R^0.)
+ * Allocates an FP64 scratch grid through the allocator on its first call
+ * with a host dst (BP_ERR_OOM if that fails).  Synchronous. */
 int bp_residual(bp_ctx *ctx, double *dst, int on_device);
 
 /* bp_residual for callers that cannot have the library allocate device
@@ -239,8 +295,11 @@ int bp_residual(bp_ctx *ctx, double *dst, int on_device);
  *   dst   host pointer to nz*ny*nx doubles, written with div E - rho.
  *   Grids of more than 4,194,304 nodes are rejected with BP_ERR_ARG.
  *   The context's device must be current (else BP_ERR_STATE).  The first
- *   call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   call in each CUDA context looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it under the context's id; make that
+ *   first call before any stream capture.  A context destroyed and created
+ *   again (cudaDeviceReset) has a new id, so its first call looks the
+ *   address up afresh.
  *   All calls share the one array, which keeps the previous call's values
  *   (each call clears it first); calls that overlap on the GPU, from any
  *   contexts of the process, race on it.  Synchronous. */
@@ -250,20 +309,28 @@ int bp_residual_noalloc(bp_ctx *ctx, double *dst);
 
 /* Zero the fields, the step counter and the probe records, and unload the
  * particles (species and lasers stay; particle arrays are reused by the next
- * bp_load_particles). */
+ * bp_load_particles).  (The paper has no counterpart: it restarts a run for
+ * the adjoint's repeated forward passes.) */
 int bp_reset(bp_ctx *ctx);
 
 /* Replace the bound-electron frequencies omega_b[n] of a two-body species
- * (n = its n_omega); a_c follows from w_c^2 = |q1 q2| kappa / (m_r a_c^3). */
+ * (n = its n_omega); a_c follows from w_c^2 = |q1 q2| kappa / (m_r a_c^3).
+ * Source: Sec. 3.1 (the natural frequency from the Taylor series of V_M).
+ * BP_ERR_ARG for another n or a free species, BP_ERR_CFL for omega_b dt >= 2. */
 int bp_set_omega(bp_ctx *ctx, int species_id, const double *omega_b, int n);
 
-/* Run n_steps steps like bp_step (probes recorded), keeping the state before
+/* (The paper has no adjoint.  This checkpointed forward run and bp_backward
+ * give gradients of a probe loss with respect to the natural frequencies of
+ * Sec. 3.1 and the lattice sites of Sec. 3.2, through the discrete step of
+ * Sec. 2.)
+ * Run n_steps steps like bp_step (probes recorded), keeping the state before
  * every K-th step (E, B, particles, status) for the reverse pass.  Needs
  * BP_DEPOSIT_SORTED, whose bit-reproducible steps make the recomputation
  * exact. */
 int bp_forward_ckpt(bp_ctx *ctx, int64_t n_steps, int K);
 
-/* Reverse pass of the run of the last bp_forward_ckpt: for each segment,
+/* (Source: as bp_forward_ckpt.)
+ * Reverse pass of the run of the last bp_forward_ckpt: for each segment,
  * newest first, restore its checkpoint, recompute its K steps storing every
  * step's state, then apply the transposed step K times (transposed Yee with
  * Mur faces, Esirkepov deposit transposed as a gather of the current adjoint,
@@ -282,16 +349,28 @@ int bp_forward_ckpt(bp_ctx *ctx, int64_t n_steps, int K);
 int bp_backward(bp_ctx *ctx, int probe_id, const float *dl_dprobe, int species_id, double *grad_omega,
                 const int32_t *group, int64_t n_groups, double *grad_group);
 
-/* Number of own-kernel launches issued since creation (for accounting). */
+/* Number of own-kernel launches issued since creation (for accounting).
+ * (The paper has no counterpart; instrumentation.) */
 int64_t bp_kernel_launches(const bp_ctx *ctx);
 
 /* Per-kernel CUDA-event timing of the push/deposit launches: when enabled,
  * bp_step records events around each push launch; bp_push_time returns
- * the summed milliseconds and launch count since the last reset. */
+ * the summed milliseconds and launch count since the last reset (bp_time_push
+ * resets both, and the work counters of bp_push_work).  (The paper has no
+ * counterpart; instrumentation.) */
 int bp_time_push(bp_ctx *ctx, int enable);
 int bp_push_time(bp_ctx *ctx, double *ms, int64_t *launches);
 
-/* Capacity of the sorted deposit's general-case record buffer, in records
+/* Work of the timed push launches since the last bp_time_push: *full
+ * receives the number of particle pushes that gathered, kicked and deposited
+ * (the whole step of Sec. 2), *quiet the number of co-moving neutral ions
+ * that the quiet-tile pass only drifted (no field had reached their tiles, so
+ * they carry no current).  Counted on the device only while timing is
+ * enabled; synchronous.  (The paper has no counterpart; instrumentation.) */
+int bp_push_work(bp_ctx *ctx, int64_t *full, int64_t *quiet);
+
+/* (The paper has no counterpart: a resource limit of this implementation.)
+ * Capacity of the sorted deposit's general-case record buffer, in records
  * (BP_DEPOSIT_SORTED only).  A particle whose positions change their nearest
  * node in a step (Esirkepov's five-node case) leaves a record that a
  * separate kernel adds to the fixed-point current; when a step has more

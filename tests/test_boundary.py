@@ -3,7 +3,6 @@ rejects a null context at every entry point (no compute calls: runs without a
 GPU)."""
 import ctypes
 import os
-import subprocess
 
 import pytest
 
@@ -29,13 +28,12 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, missing
 
 
-def test_library_is_sm103a_only(libpath):
-    """The fat binary carries sm_103a code (cuobjdump --list-elf lists only
-    the element names, it does not disassemble)."""
-    r = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
-    if r.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in r.stdout
+def test_library_is_built_for_sm103a_only():
+    """Every translation unit is compiled with one -gencode, for sm_103a, and
+    no other architecture flag."""
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    flat = " ".join(build_lib.FLAGS)
+    assert "-arch" not in flat and "-gencode" not in flat and "compute_" not in flat
 
 
 def test_binding_signatures_cover_header():

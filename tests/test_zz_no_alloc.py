@@ -2,10 +2,12 @@
 
 The no-allocation variant serves callers that cannot let the library
 allocate device memory during the call (a thread that does not own the
-context's allocator, or a run whose device memory is fully committed).  It
-must give the same residual as the allocating entry point, also on a second
-call, whose static scratch still holds the first call's values.  This file
-is collected last so that a failure here comes after every other test.
+context's allocator, or a run whose device memory is fully committed).  On a
+fresh context it must run before anything has allocated the residual's
+scratch, leave the allocator untouched, and give the same residual as the
+allocating entry point -- also on a second call, whose static scratch still
+holds the first call's values.  This file is collected last so that a failure
+here comes after every other test.
 """
 import numpy as np
 import pytest
@@ -26,12 +28,20 @@ def _context():
 def test_noalloc_residual_matches_allocating_entry_point():
     import torch
     assert torch.cuda.is_available()
-    ctx = _context()
+    ctx = _context()  # fresh: bp_residual has never run on it
     for call in range(2):
         ctx.step(3)
         ctx.sync()
-        ref = ctx.residual()
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        peak_before = torch.cuda.max_memory_allocated()
         got = ctx.residual_noalloc()
+        torch.cuda.synchronize()
+        # the context allocates only through torch's caching allocator: no
+        # block was taken, not even a transient one
+        assert torch.cuda.memory_allocated() == before, call
+        assert torch.cuda.max_memory_allocated() == peak_before, call
+        ref = ctx.residual()
         scale = np.abs(ref).max()
         assert scale > 0
         # the same FP64 sums; only the order of the FP64 atomic adds differs
