@@ -128,15 +128,30 @@ int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
     p.r = p.u2 = nullptr;
   }
   p.pidx = pidx ? (int *)dalloc(c, sizeof(int) * cap) : nullptr;
-  if (!p.cell || !p.off || !p.u1 || !p.id || !p.tstart || (two && (!p.r || !p.u2)) || (pidx && !p.pidx))
+  // on a failure nothing half-allocated stays behind: the next load starts afresh
+  auto drop_particles = [&]() {
+    void *got[] = {p.cell, p.off, p.u1, p.id, p.tstart, p.r, p.u2, p.pidx};
+    for (void *q : got) dfree(c, q);
+    p = PartP{};
+  };
+  if (!p.cell || !p.off || !p.u1 || !p.id || !p.tstart || (two && (!p.r || !p.u2)) || (pidx && !p.pidx)) {
+    drop_particles();
     return fail(c, BP_ERR_OOM, "particle arrays (%lld particles)", n);
+  }
   // sort scratch, shared by all species
-  const int nf = D + (two ? 9 : 3);
   c->sort_dirty = true;
-  if (!c->sb.hist) {
+  if (!c->sb.hist || !c->sb.bsum) {
+    dfree(c, c->sb.hist);
+    dfree(c, c->sb.bsum);
     c->sb.hist = (int *)dalloc(c, sizeof(int) * (c->g.ncell + 1));
     c->sb.bsum = (int *)dalloc(c, sizeof(int) * (sort_scan_blocks(c->g) + 4));
-    if (!c->sb.hist || !c->sb.bsum) return fail(c, BP_ERR_OOM, "sort scratch");
+    if (!c->sb.hist || !c->sb.bsum) {
+      dfree(c, c->sb.hist);
+      dfree(c, c->sb.bsum);
+      c->sb.hist = c->sb.bsum = nullptr;
+      drop_particles();
+      return fail(c, BP_ERR_OOM, "sort scratch");
+    }
   }
   long long need_f = (long long)(D + 9) * cap;
   if (cap > c->sort_cap) {
@@ -146,10 +161,19 @@ int alloc_particles(bp_ctx *c, Species &s, long long n, bool pidx) {
     c->sb.tmp_cell = (int *)dalloc(c, sizeof(int) * cap);
     c->sb.tmp_f = (float *)dalloc(c, sizeof(float) * need_f);
     c->sb.tmp_i = (int *)dalloc(c, sizeof(int) * 2 * cap);
-    if (!c->sb.tmp_cell || !c->sb.tmp_f || !c->sb.tmp_i) return fail(c, BP_ERR_OOM, "sort buffers");
+    if (!c->sb.tmp_cell || !c->sb.tmp_f || !c->sb.tmp_i) {
+      dfree(c, c->sb.tmp_cell);
+      dfree(c, c->sb.tmp_f);
+      dfree(c, c->sb.tmp_i);
+      c->sb.tmp_cell = nullptr;
+      c->sb.tmp_f = nullptr;
+      c->sb.tmp_i = nullptr;
+      c->sort_cap = 0;
+      drop_particles();
+      return fail(c, BP_ERR_OOM, "sort buffers");
+    }
     c->sort_cap = cap;
   }
-  (void)nf;
   return BP_OK;
 }
 
@@ -279,14 +303,17 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->tile_list = (int *)dalloc(c, sizeof(int) * g.ntiles);
   c->tile_n = (int *)dalloc(c, sizeof(int));
   c->status = (int *)dalloc(c, sizeof(int) * 4);
+  c->work = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 2);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
   if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
-      (nf && !c->frame)) {
+      !c->work || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
-  if (push_prepare(g, 0) || push_prepare(g, 1)) {
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->sms < 1) c->sms = 1;
+  if (push_prepare(g, 0, &c->push_blocks[0]) || push_prepare(g, 1, &c->push_blocks[1])) {
     bp_destroy(c);
     return BP_ERR_CUDA;
   }
@@ -606,6 +633,9 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   A.status = c->status;
   A.jscale = c->jscale;
   A.jinv = c->jinv;
+  A.work = c->timing ? c->work : nullptr;
+  A.push_blocks = c->push_blocks[c->det ? 1 : 0];
+  A.sms = c->sms;
   *nsp_out = nsp;
   return A;
 }
@@ -1005,13 +1035,77 @@ struct StateSpecies {
   int64_t n, cnt, pcap;
 };
 const char kStateMagic[8] = {'B', 'P', 'S', 'T', 'A', 'T', 'E', '1'};
+constexpr int32_t kStateVersion = 2;  // 2: a CRC-32 of every preceding byte ends the file
 
-bool wr(FILE *f, const void *p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+// CRC-32 of the IEEE 802.3 / zlib convention (reflected polynomial
+// 0xEDB88320, initial value and final xor 0xFFFFFFFF), table-driven eight
+// bytes at a time ("slicing by 8": table k gives the CRC contribution of a
+// byte followed by k zero bytes).  Portable C++: the same result on any host.
+struct Crc32 {
+  uint32_t t[8][256];
+  Crc32() {
+    for (uint32_t b = 0; b < 256; ++b) {
+      uint32_t c = b;
+      for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      t[0][b] = c;
+    }
+    for (uint32_t b = 0; b < 256; ++b)
+      for (int k = 1; k < 8; ++k) t[k][b] = (t[k - 1][b] >> 8) ^ t[0][t[k - 1][b] & 0xFFu];
+  }
+  // continue a running CRC (pass the previous return value; start from 0)
+  uint32_t update(uint32_t crc, const void *data, size_t n) const {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    uint32_t c = ~crc;
+    while (n >= 8) {
+      const uint32_t lo = c ^ ((uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24));
+      c = t[7][lo & 0xFFu] ^ t[6][(lo >> 8) & 0xFFu] ^ t[5][(lo >> 16) & 0xFFu] ^ t[4][lo >> 24] ^ t[3][p[4]] ^
+          t[2][p[5]] ^ t[1][p[6]] ^ t[0][p[7]];
+      p += 8;
+      n -= 8;
+    }
+    while (n--) c = t[0][(c ^ *p++) & 0xFFu] ^ (c >> 8);
+    return ~c;
+  }
+};
+const Crc32 &crc32_tables() {
+  static const Crc32 T;
+  return T;
+}
+
+// the running CRC of what bp_save has written so far
+thread_local uint32_t g_wr_crc = 0;
+bool wr(FILE *f, const void *p, size_t bytes) {
+  if (bytes == 0) return true;
+  g_wr_crc = crc32_tables().update(g_wr_crc, p, bytes);
+  return fwrite(p, 1, bytes, f) == bytes;
+}
 bool rd(FILE *f, void *p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
 bool wr_dev(FILE *f, const void *dev, size_t bytes) {
   std::vector<char> h(bytes);
   if (bytes && cudaMemcpy(h.data(), dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
   return wr(f, h.data(), bytes);
+}
+
+// Whether the file ends with the CRC-32 of everything before it: read once,
+// in chunks, before anything is loaded, so that a truncated or corrupted file
+// leaves the context untouched.
+bool state_crc_ok(FILE *f) {
+  if (fseek(f, 0, SEEK_END) != 0) return false;
+  const long long size = ftell(f);
+  if (size < (long long)sizeof(StateHeader) + 4 || fseek(f, 0, SEEK_SET) != 0) return false;
+  long long left = size - 4;
+  std::vector<unsigned char> buf(1 << 22);
+  uint32_t crc = 0;
+  while (left > 0) {
+    const size_t k = (size_t)std::min<long long>(left, (long long)buf.size());
+    if (fread(buf.data(), 1, k, f) != k) return false;
+    crc = crc32_tables().update(crc, buf.data(), k);
+    left -= (long long)k;
+  }
+  unsigned char tail[4];
+  if (fread(tail, 1, 4, f) != 4) return false;
+  const uint32_t want = (uint32_t)tail[0] | ((uint32_t)tail[1] << 8) | ((uint32_t)tail[2] << 16) | ((uint32_t)tail[3] << 24);
+  return want == crc && fseek(f, 0, SEEK_SET) == 0;
 }
 bool rd_dev(FILE *f, void *dev, size_t bytes) {
   std::vector<char> h(bytes);
@@ -1032,7 +1126,8 @@ int bp_save(bp_ctx *c, const char *path) {
   StateHeader h;
   memset(&h, 0, sizeof h);
   memcpy(h.magic, kStateMagic, 8);
-  h.version = 1;
+  h.version = kStateVersion;
+  g_wr_crc = 0;
   h.D = g.D;
   h.det = c->det;
   h.nsp = (int)c->sp.size();
@@ -1081,6 +1176,11 @@ int bp_save(bp_ctx *c, const char *path) {
   }
   for (int k = 0; k < 6; ++k) ok = ok && wr_dev(f, c->F[k], sizeof(float) * g.ncell);
   ok = ok && wr_dev(f, c->status, sizeof(int));
+  // the checksum of every byte above, little-endian
+  const uint32_t crc = g_wr_crc;
+  const unsigned char tail[4] = {(unsigned char)(crc & 0xFFu), (unsigned char)((crc >> 8) & 0xFFu),
+                                 (unsigned char)((crc >> 16) & 0xFFu), (unsigned char)(crc >> 24)};
+  ok = ok && fwrite(tail, 1, 4, f) == 4;
   ok = (fclose(f) == 0) && ok;
   return ok ? BP_OK : fail(c, BP_ERR_IO, "bp_save: write to %s failed", path);
 }
@@ -1097,8 +1197,10 @@ int bp_load(bp_ctx *c, const char *path) {
     return fail(c, code, "bp_load: %s (%s)", why, path);
   };
   StateHeader h;
-  if (!rd(f, &h, sizeof h) || memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+  if (!rd(f, &h, sizeof h) || memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion)
     return bad(BP_ERR_IO, "not a state file of this library");
+  if (!state_crc_ok(f)) return bad(BP_ERR_IO, "checksum mismatch: the file is truncated or corrupted");
+  if (!rd(f, &h, sizeof h)) return bad(BP_ERR_IO, "unreadable header");
   bool same = h.D == g.D && h.det == c->det && h.nsp == (int)c->sp.size() && h.dt == g.dtd;
   for (int a = 0; a < 3; ++a)
     same = same && h.n[a] == g.n[a] && h.bc[a] == g.bc[a] && h.L[a] == g.L[a] && h.dx[a] == g.dxd[a];
@@ -1198,6 +1300,19 @@ int bp_time_push(bp_ctx *c, int enable) {
   c->ev_used = 0;
   c->push_ms = 0.0;
   c->push_launches = 0;
+  cudaError_t e = cudaMemsetAsync(c->work, 0, sizeof(unsigned long long) * 2, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? BP_OK : cuda_fail(c, e, "time push");
+}
+
+int bp_push_work(bp_ctx *c, int64_t *full, int64_t *quiet) {
+  if (!c) return BP_ERR_ARG;
+  unsigned long long w[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(w, c->work, sizeof w, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "push work");
+  if (full) *full = (int64_t)w[0];
+  if (quiet) *quiet = (int64_t)w[1];
   return BP_OK;
 }
 

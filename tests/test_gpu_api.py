@@ -146,3 +146,98 @@ def test_async_field_reads_match_synchronous_reads():
     assert np.abs(bufs[-1].numpy()).max() > 0
     a.close()
     b.close()
+
+
+def test_state_file_checksum_rejects_truncated_and_corrupted_files(tmp_path):
+    """The state file ends with the CRC-32 (zlib's convention) of every byte
+    before it.  bp_load checks it before touching the context: a truncated
+    file and a file with one flipped bit give BP_ERR_IO, and the context can
+    still load the intact file afterwards."""
+    import zlib
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    path = os.path.join(tmp_path, "state.bp")
+    a, _, _ = gpu_from_workload(wl, deposit_mode=1)
+    a.step(5)
+    a.save(path)
+    a.sync()
+    fa = a.fields()
+    data = open(path, "rb").read()
+    assert int.from_bytes(data[-4:], "little") == zlib.crc32(data[:-4])
+    short = os.path.join(tmp_path, "short.bp")
+    open(short, "wb").write(data[: len(data) // 2])
+    flipped = bytearray(data)
+    flipped[len(data) - 1000] ^= 0x10  # inside the saved fields
+    flip = os.path.join(tmp_path, "flip.bp")
+    open(flip, "wb").write(bytes(flipped))
+    sp = wl.species[0]
+    b = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    b.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    for bad in (short, flip):
+        with pytest.raises(B.BPError) as e:
+            b.load(bad)
+        assert e.value.code == B.BP_ERR_IO
+    b.load(path)
+    b.sync()
+    assert np.array_equal(b.fields()[:6], fa[:6])
+    a.close()
+    b.close()
+
+
+def test_nonfinite_particles_are_rejected_at_load():
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    sp = wl.species[0]
+    for bad in ("x", "u"):
+        ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+        sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+        x, u = sp.x.copy(), sp.u.copy()
+        (x if bad == "x" else u)[len(x) // 3, 1] = np.nan
+        with pytest.raises(B.BPError) as e:
+            ctx.load_particles(sid, x, u)
+        assert e.value.code == B.BP_ERR_NONFINITE, bad
+        ctx.close()
+
+
+class _BudgetAllocator:
+    """A bp_allocator that hands out torch caching-allocator blocks until a
+    byte budget is spent, then returns NULL (a caller out of memory)."""
+
+    def __init__(self, budget):
+        import ctypes as C
+        import torch
+        from paper_2208_08038_gb300 import binding as B
+        self.left = budget
+        dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, user):
+            if nbytes > self.left:
+                return None
+            self.left -= nbytes
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0))
+
+        def _free(ptr, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = B.ALLOC_FN(_alloc)
+        self._f = B.FREE_FN(_free)
+        self.struct = B.Allocator(self._a, self._f, None)
+
+
+def test_allocator_failure_is_reported_as_oom():
+    """An allocator that returns NULL gives BP_ERR_OOM: at creation when it
+    fails at once, at the particle load when only the grid fits."""
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    sp = wl.species[0]
+    with pytest.raises(B.BPError) as e:
+        B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile, allocator=_BudgetAllocator(0))
+    assert e.value.code == B.BP_ERR_OOM
+    ncell = int(np.prod(wl.n))
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile,
+                    allocator=_BudgetAllocator(80 * ncell + (1 << 20)))
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    with pytest.raises(B.BPError) as e:
+        ctx.load_particles(sid, sp.x, sp.u)
+    assert e.value.code == B.BP_ERR_OOM
+    ctx.close()
