@@ -43,11 +43,12 @@ BYTES_CELL = 36
 # ncu's executed-instruction classes on the small 3D case with a field in
 # every tile: FFMA2 x 4 + FMUL2 x 2 + FADD2 x 2 + FFMA x 2 + FMUL + FADD.
 FLOPS_FULL_ION = 2371
-# DRAM bytes (read + write) per ion of the push launch, from ncu on the small
-# 3D case (one launch each; profiles/): None until captured for the current
-# kernels.
-TRAFFIC_FULL_ION = None
-TRAFFIC_QUIET_ION = None
+# DRAM bytes (read + write) per ion, from ncu on the small 3D case
+# (128x64x64 cells, 3,932,160 ions; one launch each): k_push with a field in
+# every tile (the field and current bytes included, so per ion at this
+# workload's 8 ions per cell) and k_push_quiet ahead of the field.
+TRAFFIC_FULL_ION = 106.1
+TRAFFIC_QUIET_ION = 54.6
 # the late window starts here: the field has crossed most of the medium
 LATE_START = 450
 UNIT = "ion-pushes/s"

@@ -311,6 +311,9 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
     bp_destroy(c);
     return BP_ERR_OOM;
   }
+  // 3D: tensor maps for the TMA staging of the push's field boxes (without
+  // them every tile is staged by per-thread copies)
+  if (encode_field_maps(g, c->F, &c->tmaps)) c->tmaps.on = 0;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->sms < 1) c->sms = 1;
   if (push_prepare(g, 0, &c->push_blocks[0]) || push_prepare(g, 1, &c->push_blocks[1])) {
@@ -772,7 +775,7 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
     }
     cudaEventRecord(c->ev[c->ev_used], st);
   }
-  launch_push(g, A, st);
+  launch_push(g, A, c->tmaps, st);
   if (c->timing) {
     cudaEventRecord(c->ev[c->ev_used + 1], st);
     c->ev_used += 2;

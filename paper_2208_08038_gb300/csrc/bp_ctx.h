@@ -82,6 +82,7 @@ struct bp_ctx {
   unsigned long long *work = nullptr;  // [2] push work counters (see PushArgs::work)
   int push_blocks[2] = {1, 1};         // resident push blocks per deposit mode (atomic, sorted)
   int sms = 1;                         // multiprocessors of the context's device
+  TmaMaps tmaps{};                     // tensor maps of E, B for the push's TMA staging (3D)
   std::vector<bp_species_state> sp;
   std::vector<LaserP> las;
   std::vector<bp_probe_state> pr;

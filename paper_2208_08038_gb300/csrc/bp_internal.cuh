@@ -1,6 +1,7 @@
 // bp_internal.cuh -- internal types and device helpers of the GB300 two-body
 // PIC library.  The C ABI is include/bp.h.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,15 +66,23 @@ struct Box {
   static constexpr int J0 = Geo<D>::L0 + 2 * M + 7, J1 = D >= 2 ? Geo<D>::L1 + 2 * M + 7 : 1,
                        J2 = D >= 3 ? Geo<D>::L2 + 2 * M + 7 : 1;
   static constexpr int OG = M + 2, OJ = M + 3;
-  // shared-memory layout: x fastest, row stride G0 / J0, padded plane stride
-  static constexpr int GP = D >= 3 ? pad_plane(G0 * G1) : G0 * G1;
+  // Shared-memory layout, x fastest.  The field box of a 3D tile is the
+  // image of one TMA box load per component: rows of GR = 16 floats (64
+  // bytes, the box's inner extent) whose first float lies SX = 1 cell before
+  // the box origin T0 - OG, so that the load starts at x = T0 - 4, a multiple
+  // of 4 floats (16 bytes); planes of GR * G1 floats; each component's
+  // stride rounded up to 32 floats (128 bytes).  1D/2D: rows of G0 floats.
+  // The current box: row stride J0, padded plane stride.
+  static constexpr int GR = D >= 3 ? 16 : G0, SX = D >= 3 ? 1 : 0;
+  static constexpr int GP = GR * G1;
   static constexpr int JP = D >= 3 ? pad_plane(J0 * J1) : J0 * J1;
-  static constexpr int GCELLS = GP * G2, JCELLS = JP * J2;
+  static constexpr int GCELLS = D >= 3 ? (GP * G2 + 31) / 32 * 32 : GP * G2, JCELLS = JP * J2;
   // global per-tile box layout (compact, x fastest)
   static constexpr int GCOMP = G0 * G1 * G2, JCOMP = J0 * J1 * J2;
-  __host__ __device__ static constexpr int gi(int x, int y, int z) { return x + G0 * y + GP * z; }
+  __host__ __device__ static constexpr int gi(int x, int y, int z) { return x + SX + GR * y + GP * z; }
   __host__ __device__ static constexpr int ji(int x, int y, int z) { return x + J0 * y + JP * z; }
 };
+static_assert(Box<3>::GR >= Box<3>::G0 + Box<3>::SX, "a 3D field box row holds the box's x extent");
 
 // particle cell index: the three cell coordinates packed in bit fields
 __host__ __device__ __forceinline__ int pack_cell(const GridP &g, int c0, int c1, int c2) {
@@ -131,6 +140,17 @@ struct PushArgs {
   int push_blocks;          // persistent push blocks for this grid on this device
   int sms;                  // multiprocessors of the device
 };
+
+// Tensor maps of the six field components (E_x, E_y, E_z, B_x, B_y, B_z)
+// for the TMA staging of 3D field boxes: FP32 [nz][ny][nx], box 16 x 15 x 15,
+// zero fill outside the grid.  on = 0: no maps (1D/2D grids, or the encoding
+// failed), every tile is staged by per-thread asynchronous copies.
+struct TmaMaps {
+  CUtensorMap m[6];
+  int on;
+};
+// encode the maps of a 3D grid's fields F[0..5]; 0 on success
+int encode_field_maps(const GridP &g, float *const F[6], TmaMaps *out);
 
 struct LaserP {
   int comp;
@@ -365,7 +385,7 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t k
 // ---------------------------------------------------------------------------
 // launch wrappers (host side), one translation unit each
 
-void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s);
+void launch_push(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s);
 size_t push_smem_bytes(const GridP &g, int det);
 size_t push_record_bytes();  // one general-case deposit record
 // set the push kernel's shared-memory limit for this grid and return, in

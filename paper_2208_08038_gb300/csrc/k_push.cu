@@ -859,18 +859,99 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
   }
 }
 
-// Staging of a tile's field box (E, B of the tile plus halo; zero outside
-// open faces) by asynchronous copies into shared memory: no registers held,
-// so the copies can run while the block finishes the previous tile.  A
-// QS_REST tile's box is all zero and is not staged.
+// byte offset of the field box in the push's dynamic shared memory (after the
+// current box, 128-byte aligned for the TMA loads)
+__host__ __device__ constexpr size_t push_gbox_offset(int D, bool det) {
+  return ((det ? 8 : 4) * (size_t)3 *
+              (D == 1 ? Box<1>::JCELLS : (D == 2 ? Box<2>::JCELLS : Box<3>::JCELLS)) + 127) / 128 * 128;
+}
+
+// ---------------------------------------------------------------------------
+// TMA staging of 3D field boxes: one cp.async.bulk.tensor load per component,
+// completing on an mbarrier (transaction bytes), issued by one thread.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// a bounded wait for the phase of the given parity: false when it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Whether tile t's field box comes by TMA: 3D with maps, and no periodic
+// axis wraps inside the box (TMA fills zeros outside the grid, which is what
+// an open face reads; a wrapped box is staged by per-thread copies).
 template <int D>
-__device__ __forceinline__ void stage_issue(const GridP &g, const PushArgs &A, int t, float *Gsm) {
+__device__ __forceinline__ bool tma_tile(const GridP &g, const TmaMaps &T, const int T0[3]) {
+  if constexpr (D != 3) {
+    return false;
+  } else {
+    // maps present, and the block's field box 128-byte aligned in shared memory
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!T.on || ((smem_u32(smem) + (unsigned)push_gbox_offset(3, true)) & 127u) ||
+        ((smem_u32(smem) + (unsigned)push_gbox_offset(3, false)) & 127u))
+      return false;
+    using BX = Box<3>;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int lo = T0[a] - BX::OG - (a == 0 ? BX::SX : 0);
+      const int ext = a == 0 ? BX::GR : (a == 1 ? BX::G1 : BX::G2);
+      if (g.bc[a] == BP_PERIODIC) ok &= lo >= 0 && lo + ext <= g.n[a];
+    }
+    return ok;
+  }
+}
+
+// Staging of a tile's field box (E, B of the tile plus halo; zero outside
+// open faces), in shared memory: by TMA where tma_tile allows (one thread
+// issues six box loads), else by per-thread asynchronous copies.  Neither
+// holds registers, so the copies run while the block finishes the previous
+// tile.  A QS_REST tile's box is all zero and is not staged.
+template <int D>
+__device__ __forceinline__ void stage_issue(const GridP &g, const PushArgs &A, const TmaMaps &T, int t, float *Gsm,
+                                            unsigned long long *bar) {
   using BX = Box<D>;
   constexpr int GC = BX::GCELLS;
   if (A.qstate[t] != QS_PUSH) return;
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  const unsigned gbase = (unsigned)__cvta_generic_to_shared(Gsm);
+  if (tma_tile<D>(g, T, T0)) {
+    if (threadIdx.x == 0) {
+      // the previous tile's box was read by ordinary loads before this point
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, 6u * 4u * (unsigned)(BX::GP * BX::G2));
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc)
+        tma_load_3d(Gsm + cc * GC, &T.m[cc], T0[0] - BX::OG - BX::SX, T0[1] - BX::OG, T0[2] - BX::OG, bar);
+    }
+    return;
+  }
+  const unsigned gbase = smem_u32(Gsm);
   for (int q = threadIdx.x; q < BX::GCOMP; q += blockDim.x) {
     const int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     const int bidx[3] = {b0, b1, b2};
@@ -900,14 +981,27 @@ __device__ __forceinline__ void stage_issue(const GridP &g, const PushArgs &A, i
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// wait for this thread's copies; whether any of them is non-zero
+// wait for tile t's staging (this thread's copies, or the TMA loads: the
+// mbarrier phase `phase`, flipped here after each TMA tile); whether any
+// staged value is non-zero.  A TMA wait that gives up sets ST_TIMEOUT and
+// `failed`.
 template <int D>
-__device__ __forceinline__ bool stage_done(const PushArgs &A, int t, const float *Gsm) {
+__device__ __forceinline__ bool stage_done(const GridP &g, const PushArgs &A, const TmaMaps &T, int t,
+                                           const float *Gsm, unsigned long long *bar, unsigned &phase, bool &failed) {
   using BX = Box<D>;
   constexpr int GC = BX::GCELLS;
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   bool nz = false;
   if (A.qstate[t] != QS_PUSH) return nz;
+  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  if (tma_tile<D>(g, T, T0)) {
+    if (!mbar_wait(bar, phase)) {
+      if (threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+      failed = !mbar_wait(bar, phase);  // one more bounded wait for the loads in flight
+    }
+    phase ^= 1u;
+  }
   for (int q = threadIdx.x; q < BX::GCOMP; q += blockDim.x) {
     const int b0 = q % BX::G0, b1 = (q / BX::G0) % BX::G1, b2 = q / (BX::G0 * BX::G1);
     const int si = BX::gi(b0, b1, b2);
@@ -919,20 +1013,22 @@ __device__ __forceinline__ bool stage_done(const PushArgs &A, int t, const float
 
 // one tile of the push (the block's work for tile t)
 template <int D, bool DET, typename AfterLoop>
-__device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, const int t, AfterLoop &&after_loop) {
+__device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, const TmaMaps &T, const int t,
+                                          unsigned long long *bar, unsigned &phase, bool &failed,
+                                          AfterLoop &&after_loop) {
   using JT = typename std::conditional<DET, unsigned int, float>::type;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   using BX = Box<D>;
   constexpr int JC = BX::JCELLS, GC = BX::GCELLS;
-  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * JC;  // low (and high) words
+  constexpr size_t GOFF = push_gbox_offset(D, DET);
   JT *Jsm = reinterpret_cast<JT *>(smem);
-  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
+  float *Gsm = reinterpret_cast<float *>(smem + GOFF);
   const int tid = threadIdx.x, bs = blockDim.x;
   const unsigned char qs = A.qstate[t];
   int total = 0;
   for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
   if (qs == QS_DONE || total == 0) {
-    stage_done<D>(A, t, Gsm);  // this tile's copies land before the next tile's are issued
+    stage_done<D>(g, A, T, t, Gsm, bar, phase, failed);  // this tile's copies land before the next tile's are issued
     __syncthreads();
     if (tid == 0 && qs != QS_DONE) A.occ[t] = 0;
     after_loop();
@@ -945,10 +1041,10 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
   zero_box<DET>(Jsm, 3 * JC, tid, bs);
   // the field box was staged asynchronously (stage_issue) by the caller
-  const bool nz = stage_done<D>(A, t, Gsm);
+  const bool nz = stage_done<D>(g, A, T, t, Gsm, bar, phase, failed);
   const bool nofield = !__syncthreads_or(nz);
   QRec *qrec = DET ? reinterpret_cast<QRec *>(A.grec)
-                   : reinterpret_cast<QRec *>(smem + JBYTES + sizeof(float) * 6 * (size_t)GC);
+                   : reinterpret_cast<QRec *>(smem + GOFF + sizeof(float) * 6 * (size_t)GC);
   int *const qcount = DET ? A.grec_n : nullptr;
   const int qmax = DET ? A.grec_cap : push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
@@ -1047,11 +1143,19 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
 // block's shared memory and setup are reused from tile to tile, and the next
 // tile's field box is staged while the block finishes the current one.
 template <int D, bool DET>
-__global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr size_t JBYTES = (DET ? 8 : 4) * (size_t)3 * Box<D>::JCELLS;
-  float *Gsm = reinterpret_cast<float *>(smem + JBYTES);
+__global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A, const __grid_constant__ TmaMaps T) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *Gsm = reinterpret_cast<float *>(smem + push_gbox_offset(D, DET));
   __shared__ int next;
+  __shared__ __align__(8) unsigned long long bar;  // completion of the TMA staging
+  __shared__ int give_up;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    give_up = 0;
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  bool failed = false;
   const int nlist = *A.tile_n;
   auto grab = [&]() {
     if (threadIdx.x == 0) {
@@ -1059,13 +1163,17 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A) {
       next = k < nlist ? A.tile_list[k] : -1;
     }
     __syncthreads();
-    if (next >= 0) stage_issue<D>(g, A, next, Gsm);
+    if (next >= 0) stage_issue<D>(g, A, T, next, Gsm, &bar);
   };
   grab();
   for (int t = next; t >= 0; t = next) {
-    push_tile<D, DET>(g, A, t, grab);
+    push_tile<D, DET>(g, A, T, t, &bar, phase, failed, grab);
+    if (failed) give_up = 1;
     __syncthreads();  // every thread has read `next` before it changes
+    if (give_up) break;  // a staging wait gave up twice (ST_TIMEOUT is set): stop
   }
+  // nothing may be in flight into this block's shared memory when it exits
+  if (next >= 0 && A.qstate[next] == QS_PUSH) stage_done<D>(g, A, T, next, Gsm, &bar, phase, failed);
 }
 
 // Sorted mode: the records' rows added to the fixed-point current.  Each
@@ -1105,7 +1213,7 @@ __global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict
 }
 
 template <int D, bool DET>
-void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
+void launch_one(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s) {
   cudaMemsetAsync(a.tile_n, 0, sizeof(int), s);
   k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
   const size_t smem = push_smem_bytes(g, DET);
@@ -1113,7 +1221,7 @@ void launch_one(const GridP &g, const PushArgs &a, cudaStream_t s) {
   // context for its grid and device when it was created)
   const int blocks = a.push_blocks > 0 ? a.push_blocks : 1;
   cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), s);
-  k_push<D, DET><<<blocks < g.ntiles ? blocks : g.ntiles, push_threads(D), smem, s>>>(g, a);
+  k_push<D, DET><<<blocks < g.ntiles ? blocks : g.ntiles, push_threads(D), smem, s>>>(g, a, tm);
   if constexpr (DET) {
     k_records<D><<<a.sms * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
                                           a.jscale);
@@ -1143,7 +1251,8 @@ size_t push_smem_bytes(const GridP &g, int det) {
   if (g.D == 2) { jc = Box<2>::JCELLS; gc = Box<2>::GCELLS; }
   if (g.D == 3) { jc = Box<3>::JCELLS; gc = Box<3>::GCELLS; }
   // the sorted mode keeps its records in global memory
-  return (det ? 8 : 4) * (size_t)3 * jc + 4 * (size_t)6 * gc + (det ? 0 : sizeof(QRec) * (size_t)push_qmax(g.D));
+  (void)jc;
+  return push_gbox_offset(g.D, det != 0) + 4 * (size_t)6 * gc + (det ? 0 : sizeof(QRec) * (size_t)push_qmax(g.D));
 }
 
 size_t push_record_bytes() { return sizeof(QRec); }
@@ -1159,14 +1268,46 @@ int push_prepare(const GridP &g, int det, int *blocks) {
   }
 }
 
-void launch_push(const GridP &g, const PushArgs &a, cudaStream_t s) {
+void launch_push(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s) {
   const bool det = a.jscale != 0.0f;
   switch (g.D * 2 + (det ? 1 : 0)) {
-    case 2: launch_one<1, false>(g, a, s); break;
-    case 3: launch_one<1, true>(g, a, s); break;
-    case 4: launch_one<2, false>(g, a, s); break;
-    case 5: launch_one<2, true>(g, a, s); break;
-    case 6: launch_one<3, false>(g, a, s); break;
-    default: launch_one<3, true>(g, a, s); break;
+    case 2: launch_one<1, false>(g, a, tm, s); break;
+    case 3: launch_one<1, true>(g, a, tm, s); break;
+    case 4: launch_one<2, false>(g, a, tm, s); break;
+    case 5: launch_one<2, true>(g, a, tm, s); break;
+    case 6: launch_one<3, false>(g, a, tm, s); break;
+    default: launch_one<3, true>(g, a, tm, s); break;
   }
+}
+
+// The six field maps of a 3D grid: FP32 [nz][ny][nx] (strides in bytes
+// between rows and planes), box {16, 15, 15} = one staged field box, no
+// swizzle, zeros outside the grid.  cuTensorMapEncodeTiled comes through the
+// runtime's driver entry point, so the library does not link the driver.
+int encode_field_maps(const GridP &g, float *const F[6], TmaMaps *out) {
+  out->on = 0;
+  if (g.D != 3) return 0;
+  using encode_fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void *fp = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fp)
+    return -1;
+  const encode_fn encode = reinterpret_cast<encode_fn>(fp);
+  const cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)Box<3>::GR, (cuuint32_t)Box<3>::G1, (cuuint32_t)Box<3>::G2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (strides[0] % 16 || strides[1] % 16) return -1;
+  for (int c = 0; c < 6; ++c) {
+    if (reinterpret_cast<uintptr_t>(F[c]) % 16) return -1;
+    CUresult r = encode(&out->m[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, F[c], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+  }
+  out->on = 1;
+  return 0;
 }
