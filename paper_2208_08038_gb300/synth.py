@@ -354,3 +354,101 @@ def ionized_crystal_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), cells_p
     return Workload("ionized_crystal_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las,
                     tile=(16, 16), free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
                     meta=dict(sites=st, lo=lo, hi=hi, sigma=sigma))
+
+
+# ---------------------------------------------------------------------------
+# resonance scan (Sec. 3.1: group velocity and reflection phase against a_c)
+
+N_AU_OVER_NC_12NM = 5.9e22 / (1.11485e21 / 0.0124 ** 2)  # Au atoms per n_c at 12.4 nm: 8.14e-3
+
+
+def resonance_1d(omega_b: float, role: str = "transmit", seed: int = 6, ppc: int = 2,
+                 cells_per_lambda: int = 64, nx: int = 2048, slab=None, probe_lambda: float = None,
+                 fwhm_cycles: float = 5.0, a0: float = 1e-5, Zb: float = 78.0, steps: int = None,
+                 vacuum: bool = False) -> Workload:
+    """1D scan of Sec. 3.1's gold at 12.4 nm: two-body ions with Z_b = 78
+    bound electrons and q_c = +1 (one free electron per atom, present as a
+    free species at the same positions, so the slab starts neutral), atom
+    density 5.9e22 cm^-3 = 8.14e-3 n_c, natural frequency omega_b (the a_c
+    scan of Sec. 3.1 in the equivalent omega_b form).  Ions and electrons sit
+    at regular sub-cell positions (ppc per cell, no jitter: a uniform medium).
+    role "transmit": a 12 lambda slab from x = 4 lambda, the probe 4 lambda
+    behind it (group velocity from the transmitted pulse); role "reflect": a
+    4 lambda slab from x = 6 lambda, the probe 2 lambda in front of it
+    (reflection phase from the reflected pulse).  vacuum: the same geometry
+    without the medium (the reference trace).  An a0 = 1e-5 Gaussian pulse of
+    fwhm_cycles intensity FWHM, E_y."""
+    dx = LAMBDA0 / cells_per_lambda
+    if slab is None:
+        slab = (4.0, 16.0) if role == "transmit" else (6.0, 10.0)
+    if probe_lambda is None:
+        probe_lambda = slab[1] + 4.0 if role == "transmit" else slab[0] - 2.0
+    lo, hi = int(round(slab[0] * cells_per_lambda)), int(round(slab[1] * cells_per_lambda))
+    n_ion = N_AU_OVER_NC_12NM
+    cells = np.arange(lo, hi)
+    sub = (np.arange(ppc) + 0.5) / ppc
+    x = ((cells[:, None] + sub[None, :]) * dx).reshape(-1, 1)
+    u = np.zeros((len(x), 3))
+    sp = []
+    if not vacuum:
+        sp.append(TwoBody(Zb=Zb, qc=1.0, mc=M_AU, w=n_ion / ppc, lambda0_m=12.4e-9,
+                          omega_b=np.array([omega_b]), x=x, u=u))
+        sp.append(Free(q=-1.0, m=1.0, w=n_ion / ppc, x=x.copy(), u=u.copy()))
+    fwhm = fwhm_cycles * T0
+    las = [Laser(comp=1, a0=a0, fwhm=fwhm, t0=1.5 * fwhm, ia=8)]
+    dt = 0.95 * dx
+    if steps is None:
+        # the pulse has passed the probe even when the slab delays it by 2.5
+        # times its length (group index up to 3.5)
+        steps = int(round((1.5 * fwhm + probe_lambda * T0 + 3.0 * fwhm + 2.5 * (slab[1] - slab[0]) * T0) / dt))
+    n = (nx, 1, 1)
+    probe = np.array([_lin(n, int(round(probe_lambda * cells_per_lambda)))], dtype=np.int64)
+    return Workload("resonance_1d", 1, (nx,), (dx,), dt, (1,), steps, sp, las, tile=(16,),
+                    probe_comp=1, probe_nodes=probe,
+                    free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
+                    meta=dict(slab=(lo, hi), n_ion=n_ion, omega_b=omega_b, Zb=Zb, role=role,
+                              probe_x=probe[0] * dx, fwhm=fwhm, t0=1.5 * fwhm))
+
+
+# ---------------------------------------------------------------------------
+# oblique refraction (Sec. 3.1: gold at 56 nm, Z_b = 20, incidence pi/6)
+
+N_AU_OVER_NC_56NM = 5.9e22 / (1.11485e21 / 0.056 ** 2)  # Au atoms per n_c at 56 nm: 0.166
+
+
+def refraction_2d(omega_b: float = 2.0, n=(192, 160), cells_per_lambda: int = 16, surface_lambda: float = 3.0,
+                  theta_deg: float = 30.0, waist_lambda: float = 2.0, fwhm_cycles: float = 3.0,
+                  a0: float = 1e-5, Zb: float = 20.0, steps: int = None, vacuum: bool = False) -> Workload:
+    """2D oblique refraction of Sec. 3.1's gold at 56 nm: two-body ions with
+    Z_b = 20 and q_c = +1 plus one free electron per atom (at the same
+    positions: the medium starts neutral), 5.9e22 atoms/cm^3 = 0.166 n_c,
+    natural frequency omega_b, one ion (and one electron) per cell at the cell
+    centre, filling x >= surface_lambda (to the open x face) over the
+    periodic y extent.  An s-polarised (E_z) Gaussian pulse of intensity FWHM
+    fwhm_cycles and waist waist_lambda, incident at theta_deg on the surface,
+    aimed at the centre of the surface."""
+    dx = LAMBDA0 / cells_per_lambda
+    nx, ny = n
+    lo = int(round(surface_lambda * cells_per_lambda))
+    n_ion = N_AU_OVER_NC_56NM
+    ii, jj = np.meshgrid(np.arange(lo, nx), np.arange(ny), indexing="xy")
+    x = np.stack([(ii.ravel() + 0.5) * dx, (jj.ravel() + 0.5) * dx], axis=1)
+    u = np.zeros((len(x), 3))
+    sp = []
+    if not vacuum:
+        sp.append(TwoBody(Zb=Zb, qc=1.0, mc=M_AU, w=n_ion, lambda0_m=56e-9, omega_b=np.array([omega_b]),
+                          x=x, u=u))
+        sp.append(Free(q=-1.0, m=1.0, w=n_ion, x=x.copy(), u=u.copy()))
+    th = math.radians(theta_deg)
+    ia = 8
+    Ly = ny * dx
+    yc = 0.5 * Ly - (lo - ia) * dx * math.tan(th)
+    fwhm = fwhm_cycles * T0
+    las = [Laser(comp=2, a0=a0, theta=th, waist=waist_lambda * LAMBDA0, fwhm=fwhm, t0=1.5 * fwhm, ia=ia, yc=yc)]
+    dt = 0.95 * dx / math.sqrt(2.0)
+    if steps is None:
+        # the pulse centre has gone some 7 lambda (vacuum path) past the surface
+        steps = int(round((1.5 * fwhm + ((lo - ia) * dx / math.cos(th)) + 7.0 * LAMBDA0) / dt))
+    return Workload("refraction_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las, tile=(16, 16),
+                    free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
+                    meta=dict(surface=lo, n_ion=n_ion, omega_b=omega_b, Zb=Zb, theta=th))
