@@ -167,7 +167,7 @@ def _ring_peak(F, KX, KY, exclude_deg, half_width=20.0):
     ring = (kr > 0.85) & (kr < 1.15) & (KX > 0)
     ring &= np.abs(ang - exclude_deg) > half_width
     i = np.argmax(np.where(ring, F, 0))
-    return F.flat[i], ang.flat[i], kr.flat[i]
+    return F.flat[i], ang.flat[i], kr.flat[i], KX.flat[i], KY.flat[i]
 
 
 @pytest.mark.slow
@@ -176,13 +176,30 @@ def test_bragg_peak_direction():
     to the lattice rows (Bragg's law 2 d sin(theta_B) = lambda, Sec. 3.2):
     besides the incident beam, the strongest forward component of the field
     spectrum lies at k_i + G, i.e. at 2 theta_B = 60 deg from the incident
-    direction (-30 deg), within one FFT bin.  Control (lattice rows along the
-    beam, Sec. 3.2 case (b)): nothing comparable at 60 deg from incidence."""
+    direction (-30 deg): the peak's wave vector lies within one FFT bin of
+    k_s = k_i + G, G = (2 pi / d)(0, -1), in each component (the bins of the
+    Cartesian FFT grid; |k_i| is the grid's own wavenumber at w0, 0.3% above
+    k0 at lambda/16).  Control (lattice rows along the beam, Sec. 3.2 case
+    (b)): nothing comparable at 60 deg from incidence."""
     F, KX, KY, wl = _bragg_run(30.0)
-    peak, ang, kr = _ring_peak(F, KX, KY, exclude_deg=30.0)
+    peak, ang, kr, kx, ky = _ring_peak(F, KX, KY, exclude_deg=30.0)
     L = wl.n[0] * wl.dx[0]
-    bin_deg = math.degrees(2 * math.pi / L)
-    assert abs(ang - (-30.0)) <= 1.5 * bin_deg, (ang, kr)
+    dk = 2 * math.pi / L
+    d = wl.meta["d"]
+    dx, dt = wl.dx[0], wl.dt
+    th = math.radians(30.0)
+    # the grid's wavenumber along the beam: the 2D Yee dispersion at w0,
+    # sin^2(k cos(th) dx/2) + sin^2(k sin(th) dx/2) = (dx/dt)^2 sin^2(dt/2), by bisection
+    f = lambda k: (math.sin(k * math.cos(th) * dx / 2) ** 2 + math.sin(k * math.sin(th) * dx / 2) ** 2
+                   - (dx / dt * math.sin(dt / 2)) ** 2)
+    lo, hi = 0.9, 1.1
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+    k = 0.5 * (lo + hi)
+    assert abs(k - 1.0) < 5e-3
+    ks = (k * math.cos(th), k * math.sin(th) - 2 * math.pi / d)
+    assert abs(kx - ks[0]) <= dk + 1e-9 and abs(ky - ks[1]) <= dk + 1e-9, ((kx, ky), ks, dk, ang)
     Fc, KXc, KYc, _ = _bragg_run(0.0)
     angc = np.degrees(np.arctan2(KYc, KXc))
     krc = np.hypot(KXc, KYc)
