@@ -204,6 +204,68 @@ def run_e2e(wl, n_ion, mode, steps, rank, world, dist=None):
                     "copy overlapping the next steps); context creation included"}
 
 
+BRAGG_BYTES_CELL = 168  # per cell and step: 2 B half steps (36 B), E step (72 B), clearing the current (24 B)
+
+
+def run_bragg(steps, warmup):
+    """The 2D Bragg crystal (2048^2 cells, dx = lambda/32, 40 x 40 sites of
+    4 two-body ions, 30-degree p-polarised beam): field-dominated, so the
+    figures are cell updates/s and the HBM fraction of the field kernels'
+    algorithmic bytes over the whole step (E, B, J and the fixed-point
+    current, 251 MB, exceed L2)."""
+    import torch
+    from paper_2208_08038_gb300 import binding as B
+    from paper_2208_08038_gb300 import synth
+    wl = synth.bragg_2d()
+    sp = wl.species[0]
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=B.BP_DEPOSIT_SORTED, tile=wl.tile)
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    ctx.load_particles(sid, sp.x, sp.u)
+    for L in wl.lasers:
+        ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    ctx.step(warmup)
+    ctx.sync()
+    stream = torch.cuda.current_stream()
+    ms, push_ms, push_n, full, quiet, launches = timed_window(ctx, steps, stream)
+    ctx.close()
+    ncell = wl.n[0] * wl.n[1]
+    hbm, src = peaks()
+    gbs = BRAGG_BYTES_CELL * ncell * steps / (ms * 1e-3) / 1e9
+    return {"workload": "bragg_2d: 2048x2048 cells, dx=lambda/32, 6400 two-body ions on a 40x40 lattice, "
+                        "p-polarised beam at 30 degrees, sorted deposit",
+            "steps": f"{warmup}..{warmup + steps}", "ms_per_step": ms / steps,
+            "cell_updates_per_s": ncell * steps / (ms * 1e-3), "ion_pushes_per_s": len(sp.x) * steps / (ms * 1e-3),
+            "push_ms_per_launch": push_ms / max(push_n, 1), "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_cell": BRAGG_BYTES_CELL, "peak_source": src,
+                         "scope": "whole step (field kernels' algorithmic bytes)"}}
+
+
+def run_neutral_1d(steps, warmup):
+    """The 1D neutral medium (2048 cells, dx = lambda/64, 16,384 two-body ions
+    in the 16-lambda slab, 10-cycle pulse): a few microseconds of work per
+    kernel, so the step is bound by kernel launches; reported as time per
+    step and launches per step."""
+    import torch
+    from paper_2208_08038_gb300 import binding as B
+    from paper_2208_08038_gb300 import synth
+    wl = synth.neutral_1d()
+    sp = wl.species[0]
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=B.BP_DEPOSIT_SORTED, tile=wl.tile)
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    ctx.load_particles(sid, sp.x, sp.u)
+    for L in wl.lasers:
+        ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
+    ctx.step(warmup)
+    ctx.sync()
+    ms, push_ms, push_n, full, quiet, launches = timed_window(ctx, steps, torch.cuda.current_stream())
+    ctx.close()
+    return {"workload": "neutral_1d: 2048 cells, dx=lambda/64, 16384 two-body ions, sorted deposit",
+            "steps": f"{warmup}..{warmup + steps}", "ms_per_step": ms / steps,
+            "ion_pushes_per_s": len(sp.x) * steps / (ms * 1e-3), "push_ms_per_launch": push_ms / max(push_n, 1),
+            "gpu_launches_per_step": launches / steps, "bound": "kernel launches (each kernel a few microseconds)"}
+
+
 def run_adjoint_ratio(steps=400, K=20):
     """Adjoint cost on the 2D adjoint workload (1024^2 cells, dx = lambda/32,
     524,288 ions in the bound slab on 4096 sites, per-column omega_b, 400
@@ -345,6 +407,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default: --steps)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-bragg", action="store_true", help="skip the 2D Bragg crystal and 1D medium legs")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only the adjoint/forward ratio of the 2D adjoint workload over STEPS steps")
     ap.add_argument("--late-start", type=int, default=LATE_START,
@@ -468,6 +531,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline_neutral_3d()
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = run_adjoint_ratio()
+    if rank == 0 and not args.no_bragg:
+        line["bragg_2d"] = run_bragg(max(args.steps, 100), max(args.warmup, 3))
+        line["neutral_1d"] = run_neutral_1d(1000, max(args.warmup, 3))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

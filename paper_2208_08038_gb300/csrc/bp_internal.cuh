@@ -306,33 +306,6 @@ __device__ __forceinline__ long long fx_value(const unsigned int *lo, int hoff) 
   return (long long)(int)lo[hoff] * 65536LL + (long long)(int)lo[0];
 }
 
-// The same sum with one atomic per add when values are large: the low word
-// (unsigned, initialised to 2^31) takes the low 32 bits of rne(v) and returns
-// its old value; the high word takes the high 32 bits plus the carry out of
-// the low word -- usually zero.  The pair is the exact 64-bit sum (plus the
-// 2^31 bias) whatever the order.
-__device__ __forceinline__ void fx_add_carry(unsigned int *lo, int hoff, float v) {
-  unsigned int l;
-  int hi;
-  if (fabsf(v) < 2147483648.0f) {
-    const int q = __float2int_rn(v);
-    l = (unsigned int)q;
-    hi = q >> 31;
-  } else {
-    const long long q = f2ll_rn(v);
-    l = (unsigned int)(unsigned long long)q;
-    hi = (int)(q >> 32);
-  }
-  const unsigned int old = atomicAdd(lo, l);
-  unsigned int sum;
-  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=r"(sum), "+r"(hi) : "r"(old), "r"(l));
-  (void)sum;
-  if (hi) atomicAdd(reinterpret_cast<int *>(lo + hoff), hi);
-}
-__device__ __forceinline__ long long fx_value_carry(const unsigned int *lo, int hoff) {
-  return (long long)(((unsigned long long)lo[hoff] << 32) | lo[0]) - 0x80000000LL;
-}
-
 // quadratic B-spline weights for the three nodes around the nearest node,
 // xi = position - nearest node in [-1/2, 1/2)
 __device__ __forceinline__ void qweights(float xi, float w[3]) {

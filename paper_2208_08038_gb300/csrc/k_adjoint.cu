@@ -838,7 +838,9 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
 // bodies with the gather weights into a per-tile box, in 64-bit fixed point
 // (exact, independent of the order of the adds; the scale puts the step's
 // largest |e| at 2^30, so a quantum is below 1e-9 of it), then write the box
-// (compact) for k_adj_boxsum.
+// (compact) for k_adj_boxsum.  Each add is the forward deposit's split
+// (fx_add: non-returning 32-bit shared atomics, the high word only when
+// needed), which sums the same rounded integers as any other exact order.
 struct ScatArgs {
   int nsp;
   SpecP sp[BP_MAX_SPECIES];
@@ -890,10 +892,10 @@ __device__ __forceinline__ void scatter_comp(unsigned *A, const int d1[3], const
         const float a2 = e2 * w2[1][j] * w2[2][k];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-          fx_add_carry(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, __fadd_rn(a1 * w1[0][i], a2 * w2[0][i]));
+          fx_add(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, __fadd_rn(a1 * w1[0][i], a2 * w2[0][i]));
       } else {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) fx_add_carry(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, a1 * w1[0][i]);
+        for (int i = 0; i < 3; ++i) fx_add(A + Box<D>::gi(b1[0] + i, b1[1] + j, b1[2] + k), hoff, a1 * w1[0][i]);
       }
     }
   if (two && !same) {
@@ -903,7 +905,7 @@ __device__ __forceinline__ void scatter_comp(unsigned *A, const int d1[3], const
       for (int j = 0; j < NJ; ++j) {
         const float a2 = e2 * w2[1][j] * w2[2][k];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) fx_add_carry(A + Box<D>::gi(b2[0] + i, b2[1] + j, b2[2] + k), hoff, a2 * w2[0][i]);
+        for (int i = 0; i < 3; ++i) fx_add(A + Box<D>::gi(b2[0] + i, b2[1] + j, b2[2] + k), hoff, a2 * w2[0][i]);
       }
   }
 }
@@ -926,10 +928,7 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S) {
   int ex;
   frexpf(__uint_as_float(mbits), &ex);  // emax < 2^ex
   const int k = 30 - ex;
-  for (int q = tid; q < 6 * GC; q += bs) {
-    A[q] = 0x80000000u;  // fx_add_carry's bias
-    A[6 * GC + q] = 0u;
-  }
+  for (int q = tid; q < 12 * GC; q += bs) A[q] = 0u;
   __syncthreads();
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
@@ -979,7 +978,7 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S) {
   for (int q = tid; q < 6 * GN; q += bs) {
     const int cc = q / GN, r = q - cc * GN;
     const int si = cc * GC + BX::gi(r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1));
-    out[q] = ldexpf(__ll2float_rn(fx_value_carry(A + si, 6 * GC)), -k);
+    out[q] = ldexpf(__ll2float_rn(fx_value(A + si, 6 * GC)), -k);
   }
   if (tid == 0) S.occ[t] = 1;
 }
