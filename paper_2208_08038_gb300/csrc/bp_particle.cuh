@@ -152,10 +152,12 @@ __device__ __forceinline__ void qweights2(float2 xi, float2 w[3]) {
   w[2] = __fmul2_rn(__fmul2_rn(b, H), b);
 }
 
-// components c1, c2 (stagger patterns P1, P2; boxes G1, G2) at bodies A, B
+// components c1, c2 (stagger patterns P1, P2; boxes G1, G2) at bodies A, B;
+// same: every active lane's bodies share all their stencil origins (both
+// forms give the same sums; the shared form loads each row once)
 template <int P1, int P2>
 __device__ __forceinline__ void gather_pair3(const float *__restrict__ G1, const float *__restrict__ G2, const Pos &A,
-                                             const Pos &B, float2 &oa, float2 &ob) {
+                                             const Pos &B, bool same, float2 &oa, float2 &ob) {
   float2 wa[3][3], wb[3][3];
   int a1[3], a2[3], b1[3], b2[3];
 #pragma unroll
@@ -168,8 +170,6 @@ __device__ __forceinline__ void gather_pair3(const float *__restrict__ G1, const
     b1[ax] = h1 ? B.bh[ax] : B.bn[ax];
     b2[ax] = h2 ? B.bh[ax] : B.bn[ax];
   }
-  const bool same = __all_sync(__activemask(), a1[0] == b1[0] && a1[1] == b1[1] && a1[2] == b1[2] &&
-                                                   a2[0] == b2[0] && a2[1] == b2[1] && a2[2] == b2[2]);
   float2 sa = make_float2(0.0f, 0.0f), sb = sa;
   if (same) {
 #pragma unroll
@@ -225,12 +225,16 @@ __device__ __forceinline__ void gather_pair3(const float *__restrict__ G1, const
 __device__ __forceinline__ void gather_all_p3(const float *G, const Pos &A, const Pos &Bo, float Ea[3], float Ba[3],
                                               float Eb[3], float Bb[3]) {
   constexpr int gc = Box<3>::GCELLS;
+  // one warp vote for the three pairs: both bodies on the same node and
+  // half-node stencils along every axis
+  const bool same = __all_sync(__activemask(), A.bn[0] == Bo.bn[0] && A.bn[1] == Bo.bn[1] && A.bn[2] == Bo.bn[2] &&
+                                                   A.bh[0] == Bo.bh[0] && A.bh[1] == Bo.bh[1] && A.bh[2] == Bo.bh[2]);
   float2 a, b;
-  gather_pair3<1, 5>(G + 0 * gc, G + 4 * gc, A, Bo, a, b);  // E_x, B_y
+  gather_pair3<1, 5>(G + 0 * gc, G + 4 * gc, A, Bo, same, a, b);  // E_x, B_y
   Ea[0] = a.x; Ba[1] = a.y; Eb[0] = b.x; Bb[1] = b.y;
-  gather_pair3<2, 6>(G + 1 * gc, G + 3 * gc, A, Bo, a, b);  // E_y, B_x
+  gather_pair3<2, 6>(G + 1 * gc, G + 3 * gc, A, Bo, same, a, b);  // E_y, B_x
   Ea[1] = a.x; Ba[0] = a.y; Eb[1] = b.x; Bb[0] = b.y;
-  gather_pair3<4, 3>(G + 2 * gc, G + 5 * gc, A, Bo, a, b);  // E_z, B_z
+  gather_pair3<4, 3>(G + 2 * gc, G + 5 * gc, A, Bo, same, a, b);  // E_z, B_z
   Ea[2] = a.x; Ba[2] = a.y; Eb[2] = b.x; Bb[2] = b.y;
 }
 

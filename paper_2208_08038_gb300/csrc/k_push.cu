@@ -1157,16 +1157,19 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A, c
   unsigned phase = 0;
   bool failed = false;
   const int nlist = *A.tile_n;
+  // Thread 0 reserves the block's next list entry when the block starts a
+  // tile (the atomic's latency then overlaps the tile's particles) and
+  // publishes it once the field box may be overwritten.
+  int reserved = 0;
   auto grab = [&]() {
-    if (threadIdx.x == 0) {
-      const int k = atomicAdd(A.tile_ctr, 1);
-      next = k < nlist ? A.tile_list[k] : -1;
-    }
+    if (threadIdx.x == 0) next = reserved < nlist ? A.tile_list[reserved] : -1;
     __syncthreads();
     if (next >= 0) stage_issue<D>(g, A, T, next, Gsm, &bar);
   };
+  if (threadIdx.x == 0) reserved = atomicAdd(A.tile_ctr, 1);
   grab();
   for (int t = next; t >= 0; t = next) {
+    if (threadIdx.x == 0) reserved = atomicAdd(A.tile_ctr, 1);
     push_tile<D, DET>(g, A, T, t, &bar, phase, failed, grab);
     if (failed) give_up = 1;
     __syncthreads();  // every thread has read `next` before it changes
