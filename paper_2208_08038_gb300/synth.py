@@ -452,3 +452,17 @@ def refraction_2d(omega_b: float = 2.0, n=(192, 160), cells_per_lambda: int = 16
     return Workload("refraction_2d", 2, (nx, ny), (dx, dx), dt, (1, 0), steps, sp, las, tile=(16, 16),
                     free_bounds=((2.0, -1e300, -1e300), (nx - 2.0, 1e300, 1e300)),
                     meta=dict(surface=lo, n_ion=n_ion, omega_b=omega_b, Zb=Zb, theta=th))
+
+
+def wakefield_2d(seed: int = 4, steps: int = 6000, n=(4096, 2048), span=(16.0, 112.0), a0: float = 3.0,
+                 build_particles: bool = True) -> Workload:
+    """The x-ray wakefield application of Sec. 3.2: the partially ionised
+    crystal of ionized_crystal_2d (gold pre-ionised with 30 free electrons per
+    ion, two-body ions with Z_b = 49 and q_c = +30 on a 0.6 lambda lattice,
+    free electrons at 0.1 n_c, 10 eV) driven by an a0 = 3 pulse: the
+    electrons' quiver is relativistic and the bound electrons are pulled far
+    beyond a_c, so the whole modified Coulomb potential acts, not its
+    harmonic core."""
+    wl = ionized_crystal_2d(seed=seed, steps=steps, n=n, span=span, a0=a0, build_particles=build_particles)
+    wl.name = "wakefield_2d"
+    return wl
