@@ -266,7 +266,7 @@ def run_neutral_1d(steps, warmup):
             "gpu_launches_per_step": launches / steps, "bound": "kernel launches (each kernel a few microseconds)"}
 
 
-def run_adjoint_ratio(steps=400, K=20):
+def run_adjoint_ratio(steps=400, K=20, reps=3):
     """Adjoint cost on the 2D adjoint workload (1024^2 cells, dx = lambda/32,
     524,288 ions in the bound slab on 4096 sites, per-column omega_b, 400
     steps, checkpoints every 20): (checkpointed forward + backward) / plain
@@ -306,16 +306,22 @@ def run_adjoint_ratio(steps=400, K=20):
         ctx.sync()
 
     plain()  # warm-up
-    t_plain = timed(plain)
     probe = prob.run(sp.omega_b, sites)  # warm-up of the checkpointed path
     dl = (2.0 * probe).astype(np.float32)
     prob.gradients(dl, len(sp.omega_b))
-    t_fwd = timed(lambda: prob.run(sp.omega_b, sites))
-    t_bwd = timed(lambda: prob.gradients(dl, len(sp.omega_b)))
+    # each phase `reps` times, interleaved; the medians (a single repetition
+    # is exposed to host-side delays in the set-up calls)
+    tp, tf, tb = [], [], []
+    for _ in range(reps):
+        tp.append(timed(plain))
+        tf.append(timed(lambda: prob.run(sp.omega_b, sites)))
+        tb.append(timed(lambda: prob.gradients(dl, len(sp.omega_b))))
+    t_plain, t_fwd, t_bwd = (sorted(v)[len(v) // 2] for v in (tp, tf, tb))
     ctx.close()
     return {"workload": "adjoint_2d: 1024x1024 cells, dx=lambda/32, 524288 ions on 4096 sites, "
                         "1024 per-column omega_b, 400 steps, checkpoint every 20",
             "plain_forward_ms": t_plain, "ckpt_forward_ms": t_fwd, "backward_ms": t_bwd,
+            "repetitions_ms": {"plain": tp, "ckpt_forward": tf, "backward": tb},
             "ratio": (t_fwd + t_bwd) / t_plain,
             "backward_over_forward": t_bwd / t_plain,
             "definitions": "ratio = (checkpointed forward + backward) / plain forward; backward_over_forward = "
@@ -412,6 +418,7 @@ def main():
                     help="only the adjoint/forward ratio of the 2D adjoint workload over STEPS steps")
     ap.add_argument("--late-start", type=int, default=LATE_START,
                     help="step at which the late (field-covered) window starts")
+    ap.add_argument("--adjoint-reps", type=int, default=3, help="timed repetitions of each adjoint phase")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the 3D workload on 128x64x64 cells (profiling)")
     args = ap.parse_args()
@@ -427,7 +434,8 @@ def main():
         import torch
         torch.cuda.set_device(local)
         if rank == 0:
-            print(json.dumps({"adjoint": run_adjoint_ratio(steps=args.adjoint_only)}), flush=True)
+            print(json.dumps({"adjoint": run_adjoint_ratio(steps=args.adjoint_only, reps=args.adjoint_reps)}),
+                  flush=True)
         return
 
     import torch

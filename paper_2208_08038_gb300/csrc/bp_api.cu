@@ -293,6 +293,7 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
     c->jfx = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 3 * (size_t)ncell);
     c->ant = (double *)dalloc(c, sizeof(double) * BP_MAX_LASER * (size_t)(ncell / g.n[0]));
     c->grec_n = (int *)dalloc(c, sizeof(int));
+    c->far_n = (int *)dalloc(c, sizeof(int));
   }
   else c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
@@ -306,7 +307,7 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->work = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 2);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
+  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n || !c->far_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
       !c->work || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
@@ -343,6 +344,14 @@ void bp_destroy(bp_ctx *c) {
     if (c->snap_done[k]) cudaEventDestroy(c->snap_done[k]);
   }
   if (c->sort_runs) cudaFreeHost(c->sort_runs);
+  if (c->adj.stream) {
+    cudaStreamSynchronize(c->adj.stream);
+    cudaStreamDestroy(c->adj.stream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (c->adj.rec_done[k]) cudaEventDestroy(c->adj.rec_done[k]);
+    if (c->adj.rev_done[k]) cudaEventDestroy(c->adj.rev_done[k]);
+  }
   std::vector<void *> all = c->owned;
   for (void *p : all) dfree(c, p);
   delete c;
@@ -600,6 +609,13 @@ void ensure_records(bp_ctx *c) {
     if (s.loaded) n += s.p.cap;
   const long long want =
       c->grec_fixed > 0 ? c->grec_fixed : std::min<long long>(1LL << 30, std::max<long long>(65536, n / 256));
+  // the far-ion list: as many entries as the default record capacity
+  const long long want_far = std::min<long long>(1LL << 30, std::max<long long>(65536, n / 256));
+  if (!c->far || c->far_cap < want_far) {
+    if (c->far) dfree(c, c->far);
+    c->far = (int4 *)dalloc(c, sizeof(int4) * (size_t)want_far);
+    c->far_cap = c->far ? want_far : 0;
+  }
   if (c->grec && (c->grec_fixed > 0 ? c->grec_cap == want : c->grec_cap >= want)) return;
   if (c->grec) dfree(c, c->grec);
   c->grec = dalloc(c, push_record_bytes() * (size_t)want);
@@ -626,6 +642,9 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   A.jfx = c->jfx;
   A.grec = c->grec;
   A.grec_n = c->grec_n;
+  A.far = c->far;
+  A.far_n = c->far_n;
+  A.far_cap = (int)c->far_cap;
   A.grec_cap = (int)c->grec_cap;
   A.occ = c->occ;
   A.jbb = c->jbb;
@@ -1391,8 +1410,8 @@ int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
       }
     ad.ck_fields.assign(nseg, nullptr);
     ad.ck_parts.assign(nseg, std::vector<bp_part_copy>(c->sp.size()));
-    ad.st_fields.assign(K, nullptr);
-    ad.st_parts.assign(K, std::vector<bp_part_copy>(c->sp.size()));
+    ad.st_fields.assign(2 * K, nullptr);
+    ad.st_parts.assign(2 * K, std::vector<bp_part_copy>(c->sp.size()));
     for (int k = 0; k < nseg; ++k) {
       ad.ck_fields[k] = (float *)dalloc(c, sizeof(float) * 6 * g.ncell);
       if (!ad.ck_fields[k]) return fail(c, BP_ERR_OOM, "checkpoint fields");
@@ -1400,7 +1419,7 @@ int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
         if (copy_alloc(c, c->sp[q].p, g.D, c->sp[q].sp.kind == BP_TWO_BODY, ad.ck_parts[k][q].p))
           return fail(c, BP_ERR_OOM, "checkpoint particles");
     }
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < 2 * K; ++k) {
       ad.st_fields[k] = (float *)dalloc(c, sizeof(float) * 6 * g.ncell);
       if (!ad.st_fields[k]) return fail(c, BP_ERR_OOM, "step store fields");
       for (size_t q = 0; q < c->sp.size(); ++q)
@@ -1465,7 +1484,8 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     ad.box = (float *)dalloc(c, sizeof(float) * 6 * (size_t)g.gcells * g.ntiles);
     ad.occ = (unsigned char *)dalloc(c, g.ntiles);
     ad.emax = (unsigned *)dalloc(c, sizeof(unsigned));
-    if (!ad.box || !ad.occ || !ad.emax) return fail(c, BP_ERR_OOM, "adjoint boxes");
+    ad.status = (int *)dalloc(c, sizeof(int));
+    if (!ad.box || !ad.occ || !ad.emax || !ad.status) return fail(c, BP_ERR_OOM, "adjoint boxes");
   }
   bool xb_ok = ad.xb.size() == c->sp.size() && ad.xb_cap.size() == c->sp.size();
   for (size_t q = 0; xb_ok && q < c->sp.size(); ++q) xb_ok = ad.xb_cap[q] == c->sp[q].p.cap;
@@ -1499,6 +1519,7 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     cudaMemsetAsync(ad.H[k], 0, sizeof(float) * g.ncell, st);
   }
   cudaMemsetAsync(ad.emax, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(ad.status, 0, sizeof(int), st);
   for (size_t q = 0; q < c->sp.size(); ++q) {
     cudaMemsetAsync(ad.xb[q], 0, sizeof(float) * 12 * c->sp[q].p.cap, st);
     cudaMemsetAsync(ad.acb[q], 0, sizeof(double) * c->sp[q].p.cap, st);
@@ -1516,7 +1537,27 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     acbs.push_back(ad.acb[q]);
     caps.push_back(c->sp[q].p.cap);
   }
-  for (int seg = ad.nseg - 1; seg >= 0; --seg) {
+  // Two streams: each segment (newest first) is recomputed on the context's
+  // stream into one bank of the per-step stores, and its reverse steps run on
+  // the adjoint stream from that bank; the recomputation of the next
+  // (earlier) segment, into the other bank, overlaps them.  A bank is
+  // recomputed again only after the reverse steps that read it are done.
+  if (!ad.stream) {
+    if (cudaStreamCreateWithFlags(&ad.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      ad.stream = nullptr;
+      return cuda_fail(c, cudaGetLastError(), "adjoint stream");
+    }
+    for (int k = 0; k < 2; ++k) {
+      cudaEventCreateWithFlags(&ad.rec_done[k], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&ad.rev_done[k], cudaEventDisableTiming);
+    }
+  }
+  cudaStream_t as = ad.stream;
+  const int K = ad.K;
+  auto recompute = [&](int seg) -> int {
+    const int bank = seg & 1;
+    // the reverse steps of segment seg + 2 read this bank
+    if (seg + 2 <= ad.nseg - 1) cudaStreamWaitEvent(st, ad.rev_done[bank], 0);
     // restore the checkpoint and recompute the segment, storing each step
     CopyList L;
     for (int f = 0; f < 6; ++f) cl_add(c, L, ad.ck_fields[seg] + (size_t)f * g.ncell, c->F[f], sizeof(float) * g.ncell);
@@ -1525,38 +1566,47 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     cl_add(c, L, ad.ck_status + 4 * seg, c->status, sizeof(int) * 4);
     cl_flush(c, L);
     refresh_marks(c);
-    const long long base = (long long)seg * ad.K;
-    const long long len = std::min<long long>(ad.K, ad.nsteps - base);
+    const long long base = (long long)seg * K;
+    const long long len = std::min<long long>(K, ad.nsteps - base);
     c->step = ad.start + base;
     for (long long j = 0; j < len; ++j) {
-      int rc = one_step(c, A, nsp, false, ad.st_fields[j], &ad.st_parts[j]);
+      int rc = one_step(c, A, nsp, false, ad.st_fields[bank * K + j], &ad.st_parts[bank * K + j]);
       if (rc) return rc;
     }
+    cudaEventRecord(ad.rec_done[bank], st);
+    return BP_OK;
+  };
+  auto reverse = [&](int seg) -> int {
+    const int bank = seg & 1;
+    cudaStreamWaitEvent(as, ad.rec_done[bank], 0);
+    const long long base = (long long)seg * K;
+    const long long len = std::min<long long>(K, ad.nsteps - base);
     for (long long j = len - 1; j >= 0; --j) {
       const long long n = base + j;  // step n maps state n to n + 1
       // loss on the probe sample recorded after step n
       if (n < nrec) {
-        launch_adj_inject(ad.lamE[P.comp], P.nodes, P.npts, ad.dl + n * P.npts, st);
+        launch_adj_inject(ad.lamE[P.comp], P.nodes, P.npts, ad.dl + n * P.npts, as);
         c->launches++;
       }
       // E update with Mur faces, transposed (H is clear: zeroed before the
       // first reverse step, then by the previous step's B transpose)
-      launch_adj_e(g, ad.lamE, ad.H, ad.lamB, ad.lamJ, st);
+      launch_adj_e(g, ad.lamE, ad.H, ad.lamB, ad.lamJ, as);
       for (int k = 0; k < 3; ++k) std::swap(ad.lamE[k], ad.H[k]);
       // B^{n+1/2} = B^n - dt/2 curl E^n; clears H (the old E adjoint) for the next step
-      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, ad.H, st);
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, ad.H, as);
       // particles, with E^n, B^n and the particle state stored for step n
       const float *En[3], *Bn[3], *lJ[3] = {ad.lamJ[0], ad.lamJ[1], ad.lamJ[2]};
+      const float *sf = ad.st_fields[bank * K + j];
       for (int k = 0; k < 3; ++k) {
-        En[k] = ad.st_fields[j] + (size_t)k * g.ncell;
-        Bn[k] = ad.st_fields[j] + (size_t)(3 + k) * g.ncell;
+        En[k] = sf + (size_t)k * g.ncell;
+        Bn[k] = sf + (size_t)(3 + k) * g.ncell;
       }
       std::vector<PartP> pp;
-      for (size_t q = 0; q < c->sp.size(); ++q) pp.push_back(ad.st_parts[j][q].p);
+      for (size_t q = 0; q < c->sp.size(); ++q) pp.push_back(ad.st_parts[bank * K + j][q].p);
       launch_adj_push(g, (int)c->sp.size(), sps.data(), pp.data(), xbs.data(), acbs.data(), ebs.data(), caps.data(), En,
-                      Bn, lJ, ad.box, ad.occ, ad.emax, ad.lamE, ad.lamB, st);
+                      Bn, lJ, ad.box, ad.occ, ad.emax, ad.lamE, ad.lamB, ad.status, as);
       // B^n = B^{n-1/2} - dt/2 curl E^n
-      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, nullptr, st);
+      launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, nullptr, as);
       // E transpose and its Mur passes (one per pass and open axis), two B
       // transposes, particle adjoint, scatter, box sum
       int nopen = 0;
@@ -1565,6 +1615,27 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
       int rc = check_launch(c, "backward step");
       if (rc) return rc;
     }
+    cudaEventRecord(ad.rev_done[bank], as);
+    return BP_OK;
+  };
+  {
+    int rc = recompute(ad.nseg - 1);
+    for (int seg = ad.nseg - 1; !rc && seg >= 0; --seg) {
+      if (seg >= 1) rc = recompute(seg - 1);
+      if (!rc) rc = reverse(seg);
+    }
+    if (rc) {
+      cudaStreamSynchronize(as);
+      return rc;
+    }
+    // the reductions below read the adjoint stream's results
+    cudaStreamWaitEvent(st, ad.rev_done[0], 0);
+    int ast = 0;
+    cudaError_t e = cudaMemcpyAsync(&ast, ad.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "backward");
+    if (ast & ST_DOMAIN)
+      return fail(c, BP_ERR_DOMAIN, "bp_backward: a bound electron a cell or more from its nucleus (not followed by the reverse pass)");
   }
   // FP64 reductions in a fixed order: parameters and groups (CSR over load order)
   Species &S = c->sp[sid];

@@ -29,8 +29,15 @@ struct bp_adjoint {
   std::vector<float *> ck_fields;                   // [nseg] E, B (6 ncell)
   int *ck_status = nullptr;                         // [nseg][4] device status words
   std::vector<std::vector<bp_part_copy>> ck_parts;  // [nseg][species]
-  std::vector<float *> st_fields;                   // [K] E^n, B^n
-  std::vector<std::vector<bp_part_copy>> st_parts;  // [K][species]
+  // per-step stores of a recomputed segment, two banks of K steps ([bank * K
+  // + j]): the reverse steps of one segment read one bank while the next
+  // (earlier) segment is recomputed into the other
+  std::vector<float *> st_fields;                   // [2 K] E^n, B^n
+  std::vector<std::vector<bp_part_copy>> st_parts;  // [2 K][species]
+  cudaStream_t stream = nullptr;                    // the reverse steps' stream
+  int *status = nullptr;                            // the reverse pass's status word
+  cudaEvent_t rec_done[2] = {nullptr, nullptr};     // bank b recomputed
+  cudaEvent_t rev_done[2] = {nullptr, nullptr};     // bank b's reverse steps done
   float *lamE[3] = {}, *lamB[3] = {}, *lamJ[3] = {}, *H[3] = {};
   float *box = nullptr;
   unsigned char *occ = nullptr;
@@ -63,6 +70,9 @@ struct bp_ctx {
   double *ant = nullptr;             // sorted deposit: antenna sheet values of a step, [laser][ncell / n0]
   void *grec = nullptr;              // sorted deposit: general-case deposit records of a step
   int *grec_n = nullptr;             // their count (device, cleared after each step)
+  int4 *far = nullptr;               // sorted deposit: ions with a far bound electron, moved after the push
+  int *far_n = nullptr;              // their count (device, cleared after each step)
+  long long far_cap = 0;
   long long grec_cap = 0;
   long long grec_fixed = 0;          // capacity set by the caller (0: default)
   unsigned char *occ = nullptr;

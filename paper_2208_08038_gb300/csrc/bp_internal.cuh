@@ -137,6 +137,9 @@ struct PushArgs {
   int *status;
   float jscale, jinv;      // fixed-point scale (sorted deposit), power of two
   unsigned long long *work; // [2] ions given the full push, ions moved by the quiet-tile pass (cumulative)
+  int4 *far;                // sorted deposit: two-body ions whose bound electron is a cell or more away,
+  int *far_n;               //   (species, particle, tile), moved after the push by k_push_far; their count
+  int far_cap;
   int push_blocks;          // persistent push blocks for this grid on this device
   int sms;                  // multiprocessors of the device
 };
@@ -426,6 +429,6 @@ int adj_prepare(int D);
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
                      float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
                      const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
-                     float *lamB[3], cudaStream_t s);
+                     float *lamB[3], int *status, cudaStream_t s);
 void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
                     const double *acb, const double *scale, double *out, cudaStream_t s);

@@ -547,6 +547,7 @@ struct AdjState {
   double *acb;    // [cap] adjoint of a_c, accumulated over steps
   float *eb;      // [12][cap] by slot: adjoints of the gathered E1 B1 E2 B2 (this step)
   long long cap;
+  int *status;    // the reverse pass's status word (ST_DOMAIN)
 };
 
 struct AdjArgs {
@@ -596,7 +597,14 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
     d2[a] = d[a] + di;
     f2[a] = fr;
   }
-  if (bad) return;  // the forward push skipped it too (domain error)
+  if (bad) {
+    // a body outside the tile's reach: the forward push either skipped it
+    // (a domain error) or, for a bound electron a cell or more from its
+    // nucleus, moved it on the global grid, which this reverse step does not
+    // follow: reported, never skipped silently
+    atomicOr(S.status, ST_DOMAIN);
+    return;
+  }
   // forward recompute
   float E1[3], B1[3], E2[3], B2[3];
   {
@@ -1127,7 +1135,7 @@ void adj_launch_all(const GridP &g, const AdjArgs &A, const ScatArgs &S, float *
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
                      float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
                      const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
-                     float *lamB[3], cudaStream_t s) {
+                     float *lamB[3], int *status, cudaStream_t s) {
   AdjArgs A;
   memset(&A, 0, sizeof A);
   ScatArgs S;
@@ -1140,6 +1148,7 @@ void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, f
     A.st[k].acb = acb[k];
     A.st[k].eb = eb[k];
     A.st[k].cap = cap[k];
+    A.st[k].status = status;
     S.eb[k] = eb[k];
     S.ecap[k] = cap[k];
   }

@@ -3,8 +3,9 @@
 // first-order Mur open faces, the laser antenna, the current (sorted deposit:
 // formed in the E update from the 64-bit fixed-point accumulator; atomic
 // deposit: the fixed-order sum of the per-tile boxes), the tile marks of
-// non-zero fields, and probes.  All FP32, memory bound: one thread per cell,
-// coalesced along x.
+// non-zero fields, and probes.  All FP32, memory bound: the Yee updates take
+// four consecutive x cells per thread (16-byte vector loads and stores,
+// coalesced along x); the other kernels one cell per thread.
 #include "bp_internal.cuh"
 
 namespace {
@@ -33,37 +34,126 @@ __device__ __forceinline__ int nbound(const GridP &g, int pat, const int c[3], i
 // stagger pattern of E_x, E_y, E_z (bit a: half cell along axis a)
 __device__ __forceinline__ int pat_e(int comp) { return 1 << comp; }
 
+// Four consecutive x cells per thread (rows hold a multiple of 8 cells, so a
+// group never straddles a row or a tile): float4 loads and stores of each
+// component, index arithmetic once per thread.
+struct Cell4 {
+  long long q;      // linear index of the group's first cell
+  int c[3];         // its coordinates
+  long long up[3];  // offset to the +1 neighbour along y, z (and x for the group's last cell)
+  long long dn[3];  // offset to the -1 neighbour along y, z (and x for the group's first cell)
+};
+
+template <int D>
+__device__ __forceinline__ bool row_cell4(const GridP &g, Cell4 &C) {
+  const int n0 = g.n[0], n4 = n0 >> 2;
+  const int chunks = (n4 + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int row = (int)blockIdx.x / chunks;
+  const int x4 = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
+  if (x4 >= n4) return false;
+  C.c[0] = 4 * x4;
+  C.c[1] = D >= 2 ? row % g.n[1] : 0;
+  C.c[2] = D >= 3 ? row / g.n[1] : 0;
+  C.q = (long long)row * n0 + C.c[0];
+  // along x: the neighbour after the last cell and before the first one
+  C.up[0] = C.c[0] + 4 < n0 ? 4 : 4 - n0;
+  C.dn[0] = C.c[0] > 0 ? -1 : n0 - 1;
+  long long stride = n0;
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    const int n = g.n[a];
+    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
+    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
+    stride *= n;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float el(const float4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void set_el(float4 &v, int i, float x) {
+  if (i == 0) v.x = x;
+  else if (i == 1) v.y = x;
+  else if (i == 2) v.z = x;
+  else v.w = x;
+}
+
+// whether cell x of the group is an exterior position (open axis, half
+// stagger, last cell) or a Mur node (open axis, node stagger, first or last
+// cell) of a component with stagger pattern pat
+template <int D>
+__device__ __forceinline__ bool skip_cell(const GridP &g, int pat, const int c[3], int i, bool mur) {
+  int ci[3] = {c[0] + i, c[1], c[2]};
+  return exterior_c<D>(g, pat, ci) || (mur && mur_node<D>(g, pat, ci));
+}
+
+// the tile mark of a group of four cells (see mark_nonzero): the lowest lane
+// of each tile segment (L0 / 4 lanes) that holds a non-zero value writes it
+template <int D>
+__device__ __forceinline__ void mark_nonzero4(const GridP &g, const int c[3], bool nz) {
+  const unsigned m = __ballot_sync(__activemask(), nz);
+  if (!nz) return;
+  constexpr int LANES = Geo<D>::L0 / 4;
+  static_assert(LANES >= 1 && LANES <= 32 && (LANES & (LANES - 1)) == 0, "a tile segment lies inside one warp");
+  const int lane = (int)(threadIdx.x & 31u);
+  const int base = lane & ~(LANES - 1);
+  if (m & ((1u << lane) - 1u) & ~((1u << base) - 1u)) return;
+  unsigned char *f = g.fnz + tile_of(g, c);
+  if (*f == 0) *f = 1;
+}
+
 // B <- B - h curl E (forward differences to the B locations)
 template <int D>
 __global__ void __launch_bounds__(128) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
                                                const float *__restrict__ Ey, const float *__restrict__ Ez, float h) {
-  Cell C;
-  if (!row_cell<D>(g, C)) return;
+  Cell4 C;
+  if (!row_cell4<D>(g, C)) return;
   const long long q = C.q;
+  const float4 ex = ld4(Ex + q), ey = ld4(Ey + q), ez = ld4(Ez + q);
+  const float eyn = Ey[q + C.up[0]], ezn = Ez[q + C.up[0]];  // x neighbours of the last cell
+  float4 ezy = ez, exy = ex, eyz = ey, exz = ex;
+  if (D >= 2) {
+    ezy = ld4(Ez + q + C.up[1]);
+    exy = ld4(Ex + q + C.up[1]);
+  }
+  if (D >= 3) {
+    eyz = ld4(Ey + q + C.up[2]);
+    exz = ld4(Ex + q + C.up[2]);
+  }
+  float4 bx = ld4(Bx + q), by = ld4(By + q), bz = ld4(Bz + q);
   bool nz = false;
-  if (!exterior_c<D>(g, 6, C.c)) {
-    float d = 0.0f;
-    if (D >= 2) d += (Ez[q + C.up[1]] - Ez[q]) * g.idx[1];
-    if (D >= 3) d -= (Ey[q + C.up[2]] - Ey[q]) * g.idx[2];
-    const float v = Bx[q] - h * d;
-    Bx[q] = v;
-    nz |= v != 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float ezi = el(ez, i), eyi = el(ey, i), exi = el(ex, i);
+    const float ezx = i < 3 ? el(ez, i + 1) : ezn, eyx = i < 3 ? el(ey, i + 1) : eyn;
+    if (!skip_cell<D>(g, 6, C.c, i, false)) {
+      float d = 0.0f;
+      if (D >= 2) d += (el(ezy, i) - ezi) * g.idx[1];
+      if (D >= 3) d -= (el(eyz, i) - eyi) * g.idx[2];
+      const float v = el(bx, i) - h * d;
+      set_el(bx, i, v);
+      nz |= v != 0.0f;
+    }
+    if (!skip_cell<D>(g, 5, C.c, i, false)) {
+      float d = -(ezx - ezi) * g.idx[0];
+      if (D >= 3) d += (el(exz, i) - exi) * g.idx[2];
+      const float v = el(by, i) - h * d;
+      set_el(by, i, v);
+      nz |= v != 0.0f;
+    }
+    if (!skip_cell<D>(g, 3, C.c, i, false)) {
+      float d = (eyx - eyi) * g.idx[0];
+      if (D >= 2) d -= (el(exy, i) - exi) * g.idx[1];
+      const float v = el(bz, i) - h * d;
+      set_el(bz, i, v);
+      nz |= v != 0.0f;
+    }
   }
-  if (!exterior_c<D>(g, 5, C.c)) {
-    float d = -(Ez[q + C.up[0]] - Ez[q]) * g.idx[0];
-    if (D >= 3) d += (Ex[q + C.up[2]] - Ex[q]) * g.idx[2];
-    const float v = By[q] - h * d;
-    By[q] = v;
-    nz |= v != 0.0f;
-  }
-  if (!exterior_c<D>(g, 3, C.c)) {
-    float d = (Ey[q + C.up[0]] - Ey[q]) * g.idx[0];
-    if (D >= 2) d -= (Ex[q + C.up[1]] - Ex[q]) * g.idx[1];
-    const float v = Bz[q] - h * d;
-    Bz[q] = v;
-    nz |= v != 0.0f;
-  }
-  mark_nonzero<D>(g, C.c, nz);
+  st4(Bx + q, bx);
+  st4(By + q, by);
+  st4(Bz + q, bz);
+  mark_nonzero4<D>(g, C.c, nz);
 }
 
 __device__ double laser_value(const LaserP &L, double t, double y, double z) {
@@ -154,61 +244,97 @@ __global__ void __launch_bounds__(128) k_yee_e(GridP g, float *Ex, float *Ey, fl
                                                const float *__restrict__ By, const float *__restrict__ Bz, float *Jx,
                                                float *Jy, float *Jz, unsigned long long *jfx, float jinv,
                                                AntSet as, const double *__restrict__ ant) {
-  Cell C;
-  if (!row_cell<D>(g, C)) return;
+  Cell4 C;
+  if (!row_cell4<D>(g, C)) return;
   const long long q = C.q;
-  float jx, jy, jz;
+  float4 jx, jy, jz;
   if constexpr (FX) {
     const long long nc = g.ncell;
-    const long long fx = (long long)jfx[q], fy = (long long)jfx[nc + q], fz = (long long)jfx[2 * nc + q];
-    jx = fx_to_float(fx, jinv);
-    if (as.n > 0 && C.c[0] >= as.lo && C.c[0] <= as.hi) {
-      double ay = 0.0, az = 0.0;
-      const long long yz = q / g.n[0], nyz = g.ncell / g.n[0];
+    const ulonglong2 *px = reinterpret_cast<const ulonglong2 *>(jfx + q);
+    const ulonglong2 *py = reinterpret_cast<const ulonglong2 *>(jfx + nc + q);
+    const ulonglong2 *pz = reinterpret_cast<const ulonglong2 *>(jfx + 2 * nc + q);
+    const ulonglong2 x0 = px[0], x1 = px[1], y0 = py[0], y1 = py[1], z0 = pz[0], z1 = pz[1];
+    const long long fx[4] = {(long long)x0.x, (long long)x0.y, (long long)x1.x, (long long)x1.y};
+    const long long fy[4] = {(long long)y0.x, (long long)y0.y, (long long)y1.x, (long long)y1.y};
+    const long long fz[4] = {(long long)z0.x, (long long)z0.y, (long long)z1.x, (long long)z1.y};
 #pragma unroll
-      for (int k = 0; k < BP_MAX_LASER; ++k) {
-        if (k >= as.n || C.c[0] != as.ia[k]) continue;
-        if (as.comp[k] == 1) ay += ant[k * nyz + yz];
-        else az += ant[k * nyz + yz];
-      }
-      jy = (float)((double)fy * (double)jinv + ay);
-      jz = (float)((double)fz * (double)jinv + az);
-    } else {
-      jy = fx_to_float(fy, jinv);
-      jz = fx_to_float(fz, jinv);
+    for (int i = 0; i < 4; ++i) {
+      set_el(jx, i, fx_to_float(fx[i], jinv));
+      set_el(jy, i, fx_to_float(fy[i], jinv));
+      set_el(jz, i, fx_to_float(fz[i], jinv));
     }
-    Jx[q] = jx;
-    Jy[q] = jy;
-    Jz[q] = jz;
+    if (as.n > 0 && C.c[0] + 3 >= as.lo && C.c[0] <= as.hi) {
+      // an antenna plane in the group: its sheet current added in FP64
+      // before the one rounding
+      const long long yz = q / g.n[0], nyz = g.ncell / g.n[0];
+      for (int i = 0; i < 4; ++i) {
+        double ay = 0.0, az = 0.0;
+        bool on = false;
+#pragma unroll
+        for (int k = 0; k < BP_MAX_LASER; ++k) {
+          if (k >= as.n || C.c[0] + i != as.ia[k]) continue;
+          on = true;
+          if (as.comp[k] == 1) ay += ant[k * nyz + yz];
+          else az += ant[k * nyz + yz];
+        }
+        if (on) {
+          set_el(jy, i, (float)((double)fy[i] * (double)jinv + ay));
+          set_el(jz, i, (float)((double)fz[i] * (double)jinv + az));
+        }
+      }
+    }
+    st4(Jx + q, jx);
+    st4(Jy + q, jy);
+    st4(Jz + q, jz);
   } else {
-    jx = Jx[q];
-    jy = Jy[q];
-    jz = Jz[q];
+    jx = ld4(Jx + q);
+    jy = ld4(Jy + q);
+    jz = ld4(Jz + q);
   }
+  const float4 bx = ld4(Bx + q), by = ld4(By + q), bz = ld4(Bz + q);
+  const float byp = By[q + C.dn[0]], bzp = Bz[q + C.dn[0]];  // x neighbours of the first cell
+  float4 bzy = bz, bxy = bx, byz = by, bxz = bx;
+  if (D >= 2) {
+    bzy = ld4(Bz + q + C.dn[1]);
+    bxy = ld4(Bx + q + C.dn[1]);
+  }
+  if (D >= 3) {
+    byz = ld4(By + q + C.dn[2]);
+    bxz = ld4(Bx + q + C.dn[2]);
+  }
+  float4 ex = ld4(Ex + q), ey = ld4(Ey + q), ez = ld4(Ez + q);
   bool nz = false;
-  if (!exterior_c<D>(g, 1, C.c) && !mur_node<D>(g, 1, C.c)) {
-    float d = 0.0f;
-    if (D >= 2) d += (Bz[q] - Bz[q + C.dn[1]]) * g.idx[1];
-    if (D >= 3) d -= (By[q] - By[q + C.dn[2]]) * g.idx[2];
-    const float v = Ex[q] + g.dt * (d - jx);
-    Ex[q] = v;
-    nz |= v != 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float bxi = el(bx, i), byi = el(by, i), bzi = el(bz, i);
+    const float byx = i > 0 ? el(by, i - 1) : byp, bzx = i > 0 ? el(bz, i - 1) : bzp;
+    if (!skip_cell<D>(g, 1, C.c, i, true)) {
+      float d = 0.0f;
+      if (D >= 2) d += (bzi - el(bzy, i)) * g.idx[1];
+      if (D >= 3) d -= (byi - el(byz, i)) * g.idx[2];
+      const float v = el(ex, i) + g.dt * (d - el(jx, i));
+      set_el(ex, i, v);
+      nz |= v != 0.0f;
+    }
+    if (!skip_cell<D>(g, 2, C.c, i, true)) {
+      float d = -(bzi - bzx) * g.idx[0];
+      if (D >= 3) d += (bxi - el(bxz, i)) * g.idx[2];
+      const float v = el(ey, i) + g.dt * (d - el(jy, i));
+      set_el(ey, i, v);
+      nz |= v != 0.0f;
+    }
+    if (!skip_cell<D>(g, 4, C.c, i, true)) {
+      float d = (byi - byx) * g.idx[0];
+      if (D >= 2) d -= (bxi - el(bxy, i)) * g.idx[1];
+      const float v = el(ez, i) + g.dt * (d - el(jz, i));
+      set_el(ez, i, v);
+      nz |= v != 0.0f;
+    }
   }
-  if (!exterior_c<D>(g, 2, C.c) && !mur_node<D>(g, 2, C.c)) {
-    float d = -(Bz[q] - Bz[q + C.dn[0]]) * g.idx[0];
-    if (D >= 3) d += (Bx[q] - Bx[q + C.dn[2]]) * g.idx[2];
-    const float v = Ey[q] + g.dt * (d - jy);
-    Ey[q] = v;
-    nz |= v != 0.0f;
-  }
-  if (!exterior_c<D>(g, 4, C.c) && !mur_node<D>(g, 4, C.c)) {
-    float d = (By[q] - By[q + C.dn[0]]) * g.idx[0];
-    if (D >= 2) d -= (Bx[q] - Bx[q + C.dn[1]]) * g.idx[1];
-    const float v = Ez[q] + g.dt * (d - jz);
-    Ez[q] = v;
-    nz |= v != 0.0f;
-  }
-  mark_nonzero<D>(g, C.c, nz);
+  st4(Ex + q, ex);
+  st4(Ey + q, ey);
+  st4(Ez + q, ez);
+  mark_nonzero4<D>(g, C.c, nz);
 }
 
 // the marks of the fields as they are (after a write from outside the step):
@@ -460,6 +586,12 @@ __global__ void k_probe(const float *F, const long long *nodes, long long npts, 
     buf[q] = F[nodes[q]];
 }
 
+// blocks of a four-cells-per-thread row launch (rows of n0 / 4 threads)
+int row_blocks4(const GridP &g, int bs) {
+  const long long rows = g.ncell / g.n[0];
+  return (int)(rows * ((g.n[0] / 4 + bs - 1) / bs));
+}
+
 int grid_blocks(long long n, int bs) {
   long long b = (n + bs - 1) / bs;
   long long cap = 152LL * 16;
@@ -476,7 +608,7 @@ long long frame_floats(const GridP &g) {
 }
 
 void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s) {
-  const int nb = row_blocks(g, 128);
+  const int nb = row_blocks4(g, 128);
   if (g.D == 1) k_yee_b<1><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
   else if (g.D == 2) k_yee_b<2><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
   else k_yee_b<3><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
@@ -487,7 +619,7 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
                   cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
-  const int nb = row_blocks(g, 128);
+  const int nb = row_blocks4(g, 128);
   AntSet as;
   as.n = jfx ? nlas : 0;
   as.lo = 1 << 30;

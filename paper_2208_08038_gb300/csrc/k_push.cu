@@ -398,6 +398,112 @@ __device__ __noinline__ void deposit_in_place(JT *Jsm, const QIn &in, float scal
     }
 }
 
+// one row of a record added to the global fixed-point current (sorted
+// mode): each contribution rounded to the fixed-point unit as the
+// shared-memory path rounds it; grid coordinates = the record's origin + box
+// coordinates (periodic axes wrapped, nodes beyond an open face dropped, as
+// the push drops them)
+template <int D>
+__device__ __forceinline__ void record_row_global(const GridP &g, const QRec &R, int b, int c, int row,
+                                                  unsigned long long *jfx, float scale) {
+  record_row<D>(R, b, c, row, [&](int cc, int x, int y, int z, float v) {
+    const float vs = v * scale;
+    if (fabsf(vs) <= 0.5f) return;  // rounds to zero
+    const int bx[3] = {x, y, z};
+    long long gidx = 0, stride = 1;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int cg = R.org[a] + bx[a];
+      if (a < D) {
+        if (g.bc[a] == BP_PERIODIC) cg = wrap_once(cg, g.n[a]);
+        else ok &= (cg >= 0 && cg < g.n[a]);
+      }
+      gidx += (long long)cg * stride;
+      stride *= g.n[a];
+    }
+    if (ok) atomicAdd(jfx + (size_t)cc * g.ncell + gidx, (unsigned long long)f2ll_rn(vs));
+  });
+}
+
+// a one-body deposit with its own grid origin org (a bound electron pulled
+// a cell or more from its nucleus, outside the tile's current box): queued as
+// a record for k_records, or, when the record buffer is full, added to the
+// global current here
+template <int D>
+__device__ __noinline__ void deposit_far(const GridP &g, const QIn &in, const int org[3], QRec *qrec, int *qn,
+                                         int qmax, unsigned long long *jfx, float scale) {
+  const int slot = atomicAdd(qn, 1);
+  if (slot < qmax) {
+    queue_record<D>(qrec[slot], in);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) qrec[slot].org[a] = org[a];
+    return;
+  }
+  QRec R;
+  queue_record<D>(R, in);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) R.org[a] = org[a];
+  constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
+  for (int it = 0; it < IPB; ++it) {
+    const int c = it < NR0 ? 0 : (it < NR0 + NR1 ? 1 : 2);
+    const int row = it - (c == 0 ? 0 : (c == 1 ? NR0 : NR0 + NR1));
+    record_row_global<D>(g, R, 0, c, row, jfx, scale);
+  }
+}
+
+// E and B of one body read from the global fields (a body outside the
+// tile's staged box): the staggered quadratic gather over the body's cell c
+// and offset f, periodic axes wrapped, zero beyond open faces
+template <int D>
+__device__ __noinline__ void gather_global(const GridP &g, const float *const *Eg, const float *const *Bg,
+                                           const int c[3], const float f[3], float E[3], float B[3]) {
+#pragma unroll 1
+  for (int cc = 0; cc < 6; ++cc) {
+    // stagger pattern of component cc: bit a set when it sits half a cell along a
+    const int pat = cc < 3 ? (1 << cc) : (7 & ~(1 << (cc - 3)));
+    const float *F = cc < 3 ? Eg[cc] : Bg[cc - 3];
+    int base[3];
+    float w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < D) {
+        const bool half = (pat >> a) & 1;
+        const int up = half ? 0 : (f[a] >= 0.5f ? 1 : 0);
+        base[a] = c[a] + up - 1;
+        qweights(half ? f[a] - 0.5f : f[a] - (float)up, w[a]);
+      } else {
+        base[a] = 0;
+        w[a][0] = 1.0f;
+        w[a][1] = w[a][2] = 0.0f;
+      }
+    }
+    float acc = 0.0f;
+    for (int k = 0; k < (D >= 3 ? 3 : 1); ++k)
+      for (int j = 0; j < (D >= 2 ? 3 : 1); ++j)
+        for (int i = 0; i < 3; ++i) {
+          const int n[3] = {base[0] + i, base[1] + j, base[2] + k};
+          long long gi = 0, stride = 1;
+          bool ok = true;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            int x = n[a];
+            if (a < D) {
+              if (g.bc[a] == BP_PERIODIC) x = wrap_once(x, g.n[a]);
+              else ok &= (x >= 0 && x < g.n[a]);
+            } else {
+              x = 0;
+            }
+            gi += (long long)x * stride;
+            stride *= g.n[a];
+          }
+          if (ok) acc = fmaf(w[0][i] * w[1][j] * w[2][k], F[gi], acc);
+        }
+    if (cc < 3) E[cc] = acc;
+    else B[cc - 3] = acc;
+  }
+}
+
 // node bounding box of a thread's deposits, one byte per axis (box
 // coordinates are below 256); axes the grid does not simulate stay at 0
 template <int D>
@@ -552,10 +658,133 @@ __device__ __forceinline__ bool quiet_done(const PartP &P, long long i) {
   return quiet_state(r, u1, u2);
 }
 
+// The whole step of a two-body ion whose bound electron is a cell or more
+// from its nucleus (a strong field pulls it into the Coulomb tail of the
+// modified potential), sorted mode: outside the tile's boxes, so both bodies
+// gather from the global E and B and deposit as one-body records at their own
+// grid origins (k_records adds them to the fixed-point current; directly
+// when the record buffer is full).  The same arithmetic as push_particle's.
+// Out of line and self-contained (it reloads the particle), so the common
+// path carries none of it.  Returns false when the ion cannot be moved this
+// way (body 1 outside its tile's margin, body 2 beyond an open face or a
+// displacement that is not finite): a domain error for the caller.
+template <int D>
+__device__ __noinline__ bool push_far(const GridP &g, const SpecP &sp, const PartP &P, long long i, int t0x, int t0y,
+                                      int t0z, int *status, QRec *qrec, int *qn, int qmax, const float *const *Eg,
+                                      const float *const *Bg, unsigned long long *jfx, float scale) {
+  const long long cap = P.cap;
+  const int T0[3] = {t0x, t0y, t0z};
+  int c[3];
+  unpack_cell(g, P.cell[i], c);
+  float f[3] = {0.0f, 0.0f, 0.0f}, r[3], u1[3], u2[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) f[a] = P.off[a * cap + i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[a] = P.r[a * cap + i];
+    u1[a] = P.u1[a * cap + i];
+    u2[a] = P.u2[a * cap + i];
+  }
+  int c2[3] = {0, 0, 0};
+  float f2[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (outside_margin<D>(a, rel_cell<D>(g, a, c[a], T0[a]))) return false;
+    const float rc = r[a] * g.idx[a];
+    if (!(fabsf(rc) < (float)g.n[a])) return false;
+    const float X = f[a] - rc;
+    const float fl = floorf(X);
+    float fr = X - fl;
+    int di = (int)fl;
+    if (fr >= 1.0f) { fr = 0.0f; di += 1; }
+    c2[a] = c[a] + di;
+    if (g.bc[a] == BP_PERIODIC) c2[a] = wrap_mod(c2[a], g.n[a]);
+    else if (c2[a] < 0 || c2[a] >= g.n[a]) return false;
+    f2[a] = fr;
+  }
+  float E1[3], B1[3], E2[3], B2[3];
+  gather_global<D>(g, Eg, Bg, c, f, E1, B1);
+  gather_global<D>(g, Eg, Bg, c2, f2, E2, B2);
+  const int pi = P.pidx ? P.pidx[i] : 0;
+  const float ac = sp.ac[pi];
+  const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + ac * ac;
+  const float rs = rsqrtf(rr);
+  const float s = sp.kappa * rs * rs * rs;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    E1[a] = fmaf(sp.q2 * s, r[a], E1[a]);
+    E2[a] = fmaf(-sp.q1 * s, r[a], E2[a]);
+  }
+  boris(sp.h2, E2, B2, u2);
+  boris(sp.h1, E1, B1, u1);
+  float v1[3], v2[3];
+  const float g1 = inv_gamma(u1), g2 = inv_gamma(u2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v1[a] = u1[a] * g1;
+    v2[a] = u2[a] * g2;
+  }
+  float fn[3] = {0.0f, 0.0f, 0.0f}, de1[3] = {0.0f, 0.0f, 0.0f}, de2[3] = {0.0f, 0.0f, 0.0f}, rn[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    fn[a] = drift_offset(g, a, f[a], v1[a]);
+    de1[a] = fn[a] - f[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    rn[a] = r[a] + g.dt * (v1[a] - v2[a]);
+    if (a < D) de2[a] = de1[a] - (rn[a] - r[a]) * g.idx[a];
+  }
+  // each body a one-body record at its own grid origin (cell - OJ)
+  QIn in;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    in.f[a] = f[a]; in.de1[a] = de1[a]; in.v1[a] = v1[a]; in.dxdt[a] = g.dx[a] / g.dt; in.d[a] = 0;
+    in.f2[a] = in.de2[a] = in.v2[a] = 0.0f;
+    in.d2[a] = 0;
+  }
+  in.qw1 = sp.qw1;
+  in.qw2 = 0.0f;
+  in.two = 0;
+  int org[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) org[a] = a < D ? c[a] - Box<D>::OJ : 0;
+  deposit_far<D>(g, in, org, qrec, qn, qmax, jfx, scale);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    in.f[a] = f2[a]; in.de1[a] = de2[a]; in.v1[a] = v2[a];
+    org[a] = a < D ? c2[a] - Box<D>::OJ : 0;
+  }
+  in.qw1 = sp.qw2;
+  deposit_far<D>(g, in, org, qrec, qn, qmax, jfx, scale);
+  bool bad = false, removed = false, need_sort = false, nonfinite = false;
+  advance_cell<D>(g, T0, true, c, fn, bad, removed, need_sort);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nonfinite |= !isfinite(u1[a]) || !isfinite(u2[a]);
+  if (bad) atomicOr(status, ST_DOMAIN);
+  if (nonfinite) atomicOr(status, ST_NONFINITE);
+  if (bad) {
+    P.cell[i] = -1;
+    return true;
+  }
+  if (need_sort) atomicOr(status, ST_NEED_SORT);
+  P.cell[i] = pack_cell(g, c[0], c[1], c[2]);
+#pragma unroll
+  for (int a = 0; a < D; ++a) P.off[a * cap + i] = fn[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P.u1[a * cap + i] = u1[a];
+    P.r[a * cap + i] = rn[a];
+    P.u2[a * cap + i] = u2[a];
+  }
+  return true;
+}
+
 template <int D, bool DET, typename JT>
 __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, long long i, const int T0[3],
                               const float *Gsm, JT *Jsm, int *status, float scale, QRec *qrec, int *qn, int qmax,
-                              unsigned &blo, unsigned &bhi, bool nofield) {
+                              unsigned &blo, unsigned &bhi, bool nofield, int4 *far, int *far_n, int far_cap, int s,
+                              int t) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   int cell = P.cell[i];
@@ -593,6 +822,16 @@ __device__ void push_particle(const GridP &g, const SpecP &sp, const PartP &P, l
     f2[a] = fr;
   }
   if (bad) {
+    // sorted mode: perhaps a bound electron a cell or more from its nucleus,
+    // which k_push_far moves on the global grid after this kernel (it
+    // reports a domain error for anything else); atomic mode: a domain error
+    if (DET && two) {
+      const int k = atomicAdd(far_n, 1);
+      if (k < far_cap) {
+        far[k] = make_int4(s, (int)i, t, 0);
+        return;
+      }
+    }
     atomicOr(status, ST_DOMAIN);
     return;
   }
@@ -831,7 +1070,19 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
     }
     if (use) marked = g.fnz[nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2])] != 0;
   }
-  if (__syncthreads_or(marked)) {
+  // a tile without particles has nothing to push or deposit, whatever its
+  // fields: done here, so the push neither stages its fields nor visits it
+  bool occupied = false;
+  if (tid < A.nsp) occupied = A.p[tid].tstart[t + 1] > A.p[tid].tstart[t];
+  const bool any_marked = __syncthreads_or(marked);
+  if (!__syncthreads_or(occupied)) {
+    if (tid == 0) {
+      A.qstate[t] = QS_DONE;
+      A.occ[t] = 0;
+    }
+    return;
+  }
+  if (any_marked) {
     if (tid == 0) {
       A.qstate[t] = QS_PUSH;
       A.tile_list[atomicAdd(A.tile_n, 1)] = t;
@@ -1065,7 +1316,7 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
       if (moved && quiet_done(A.p[s], i)) continue;
       if (i + bs < end) prefetch_particle<D>(A.p[s], i + bs, A.sp[s].kind == BP_TWO_BODY);
       push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec,
-                                DET ? qcount : &qn, qmax, blo, bhi, nofield);
+                                DET ? qcount : &qn, qmax, blo, bhi, nofield, A.far, A.far_n, A.far_cap, s, t);
       ++pushed;
     }
     __syncthreads();
@@ -1157,19 +1408,20 @@ __global__ void __launch_bounds__(push_threads(D)) k_push(GridP g, PushArgs A, c
   unsigned phase = 0;
   bool failed = false;
   const int nlist = *A.tile_n;
-  // Thread 0 reserves the block's next list entry when the block starts a
-  // tile (the atomic's latency then overlaps the tile's particles) and
-  // publishes it once the field box may be overwritten.
-  int reserved = 0;
+  // The next list entry is taken only once the block has finished the
+  // current tile's particles: reserving it earlier would let one block hold
+  // two costly tiles in a row while others have none (grids with few
+  // occupied tiles ran 20% slower that way).
   auto grab = [&]() {
-    if (threadIdx.x == 0) next = reserved < nlist ? A.tile_list[reserved] : -1;
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(A.tile_ctr, 1);
+      next = k < nlist ? A.tile_list[k] : -1;
+    }
     __syncthreads();
     if (next >= 0) stage_issue<D>(g, A, T, next, Gsm, &bar);
   };
-  if (threadIdx.x == 0) reserved = atomicAdd(A.tile_ctr, 1);
   grab();
   for (int t = next; t >= 0; t = next) {
-    if (threadIdx.x == 0) reserved = atomicAdd(A.tile_ctr, 1);
     push_tile<D, DET>(g, A, T, t, &bar, phase, failed, grab);
     if (failed) give_up = 1;
     __syncthreads();  // every thread has read `next` before it changes
@@ -1194,24 +1446,24 @@ __global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict
     if (b >= R.nb) continue;
     const int c = it < NR0 ? 0 : (it < NR0 + NR1 ? 1 : 2);
     const int row = it - (c == 0 ? 0 : (c == 1 ? NR0 : NR0 + NR1));
-    record_row<D>(R, b, c, row, [&](int cc, int x, int y, int z, float v) {
-      const float vs = v * scale;
-      if (fabsf(vs) <= 0.5f) return;  // rounds to zero
-      const int bx[3] = {x, y, z};
-      long long gidx = 0, stride = 1;
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int cg = R.org[a] + bx[a];
-        if (a < D) {
-          if (g.bc[a] == BP_PERIODIC) cg = wrap_once(cg, g.n[a]);
-          else ok &= (cg >= 0 && cg < g.n[a]);
-        }
-        gidx += (long long)cg * stride;
-        stride *= g.n[a];
-      }
-      if (ok) atomicAdd(jfx + (size_t)cc * g.ncell + gidx, (unsigned long long)f2ll_rn(vs));
-    });
+    record_row_global<D>(g, R, b, c, row, jfx, scale);
+  }
+}
+
+// Sorted mode: the ions the push listed as far (a bound electron a cell or
+// more from its nucleus), each moved by push_far; anything push_far cannot
+// move is a domain error.
+template <int D>
+__global__ void __launch_bounds__(128) k_push_far(GridP g, PushArgs A) {
+  const int n = min(*A.far_n, A.far_cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int4 e = A.far[k];
+    const int t = e.z;
+    const int T0[3] = {(t % g.nt[0]) * Geo<D>::L0, ((t / g.nt[0]) % g.nt[1]) * Geo<D>::L1,
+                       (t / (g.nt[0] * g.nt[1])) * Geo<D>::L2};
+    if (!push_far<D>(g, A.sp[e.x], A.p[e.x], e.y, T0[0], T0[1], T0[2], A.status, reinterpret_cast<QRec *>(A.grec),
+                     A.grec_n, A.grec_cap, A.E, A.B, A.jfx, A.jscale))
+      atomicOr(A.status, ST_DOMAIN);
   }
 }
 
@@ -1226,6 +1478,8 @@ void launch_one(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream
   cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), s);
   k_push<D, DET><<<blocks < g.ntiles ? blocks : g.ntiles, push_threads(D), smem, s>>>(g, a, tm);
   if constexpr (DET) {
+    k_push_far<D><<<a.sms, 128, 0, s>>>(g, a);
+    cudaMemsetAsync(a.far_n, 0, sizeof(int), s);
     k_records<D><<<a.sms * 8, 256, 0, s>>>(g, reinterpret_cast<const QRec *>(a.grec), a.grec_n, a.grec_cap, a.jfx,
                                           a.jscale);
     cudaMemsetAsync(a.grec_n, 0, sizeof(int), s);

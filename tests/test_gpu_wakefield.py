@@ -57,3 +57,43 @@ def test_wakefield_reduced_parity_and_regime():
     assert np.abs((R - R0)[..., keep]).max() < 1e-3 * qe
     gpu.close()
     ora.close()
+
+
+def test_far_bound_electrons_3d():
+    """3D: neutral two-body ions of the medium (Z_b = 1, w_b = 3: the modified
+    Coulomb field holds the bound electron with at most ~0.02) hit by an
+    a0 = 3 pulse, which tears the bound electrons several cells from their
+    nuclei.  Those bodies are gathered and deposited on the global grid (the
+    sorted mode's far path); fields and both bodies match the oracle.  The
+    atomic mode, which has no far path, reports a domain error."""
+    from paper_2208_08038_gb300 import binding as B
+    wl = synth.neutral_3d(seed=8, steps=60, n=(48, 16, 16), ppc=1, sigma_u=0.0, margin=3)
+    wl.bc = (1, 0, 0)
+    L = wl.lasers[0]
+    L.a0, L.waist, L.fwhm = 3.0, 0.0, 2 * synth.T0
+    L.t0 = 1.5 * L.fwhm
+    ora, osid, _ = oracle_from_workload(wl)
+    gpu, gsid, _ = gpu_from_workload(wl, deposit_mode=1)
+    ora.step(wl.steps)
+    gpu.step(wl.steps)
+    gpu.sync()
+    x1o, x2o, u1o, u2o = ora.bodies(osid[0])
+    dist = np.linalg.norm(x1o - x2o, axis=1)
+    assert dist.max() > 3 * wl.dx[0], dist.max()  # the far path ran
+    err = field_rel_l2(gpu.fields(), ora.fields())
+    print(f"far bodies 3D: {int((dist > wl.dx[0]).sum())} ions with r > dx, E,B rel L2 {err:.3e}")
+    assert err < 1e-3, err
+    x1g, x2g, u1g, u2g = gpu.read_particles(gsid[0], len(x1o))
+    Lb = np.array(wl.n) * np.array(wl.dx)
+    d = (x2g - x2o + 0.5 * Lb) % Lb - 0.5 * Lb
+    assert np.abs(d).max() < 1e-3 * wl.dx[0], np.abs(d).max()
+    assert rel_l2(u2g, u2o) < 1e-3
+    gpu.close()
+    ora.close()
+    # the atomic mode has no far path: a domain error
+    gpu, _, _ = gpu_from_workload(wl, deposit_mode=0)
+    gpu.step(wl.steps)
+    with pytest.raises(B.BPError) as e:
+        gpu.sync()
+    assert e.value.code == B.BP_ERR_DOMAIN
+    gpu.close()
