@@ -1471,7 +1471,7 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   if (P.comp > 2) return fail(c, BP_ERR_ARG, "bp_backward: the loss probe must record an E component");
   const long long c0 = ad.probe_c0[probe_id];
   const long long nrec = std::min<long long>(ad.nsteps, P.cap - c0);
-  if (adj_prepare(g.D)) return fail(c, BP_ERR_CUDA, "adjoint kernel set-up");
+  if (adj_prepare(g.D, &ad.push_blocks, &ad.scat_blocks)) return fail(c, BP_ERR_CUDA, "adjoint kernel set-up");
   // buffers
   if (!ad.lamE[0]) {
     for (int k = 0; k < 3; ++k) {
@@ -1481,11 +1481,24 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
       ad.H[k] = (float *)dalloc(c, sizeof(float) * g.ncell);
       if (!ad.lamE[k] || !ad.lamB[k] || !ad.lamJ[k] || !ad.H[k]) return fail(c, BP_ERR_OOM, "adjoint fields");
     }
-    ad.box = (float *)dalloc(c, sizeof(float) * 6 * (size_t)g.gcells * g.ntiles);
-    ad.occ = (unsigned char *)dalloc(c, g.ntiles);
+    ad.lfx = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 6 * (size_t)g.ncell);
+    ad.dirty = (unsigned char *)dalloc(c, g.ntiles);
     ad.emax = (unsigned *)dalloc(c, sizeof(unsigned));
     ad.status = (int *)dalloc(c, sizeof(int));
-    if (!ad.box || !ad.occ || !ad.emax || !ad.status) return fail(c, BP_ERR_OOM, "adjoint boxes");
+    ad.kst = (int *)dalloc(c, sizeof(int));
+    ad.nwork = (int *)dalloc(c, sizeof(int));
+    if (!ad.lfx || !ad.dirty || !ad.emax || !ad.status || !ad.kst || !ad.nwork)
+      return fail(c, BP_ERR_OOM, "adjoint accumulators");
+  }
+  // work items: every tile and species contributes at most one partial chunk
+  long long want_work = 0;
+  for (auto &s : c->sp) want_work += (s.p.cap + kAdjChunk - 1) / kAdjChunk + g.ntiles;
+  if (want_work > INT32_MAX) return fail(c, BP_ERR_ARG, "bp_backward: too many particles for the work list");
+  if (ad.work_cap < want_work) {
+    dfree(c, ad.work);
+    ad.work = (int4 *)dalloc(c, sizeof(int4) * (size_t)want_work);
+    if (!ad.work) return fail(c, BP_ERR_OOM, "adjoint work list");
+    ad.work_cap = want_work;
   }
   bool xb_ok = ad.xb.size() == c->sp.size() && ad.xb_cap.size() == c->sp.size();
   for (size_t q = 0; xb_ok && q < c->sp.size(); ++q) xb_ok = ad.xb_cap[q] == c->sp[q].p.cap;
@@ -1520,6 +1533,11 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   }
   cudaMemsetAsync(ad.emax, 0, sizeof(unsigned), st);
   cudaMemsetAsync(ad.status, 0, sizeof(int), st);
+  cudaMemsetAsync(ad.nwork, 0, sizeof(int), st);
+  // kept clear from step to step by k_adj_fxsum; cleared here too, in case
+  // an earlier backward pass stopped on an error
+  cudaMemsetAsync(ad.lfx, 0, sizeof(unsigned long long) * 6 * (size_t)g.ncell, st);
+  cudaMemsetAsync(ad.dirty, 0, g.ntiles, st);
   for (size_t q = 0; q < c->sp.size(); ++q) {
     cudaMemsetAsync(ad.xb[q], 0, sizeof(float) * 12 * c->sp[q].p.cap, st);
     cudaMemsetAsync(ad.acb[q], 0, sizeof(double) * c->sp[q].p.cap, st);
@@ -1554,6 +1572,8 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   }
   cudaStream_t as = ad.stream;
   const int K = ad.K;
+  const AdjBufs bufs{ad.lfx, ad.dirty, ad.kst, ad.emax, ad.nwork, ad.work, (int)ad.work_cap, kAdjChunk,
+                     ad.push_blocks, ad.scat_blocks};
   auto recompute = [&](int seg) -> int {
     const int bank = seg & 1;
     // the reverse steps of segment seg + 2 read this bank
@@ -1604,14 +1624,14 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
       std::vector<PartP> pp;
       for (size_t q = 0; q < c->sp.size(); ++q) pp.push_back(ad.st_parts[bank * K + j][q].p);
       launch_adj_push(g, (int)c->sp.size(), sps.data(), pp.data(), xbs.data(), acbs.data(), ebs.data(), caps.data(), En,
-                      Bn, lJ, ad.box, ad.occ, ad.emax, ad.lamE, ad.lamB, ad.status, as);
+                      Bn, lJ, bufs, ad.lamE, ad.lamB, ad.status, as);
       // B^n = B^{n-1/2} - dt/2 curl E^n
       launch_adj_b(g, ad.lamE, ad.lamB, 0.5f * g.dt, nullptr, as);
       // E transpose and its Mur passes (one per pass and open axis), two B
-      // transposes, particle adjoint, scatter, box sum
+      // transposes, work list, particle adjoint, scatter, fixed-point sum
       int nopen = 0;
       for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
-      c->launches += 1 + nopen * nopen + 2 + 3;
+      c->launches += 1 + nopen * nopen + 2 + 4;
       int rc = check_launch(c, "backward step");
       if (rc) return rc;
     }

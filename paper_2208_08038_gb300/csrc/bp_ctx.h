@@ -39,8 +39,13 @@ struct bp_adjoint {
   cudaEvent_t rec_done[2] = {nullptr, nullptr};     // bank b recomputed
   cudaEvent_t rev_done[2] = {nullptr, nullptr};     // bank b's reverse steps done
   float *lamE[3] = {}, *lamB[3] = {}, *lamJ[3] = {}, *H[3] = {};
-  float *box = nullptr;
-  unsigned char *occ = nullptr;
+  unsigned long long *lfx = nullptr;  // [6][ncell] scattered field adjoints, fixed point
+  unsigned char *dirty = nullptr;     // [ntiles]
+  int *kst = nullptr;                 // the step's fixed-point exponent
+  int *nwork = nullptr;               // the step's work items (count, list)
+  int4 *work = nullptr;
+  long long work_cap = 0;
+  int push_blocks = 0, scat_blocks = 0;
   std::vector<float *> xb;     // per species [12][cap]
   std::vector<double *> acb;   // per species [cap]
   std::vector<float *> eb;     // per species [12][cap], the step's gathered-field adjoints by slot

@@ -230,6 +230,57 @@ inline int row_blocks(const GridP &g, int bs) {
   return (int)(rows * ((g.n[0] + bs - 1) / bs));
 }
 
+// Four consecutive x cells per thread (rows hold a multiple of 8 cells, so a
+// group never straddles a row or a tile): float4 loads and stores of each
+// component, index arithmetic once per thread.
+struct Cell4 {
+  long long q;      // linear index of the group's first cell
+  int c[3];         // its coordinates
+  long long up[3];  // offset to the +1 neighbour along y, z (and x for the group's last cell)
+  long long dn[3];  // offset to the -1 neighbour along y, z (and x for the group's first cell)
+};
+
+template <int D>
+__device__ __forceinline__ bool row_cell4(const GridP &g, Cell4 &C) {
+  const int n0 = g.n[0], n4 = n0 >> 2;
+  const int chunks = (n4 + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int row = (int)blockIdx.x / chunks;
+  const int x4 = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
+  if (x4 >= n4) return false;
+  C.c[0] = 4 * x4;
+  C.c[1] = D >= 2 ? row % g.n[1] : 0;
+  C.c[2] = D >= 3 ? row / g.n[1] : 0;
+  C.q = (long long)row * n0 + C.c[0];
+  // along x: the neighbour after the last cell and before the first one
+  C.up[0] = C.c[0] + 4 < n0 ? 4 : 4 - n0;
+  C.dn[0] = C.c[0] > 0 ? -1 : n0 - 1;
+  long long stride = n0;
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    const int n = g.n[a];
+    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
+    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
+    stride *= n;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float el(const float4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void set_el(float4 &v, int i, float x) {
+  if (i == 0) v.x = x;
+  else if (i == 1) v.y = x;
+  else if (i == 2) v.z = x;
+  else v.w = x;
+}
+
+// blocks of a four-cells-per-thread row launch (rows of n0 / 4 threads)
+inline int row_blocks4(const GridP &g, int bs) {
+  const long long rows = g.ncell / g.n[0];
+  return (int)(rows * ((g.n[0] / 4 + bs - 1) / bs));
+}
+
 // tile of a cell (row-major over tiles, x fastest)
 __host__ __device__ __forceinline__ int tile_of(const GridP &g, const int c[3]) {
   return c[0] / g.L[0] + g.nt[0] * (c[1] / g.L[1] + g.nt[1] * (c[2] / g.L[2]));
@@ -425,10 +476,23 @@ void launch_copy_many(const CopyList &L, cudaStream_t s);
 // zero (optional): three arrays cleared on the way
 void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float *zero[3], cudaStream_t s);
 size_t adj_push_smem(int D);
-int adj_prepare(int D);
+constexpr int kAdjChunk = 256;  // particles per work item of the particle adjoint
+int adj_prepare(int D, int *push_blocks, int *scat_blocks);
+// device buffers and launch shapes of the particle adjoint
+struct AdjBufs {
+  unsigned long long *lfx;  // [6][ncell] field-adjoint sums in fixed point (kept zero between steps)
+  unsigned char *dirty;     // [ntiles] tiles with lfx entries
+  int *kst;                 // the step's fixed-point exponent
+  unsigned *emax;           // the step's largest |gathered-field adjoint| (float bits)
+  int *nwork;               // work items of the step
+  int4 *work;
+  int work_cap;
+  int chunk;                // particles per work item
+  int push_blocks, scat_blocks;
+};
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
                      float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
-                     const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
-                     float *lamB[3], int *status, cudaStream_t s);
+                     const float *const lamJ[3], const AdjBufs &b, float *lamE[3], float *lamB[3], int *status,
+                     cudaStream_t s);
 void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,
                     const double *acb, const double *scale, double *out, cudaStream_t s);

@@ -90,94 +90,168 @@ template <int D>
 __device__ __forceinline__ bool e_int(const GridP &g, int comp, const int x[3]) {
   return !exterior_c<D>(g, 1 << comp, x) && !mur_node<D>(g, 1 << comp, x);
 }
-// G of component comp at the +1 neighbour along a, masked to interior E nodes
-// (0 off an open face)
+// Both transposes take four consecutive x cells per thread (float4 loads
+// and stores, as the forward Yee kernels); the masks are those of the
+// forward update, cell by cell.
+//
+// G of component comp at cell i of a group (G: the group), at its +1
+// neighbour along x (gn: the value after the group's last cell) and along y
+// or z (Gu: the group one row or plane up), masked to interior E nodes (0
+// off an open face)
 template <int D>
-__device__ __forceinline__ float g_up(const GridP &g, const float *G, int comp, const Cell &C, int a) {
-  int x[3] = {C.c[0], C.c[1], C.c[2]};
+__device__ __forceinline__ float g_here4(const GridP &g, const float4 &G, int comp, const int c[3], int i) {
+  const int x[3] = {c[0] + i, c[1], c[2]};
+  return e_int<D>(g, comp, x) ? el(G, i) : 0.0f;
+}
+template <int D>
+__device__ __forceinline__ float g_up_x4(const GridP &g, const float4 &G, float gn, int comp, const int c[3], int i) {
+  int x[3] = {c[0] + i + 1, c[1], c[2]};
+  if (x[0] >= g.n[0]) {
+    if (g.bc[0] != BP_PERIODIC) return 0.0f;
+    x[0] = 0;
+  }
+  return e_int<D>(g, comp, x) ? (i < 3 ? el(G, i + 1) : gn) : 0.0f;
+}
+template <int D>
+__device__ __forceinline__ float g_up_a4(const GridP &g, const float4 &Gu, int comp, const int c[3], int i, int a) {
+  int x[3] = {c[0] + i, c[1], c[2]};
   if (++x[a] >= g.n[a]) {
     if (g.bc[a] != BP_PERIODIC) return 0.0f;
     x[a] = 0;
   }
-  return e_int<D>(g, comp, x) ? G[C.q + C.up[a]] : 0.0f;
-}
-template <int D>
-__device__ __forceinline__ float g_here(const GridP &g, const float *G, int comp, const Cell &C) {
-  return e_int<D>(g, comp, C.c) ? G[C.q] : 0.0f;
+  return e_int<D>(g, comp, x) ? el(Gu, i) : 0.0f;
 }
 
 // interior E update transposed: H += G (interior and exterior nodes),
 // lamJ = -dt G (interior), lamB += dt curl_B^T (G on interior nodes)
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_e(GridP g, const float *G0, const float *G1, const float *G2, float *H0,
+__global__ void __launch_bounds__(128) k_adj_e(GridP g, const float *G0, const float *G1, const float *G2, float *H0,
                                                float *H1, float *H2, float *B0, float *B1, float *B2, float *J0,
                                                float *J1, float *J2) {
-  Cell C;
-  if (!row_cell<D>(g, C)) return;
-  const float *G[3] = {G0, G1, G2};
-  float *H[3] = {H0, H1, H2}, *J[3] = {J0, J1, J2};
-  const float dt = g.dt;
+  Cell4 C;
+  if (!row_cell4<D>(g, C)) return;
   const long long q = C.q;
+  const float dt = g.dt;
+  const float4 g0 = ld4(G0 + q), g1 = ld4(G1 + q), g2 = ld4(G2 + q);
+  {
+    const float4 gg[3] = {g0, g1, g2};
+    float *H[3] = {H0, H1, H2}, *J[3] = {J0, J1, J2};
 #pragma unroll
-  for (int comp = 0; comp < 3; ++comp) {
-    const bool ex = exterior_c<D>(g, 1 << comp, C.c);
-    const bool in = !ex && !mur_node<D>(g, 1 << comp, C.c);
-    const float v = G[comp][q];
-    if (in || ex) H[comp][q] += v;
-    J[comp][q] = in ? -dt * v : 0.0f;
+    for (int comp = 0; comp < 3; ++comp) {
+      float4 h = ld4(H[comp] + q), j;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int x[3] = {C.c[0] + i, C.c[1], C.c[2]};
+        const bool ex = exterior_c<D>(g, 1 << comp, x);
+        const bool in = !ex && !mur_node<D>(g, 1 << comp, x);
+        const float v = el(gg[comp], i);
+        if (in || ex) set_el(h, i, el(h, i) + v);
+        set_el(j, i, in ? -dt * v : 0.0f);
+      }
+      st4(H[comp] + q, h);
+      st4(J[comp] + q, j);
+    }
   }
-  float bx = 0.0f, by = 0.0f, bz = 0.0f;
-  if (D >= 3) bx += (g_here<D>(g, G[1], 1, C) - g_up<D>(g, G[1], 1, C, 2)) * g.idx[2];
-  if (D >= 2) bx -= (g_here<D>(g, G[2], 2, C) - g_up<D>(g, G[2], 2, C, 1)) * g.idx[1];
-  if (D >= 3) by -= (g_here<D>(g, G[0], 0, C) - g_up<D>(g, G[0], 0, C, 2)) * g.idx[2];
-  by += (g_here<D>(g, G[2], 2, C) - g_up<D>(g, G[2], 2, C, 0)) * g.idx[0];
-  if (D >= 2) bz += (g_here<D>(g, G[0], 0, C) - g_up<D>(g, G[0], 0, C, 1)) * g.idx[1];
-  bz -= (g_here<D>(g, G[1], 1, C) - g_up<D>(g, G[1], 1, C, 0)) * g.idx[0];
-  B0[q] += dt * bx;
-  B1[q] += dt * by;
-  B2[q] += dt * bz;
+  const float g1n = G1[q + C.up[0]], g2n = G2[q + C.up[0]];  // x neighbours of the last cell
+  float4 g2y = g2, g0y = g0, g1z = g1, g0z = g0;
+  if (D >= 2) {
+    g2y = ld4(G2 + q + C.up[1]);
+    g0y = ld4(G0 + q + C.up[1]);
+  }
+  if (D >= 3) {
+    g1z = ld4(G1 + q + C.up[2]);
+    g0z = ld4(G0 + q + C.up[2]);
+  }
+  float4 b0 = ld4(B0 + q), b1 = ld4(B1 + q), b2 = ld4(B2 + q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float bx = 0.0f, by = 0.0f, bz = 0.0f;
+    if (D >= 3) bx += (g_here4<D>(g, g1, 1, C.c, i) - g_up_a4<D>(g, g1z, 1, C.c, i, 2)) * g.idx[2];
+    if (D >= 2) bx -= (g_here4<D>(g, g2, 2, C.c, i) - g_up_a4<D>(g, g2y, 2, C.c, i, 1)) * g.idx[1];
+    if (D >= 3) by -= (g_here4<D>(g, g0, 0, C.c, i) - g_up_a4<D>(g, g0z, 0, C.c, i, 2)) * g.idx[2];
+    by += (g_here4<D>(g, g2, 2, C.c, i) - g_up_x4<D>(g, g2, g2n, 2, C.c, i)) * g.idx[0];
+    if (D >= 2) bz += (g_here4<D>(g, g0, 0, C.c, i) - g_up_a4<D>(g, g0y, 0, C.c, i, 1)) * g.idx[1];
+    bz -= (g_here4<D>(g, g1, 1, C.c, i) - g_up_x4<D>(g, g1, g1n, 1, C.c, i)) * g.idx[0];
+    set_el(b0, i, el(b0, i) + dt * bx);
+    set_el(b1, i, el(b1, i) + dt * by);
+    set_el(b2, i, el(b2, i) + dt * bz);
+  }
+  st4(B0 + q, b0);
+  st4(B1 + q, b1);
+  st4(B2 + q, b2);
 }
 
-// B adjoint of component comp (stagger 6, 5, 3) at the -1 neighbour along a,
-// masked to non-exterior B nodes (0 off an open face)
+// B adjoint of component stagger pat (6, 5, 3 for x, y, z) at cell i of a
+// group (B: the group), at its -1 neighbour along x (bp: the value before the
+// group's first cell) and along y or z (Bd: the group one row or plane
+// down), masked to non-exterior B nodes (0 off an open face)
 template <int D>
-__device__ __forceinline__ float b_dn(const GridP &g, const float *Bb, int pat, const Cell &C, int a) {
-  int x[3] = {C.c[0], C.c[1], C.c[2]};
+__device__ __forceinline__ float b_here4(const GridP &g, const float4 &B, int pat, const int c[3], int i) {
+  const int x[3] = {c[0] + i, c[1], c[2]};
+  return exterior_c<D>(g, pat, x) ? 0.0f : el(B, i);
+}
+template <int D>
+__device__ __forceinline__ float b_dn_x4(const GridP &g, const float4 &B, float bp, int pat, const int c[3], int i) {
+  int x[3] = {c[0] + i - 1, c[1], c[2]};
+  if (x[0] < 0) {
+    if (g.bc[0] != BP_PERIODIC) return 0.0f;
+    x[0] = g.n[0] - 1;
+  }
+  return exterior_c<D>(g, pat, x) ? 0.0f : (i > 0 ? el(B, i - 1) : bp);
+}
+template <int D>
+__device__ __forceinline__ float b_dn_a4(const GridP &g, const float4 &Bd, int pat, const int c[3], int i, int a) {
+  int x[3] = {c[0] + i, c[1], c[2]};
   if (--x[a] < 0) {
     if (g.bc[a] != BP_PERIODIC) return 0.0f;
     x[a] = g.n[a] - 1;
   }
-  return exterior_c<D>(g, pat, x) ? 0.0f : Bb[C.q + C.dn[a]];
-}
-template <int D>
-__device__ __forceinline__ float b_here(const GridP &g, const float *Bb, int pat, const Cell &C) {
-  return exterior_c<D>(g, pat, C.c) ? 0.0f : Bb[C.q];
+  return exterior_c<D>(g, pat, x) ? 0.0f : el(Bd, i);
 }
 
 // B <- B - h curl E transposed: E adjoint -= h curl_E^T (B adjoint on
 // non-exterior B nodes); the B adjoint itself passes through.  Z0..Z2, when
 // given, are cleared on the way (the buffer the next E transpose fills).
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_b(GridP g, float *E0, float *E1, float *E2, const float *B0,
+__global__ void __launch_bounds__(128) k_adj_b(GridP g, float *E0, float *E1, float *E2, const float *B0,
                                                const float *B1, const float *B2, float h, float *Z0, float *Z1,
                                                float *Z2) {
-  Cell C;
-  if (!row_cell<D>(g, C)) return;
+  Cell4 C;
+  if (!row_cell4<D>(g, C)) return;
   const long long q = C.q;
-  float ex = 0.0f, ey = 0.0f, ez = 0.0f;
-  if (D >= 3) ex += (b_dn<D>(g, B1, 5, C, 2) - b_here<D>(g, B1, 5, C)) * g.idx[2];
-  if (D >= 2) ex -= (b_dn<D>(g, B2, 3, C, 1) - b_here<D>(g, B2, 3, C)) * g.idx[1];
-  if (D >= 3) ey -= (b_dn<D>(g, B0, 6, C, 2) - b_here<D>(g, B0, 6, C)) * g.idx[2];
-  ey += (b_dn<D>(g, B2, 3, C, 0) - b_here<D>(g, B2, 3, C)) * g.idx[0];
-  if (D >= 2) ez += (b_dn<D>(g, B0, 6, C, 1) - b_here<D>(g, B0, 6, C)) * g.idx[1];
-  ez -= (b_dn<D>(g, B1, 5, C, 0) - b_here<D>(g, B1, 5, C)) * g.idx[0];
-  E0[q] -= h * ex;
-  E1[q] -= h * ey;
-  E2[q] -= h * ez;
+  const float4 b0 = ld4(B0 + q), b1 = ld4(B1 + q), b2 = ld4(B2 + q);
+  const float b1p = B1[q + C.dn[0]], b2p = B2[q + C.dn[0]];  // x neighbours of the first cell
+  float4 b1z = b1, b2y = b2, b0z = b0, b0y = b0;
+  if (D >= 2) {
+    b2y = ld4(B2 + q + C.dn[1]);
+    b0y = ld4(B0 + q + C.dn[1]);
+  }
+  if (D >= 3) {
+    b1z = ld4(B1 + q + C.dn[2]);
+    b0z = ld4(B0 + q + C.dn[2]);
+  }
+  float4 e0 = ld4(E0 + q), e1 = ld4(E1 + q), e2 = ld4(E2 + q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+    if (D >= 3) ex += (b_dn_a4<D>(g, b1z, 5, C.c, i, 2) - b_here4<D>(g, b1, 5, C.c, i)) * g.idx[2];
+    if (D >= 2) ex -= (b_dn_a4<D>(g, b2y, 3, C.c, i, 1) - b_here4<D>(g, b2, 3, C.c, i)) * g.idx[1];
+    if (D >= 3) ey -= (b_dn_a4<D>(g, b0z, 6, C.c, i, 2) - b_here4<D>(g, b0, 6, C.c, i)) * g.idx[2];
+    ey += (b_dn_x4<D>(g, b2, b2p, 3, C.c, i) - b_here4<D>(g, b2, 3, C.c, i)) * g.idx[0];
+    if (D >= 2) ez += (b_dn_a4<D>(g, b0y, 6, C.c, i, 1) - b_here4<D>(g, b0, 6, C.c, i)) * g.idx[1];
+    ez -= (b_dn_x4<D>(g, b1, b1p, 5, C.c, i) - b_here4<D>(g, b1, 5, C.c, i)) * g.idx[0];
+    set_el(e0, i, el(e0, i) - h * ex);
+    set_el(e1, i, el(e1, i) - h * ey);
+    set_el(e2, i, el(e2, i) - h * ez);
+  }
+  st4(E0 + q, e0);
+  st4(E1 + q, e1);
+  st4(E2 + q, e2);
   if (Z0) {
-    Z0[q] = 0.0f;
-    Z1[q] = 0.0f;
-    Z2[q] = 0.0f;
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    st4(Z0 + q, z);
+    st4(Z1 + q, z);
+    st4(Z2 + q, z);
   }
 }
 
@@ -542,6 +616,20 @@ __device__ __noinline__ void deposit_adj_general(const float *Jl, AdjGen &A) {
   if (A.two) deposit_adj<D, 5, 1>(Jl, A.n2, A.xi + 1, A.dd + 1, A.qw + 1, A.vv + 1, A.dxdt, A.X0 + 1, A.X1 + 1, A.vb + 1);
 }
 
+// The step's work: every occupied tile's particles of each species, cut
+// into chunks of at most `chunk` particles; an item is (tile, species,
+// first, end) in the stored particle arrays.  k_adj_push and k_adj_scatter
+// hand the items to their resident blocks round-robin, so the blocks stay
+// busy whatever the number of occupied tiles and their populations.  Each
+// particle's results depend on the particle alone (its adjoint state is
+// written by load id, its field-adjoint adds are exact integers), so the
+// order of the list, which the appends leave open, changes nothing.
+struct AdjWork {
+  int *n;       // items in the list (cleared by k_adj_fxsum)
+  int4 *item;
+  int cap;
+};
+
 struct AdjState {
   float *xb;      // [12][cap] by load id: x1b(3) x2b(3) u1b(3) u2b(3)
   double *acb;    // [cap] adjoint of a_c, accumulated over steps
@@ -778,20 +866,29 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
   }
 }
 
+// one thread per tile and species: the chunks of its particles appended
+__global__ void k_adj_work(GridP g, AdjArgs A, AdjWork W, int chunk) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.ntiles * A.nsp) return;
+  const int t = q % g.ntiles, s = q / g.ntiles;
+  const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+  if (end <= beg) return;
+  const int m = (end - beg + chunk - 1) / chunk;
+  const int at = atomicAdd(W.n, m);
+  for (int k = 0; k < m && at + k < W.cap; ++k)
+    W.item[at + k] = make_int4(t, s, beg + k * chunk, min(beg + (k + 1) * chunk, end));
+}
+
+// the staged boxes of tile t: E^n, B^n (gather box) and the J adjoint
 template <int D>
-__global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjArgs A) {
+__device__ __forceinline__ void adj_stage(const GridP &g, const AdjArgs &A, int t, int T0[3], float *Gsm, float *Jl) {
   using BX = Box<D>;
   constexpr int GC = BX::GCELLS, JC = BX::JCELLS;
-  extern __shared__ __align__(16) unsigned char smem[];
-  float *Gsm = reinterpret_cast<float *>(smem);  // E^n, B^n
-  float *Jl = Gsm + 6 * GC;                      // adjoint of J
-  const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
-  int total = 0;
-  for (int s = 0; s < A.nsp; ++s) total += A.p[s].tstart[t + 1] - A.p[s].tstart[t];
-  if (total == 0) return;
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
-  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+  T0[0] = tc[0] * Geo<D>::L0;
+  T0[1] = tc[1] * Geo<D>::L1;
+  T0[2] = tc[2] * Geo<D>::L2;
   for (int q = tid; q < BX::GCOMP; q += bs) {
     int bidx[3] = {q % BX::G0, (q / BX::G0) % BX::G1, q / (BX::G0 * BX::G1)};
     const int si = BX::gi(bidx[0], bidx[1], bidx[2]);
@@ -831,11 +928,31 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + si] = ok ? A.lamJ[cc][gi] : 0.0f;
   }
-  __syncthreads();
+}
+
+// the reversed push of the step's work items; a block restages its boxes
+// only when the tile changes
+template <int D>
+__global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjArgs A, AdjWork W) {
+  using BX = Box<D>;
+  constexpr int GC = BX::GCELLS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *Gsm = reinterpret_cast<float *>(smem);  // E^n, B^n
+  float *Jl = Gsm + 6 * GC;                      // adjoint of J
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const int nw = min(*W.n, W.cap);
+  int staged = -1, T0[3] = {0, 0, 0};
   float emax = 0.0f;
-  for (int s = 0; s < A.nsp; ++s) {
-    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
-    for (long long i = beg + tid; i < end; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, emax);
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int4 it = W.item[w];
+    if (it.x != staged) {
+      __syncthreads();  // every thread is done with the previous boxes
+      adj_stage<D>(g, A, it.x, T0, Gsm, Jl);
+      staged = it.x;
+      __syncthreads();
+    }
+    const int s = it.y;
+    for (long long i = it.z + tid; i < it.w; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, emax);
   }
   // non-negative floats order like their bit patterns
   const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(emax));
@@ -843,12 +960,15 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
 }
 
 // Gather transposed, part 2: scatter the stored field adjoints e of both
-// bodies with the gather weights into a per-tile box, in 64-bit fixed point
-// (exact, independent of the order of the adds; the scale puts the step's
-// largest |e| at 2^30, so a quantum is below 1e-9 of it), then write the box
-// (compact) for k_adj_boxsum.  Each add is the forward deposit's split
-// (fx_add: non-returning 32-bit shared atomics, the high word only when
-// needed), which sums the same rounded integers as any other exact order.
+// bodies with the gather weights, in 64-bit fixed point (exact, independent
+// of the order of the adds; the scale puts the step's largest |e| at 2^30,
+// so a quantum is below 1e-9 of it).  A block takes a work item (a chunk of
+// one tile's particles), adds into the tile's box in shared memory with the
+// forward deposit's split (fx_add: non-returning 32-bit shared atomics, the
+// high word only when needed), then adds the box's non-zero nodes into the
+// per-cell 64-bit accumulator lfx (integer adds: exact in any order) and
+// marks the tiles the box reaches; k_adj_fxsum converts the marked tiles'
+// cells once to FP32 and adds them to the field adjoints.
 struct ScatArgs {
   int nsp;
   SpecP sp[BP_MAX_SPECIES];
@@ -856,8 +976,9 @@ struct ScatArgs {
   const float *eb[BP_MAX_SPECIES];
   long long ecap[BP_MAX_SPECIES];
   const unsigned *emax;
-  float *box;              // [ntiles][6][gcells] (compact)
-  unsigned char *occ;
+  unsigned long long *lfx;  // [6][ncell] field-adjoint sums, fixed point, scale 2^k
+  unsigned char *dirty;     // [ntiles] a box added into the tile's cells
+  int *kst;                 // k of this step, for k_adj_fxsum
 };
 
 // stencil base and weights of component PAT at one body
@@ -919,33 +1040,30 @@ __device__ __forceinline__ void scatter_comp(unsigned *A, const int d1[3], const
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S) {
+__global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWork W) {
   using BX = Box<D>;
-  constexpr int GC = BX::GCELLS;
+  constexpr int GC = BX::GCELLS, GN = BX::GCOMP;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned *A = reinterpret_cast<unsigned *>(smem);  // [6][GC] low words, then [6][GC] high words
-  const int t = blockIdx.x;
   const int tid = threadIdx.x, bs = blockDim.x;
-  int total = 0;
-  for (int s = 0; s < S.nsp; ++s) total += S.p[s].tstart[t + 1] - S.p[s].tstart[t];
   const unsigned mbits = *S.emax;
-  if (total == 0 || mbits == 0) {
-    if (tid == 0) S.occ[t] = 0;
-    return;
-  }
+  if (mbits == 0) return;  // every gathered-field adjoint is zero
+  const int nw = min(*W.n, W.cap);
   int ex;
   frexpf(__uint_as_float(mbits), &ex);  // emax < 2^ex
   const int k = 30 - ex;
+  if (blockIdx.x == 0 && tid == 0) *S.kst = k;
   for (int q = tid; q < 12 * GC; q += bs) A[q] = 0u;
-  __syncthreads();
-  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
-  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  for (int s = 0; s < S.nsp; ++s) {
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int4 it = W.item[w];
+    const int t = it.x, s = it.y;
+    const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+    const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+    __syncthreads();  // the box is clear (the previous item's flush cleared what it read)
     const PartP &P = S.p[s];
     const bool two = S.sp[s].kind == BP_TWO_BODY;
     const long long cap = P.cap, ec = S.ecap[s];
-    const int beg = P.tstart[t], end = P.tstart[t + 1];
-    for (long long i = beg + tid; i < end; i += bs) {
+    for (long long i = it.z + tid; i < it.w; i += bs) {
       const int cell = P.cell[i];
       if (cell < 0) continue;
       int c[3];
@@ -979,69 +1097,81 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S) {
       scatter_comp<D, 5>(A + 4 * GC, d, f, e[4], d2, f2, e[10], two);
       scatter_comp<D, 3>(A + 5 * GC, d, f, e[5], d2, f2, e[11], two);
     }
+    __syncthreads();
+    // the box's non-zero nodes into lfx (nodes beyond an open face carry no
+    // field the gather read), each node cleared once read
+    for (int q = tid; q < 6 * GN; q += bs) {
+      const int cc = q / GN, r = q - cc * GN;
+      const int bidx[3] = {r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1)};
+      const int si = cc * GC + BX::gi(bidx[0], bidx[1], bidx[2]);
+      const unsigned lo = A[si], hi = A[si + 6 * GC];
+      if ((lo | hi) == 0u) continue;
+      A[si] = 0u;
+      A[si + 6 * GC] = 0u;
+      const long long v = (long long)(int)hi * 65536LL + (long long)(int)lo;  // fx_value
+      if (v == 0) continue;
+      long long gidx = 0, stride = 1;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int x = T0[a] - (a < D ? BX::OG : 0) + bidx[a];
+        if (a < D) {
+          if (g.bc[a] == BP_PERIODIC) x = wrap_once(x, g.n[a]);
+          else ok &= (x >= 0 && x < g.n[a]);
+        }
+        gidx += (long long)x * stride;
+        stride *= g.n[a];
+      }
+      if (ok) atomicAdd(S.lfx + (size_t)cc * g.ncell + gidx, (unsigned long long)v);
+    }
+    // the box spans the tile and less than one tile on each side
+    constexpr int NM = D == 1 ? 3 : (D == 2 ? 9 : 27);
+    if (tid < NM) {
+      int o[3] = {tid % 3 - 1, D >= 2 ? (tid / 3) % 3 - 1 : 0, D >= 3 ? tid / 9 - 1 : 0};
+      int u[3];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        u[a] = tc[a] + o[a];
+        if (a < D && g.bc[a] == BP_PERIODIC) u[a] = wrap_once(u[a], g.nt[a]);
+        else ok &= u[a] >= 0 && u[a] < g.nt[a];
+      }
+      if (ok) S.dirty[u[0] + g.nt[0] * (u[1] + g.nt[1] * u[2])] = 1;
+    }
   }
-  __syncthreads();
-  constexpr int GN = BX::GCOMP;
-  float *out = S.box + (size_t)t * 6 * GN;
-  for (int q = tid; q < 6 * GN; q += bs) {
-    const int cc = q / GN, r = q - cc * GN;
-    const int si = cc * GC + BX::gi(r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1));
-    out[q] = ldexpf(__ll2float_rn(fx_value(A + si, 6 * GC)), -k);
-  }
-  if (tid == 0) S.occ[t] = 1;
 }
 
-// adds the per-tile gather-adjoint boxes to the field adjoints, in a fixed
-// order of the covering tiles
+// the marked tiles' cells: lfx to FP32 (one rounding of the exact sum) added
+// to the field adjoints, lfx cleared; the step's emax and work list cleared
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_boxsum(GridP g, const float *box, const unsigned char *occ, float *E0,
-                                                    float *E1, float *E2, float *B0, float *B1, float *B2,
-                                                    unsigned *emax) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *emax = 0u;  // the scatter of this step has read it
-  Cell C;
-  if (!row_cell<D>(g, C)) return;
+__global__ void __launch_bounds__(256) k_adj_fxsum(GridP g, unsigned long long *lfx, unsigned char *dirty,
+                                                   const int *kst, float *E0, float *E1, float *E2, float *B0,
+                                                   float *B1, float *B2, unsigned *emax, int *nwork) {
+  const int t = blockIdx.x, tid = threadIdx.x;
+  if (t == 0 && tid == 0) {
+    *emax = 0u;  // read by this step's scatter
+    *nwork = 0;  // read by this step's push and scatter
+  }
+  const bool mine = dirty[t] != 0;
+  __syncthreads();  // every thread has read the mark before it is cleared
+  if (!mine) return;
   float *out[6] = {E0, E1, E2, B0, B1, B2};
-  const int *c = C.c;
-  int tw[3][3], loc[3][3], nc[3];
+  const int k = *kst;
+  constexpr int L0 = Geo<D>::L0, L1 = Geo<D>::L1, L2 = Geo<D>::L2;
+  const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+  for (int q = tid; q < L0 * L1 * L2; q += blockDim.x) {
+    const int x = tc[0] * L0 + q % L0, y = tc[1] * L1 + (q / L0) % L1, z = tc[2] * L2 + q / (L0 * L1);
+    const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    nc[a] = 0;
-    if (a >= D) {
-      tw[a][0] = 0;
-      loc[a][0] = 0;
-      nc[a] = 1;
-      continue;
-    }
-    const int tb = c[a] / g.L[a];
-#pragma unroll
-    for (int dt = -1; dt <= 1; ++dt) {
-      const int tu = tb + dt;
-      const int l = c[a] - (tu * g.L[a] - g.og[a]);
-      if (l < 0 || l >= g.gb[a]) continue;
-      int tt = tu;
-      if (g.bc[a] == BP_PERIODIC) tt = wrap_once(tu, g.nt[a]);
-      else if (tu < 0 || tu >= g.nt[a]) continue;
-      tw[a][nc[a]] = tt;
-      loc[a][nc[a]] = l;
-      ++nc[a];
+    for (int cc = 0; cc < 6; ++cc) {
+      unsigned long long *p = lfx + (size_t)cc * g.ncell + cell;
+      const long long v = (long long)*p;
+      if (v == 0) continue;
+      *p = 0ull;
+      out[cc][cell] += ldexpf(__ll2float_rn(v), -k);
     }
   }
-  float acc[6] = {0, 0, 0, 0, 0, 0};
-  bool any = false;
-  for (int k = 0; k < nc[2]; ++k)
-    for (int j = 0; j < nc[1]; ++j)
-      for (int i = 0; i < nc[0]; ++i) {
-        const int tile = tw[0][i] + g.nt[0] * (tw[1][j] + g.nt[1] * tw[2][k]);
-        if (!occ[tile]) continue;
-        any = true;
-        const long long l = loc[0][i] + (long long)g.gb[0] * (loc[1][j] + (long long)g.gb[1] * loc[2][k]);
-        const float *b = box + (size_t)tile * 6 * g.gcells;
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) acc[cc] += b[(size_t)cc * g.gcells + l];
-      }
-  if (!any) return;  // no box covers the cell: nothing to add
-#pragma unroll
-  for (int cc = 0; cc < 6; ++cc) out[cc][C.q] += acc[cc];
+  if (tid == 0) dirty[t] = 0;
 }
 
 // deterministic FP64 row sums: out[r * ncomp + k] = scale[r] * sum over the
@@ -1082,18 +1212,18 @@ void launch_adj_e(const GridP &g, float *G[3], float *H[3], float *lamB[3], floa
     for (int a = 0; a < g.D; ++a)
       if (g.bc[a] == BP_OPEN)
         k_adj_mur<<<blocks_for(4 * (g.ncell / g.n[a]), 256), 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], a, p);
-  const int nb = row_blocks(g, 256);
-  if (g.D == 1) k_adj_e<1><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
-  else if (g.D == 2) k_adj_e<2><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
-  else k_adj_e<3><<<nb, 256, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
+  const int nb = row_blocks4(g, 128);
+  if (g.D == 1) k_adj_e<1><<<nb, 128, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
+  else if (g.D == 2) k_adj_e<2><<<nb, 128, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
+  else k_adj_e<3><<<nb, 128, 0, s>>>(g, G[0], G[1], G[2], H[0], H[1], H[2], lamB[0], lamB[1], lamB[2], lamJ[0], lamJ[1], lamJ[2]);
 }
 
 void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float *zero[3], cudaStream_t s) {
-  const int nb = row_blocks(g, 256);
+  const int nb = row_blocks4(g, 128);
   float *z0 = zero ? zero[0] : nullptr, *z1 = zero ? zero[1] : nullptr, *z2 = zero ? zero[2] : nullptr;
-  if (g.D == 1) k_adj_b<1><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
-  else if (g.D == 2) k_adj_b<2><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
-  else k_adj_b<3><<<nb, 256, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
+  if (g.D == 1) k_adj_b<1><<<nb, 128, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
+  else if (g.D == 2) k_adj_b<2><<<nb, 128, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
+  else k_adj_b<3><<<nb, 128, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
 }
 
 size_t adj_push_smem(int D) {
@@ -1108,34 +1238,47 @@ size_t adj_scatter_smem(int D) {
 }
 
 template <int D>
-cudaError_t adj_prepare_one() {
+cudaError_t adj_prepare_one(int *push_blocks, int *scat_blocks) {
   cudaError_t e = cudaFuncSetAttribute(k_adj_push<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_push_smem(D));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_scatter_smem(D));
+  int dev = 0, sms = 0, bp = 0, bsc = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_adj_push<D>, 256, adj_push_smem(D));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bsc, k_adj_scatter<D>, 256, adj_scatter_smem(D));
+  *push_blocks = sms * (bp < 1 ? 1 : bp);
+  *scat_blocks = sms * (bsc < 1 ? 1 : bsc);
   return e;
 }
 
-int adj_prepare(int D) {
-  cudaError_t e = D == 1 ? adj_prepare_one<1>() : (D == 2 ? adj_prepare_one<2>() : adj_prepare_one<3>());
+// kernel attributes and the resident grids of the two work-list kernels
+int adj_prepare(int D, int *push_blocks, int *scat_blocks) {
+  cudaError_t e = D == 1   ? adj_prepare_one<1>(push_blocks, scat_blocks)
+                  : D == 2 ? adj_prepare_one<2>(push_blocks, scat_blocks)
+                           : adj_prepare_one<3>(push_blocks, scat_blocks);
   return e == cudaSuccess ? 0 : -1;
 }
 
 template <int D>
-void adj_launch_all(const GridP &g, const AdjArgs &A, const ScatArgs &S, float *lamE[3], float *lamB[3],
-                    unsigned *emax, cudaStream_t s) {
-  k_adj_push<D><<<g.ntiles, 256, adj_push_smem(D), s>>>(g, A);
-  k_adj_scatter<D><<<g.ntiles, 256, adj_scatter_smem(D), s>>>(g, S);
-  k_adj_boxsum<D><<<row_blocks(g, 256), 256, 0, s>>>(g, S.box, S.occ, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1],
-                                                        lamB[2], emax);
+void adj_launch_all(const GridP &g, const AdjArgs &A, const ScatArgs &S, const AdjWork &W, const AdjBufs &b,
+                    float *lamE[3], float *lamB[3], cudaStream_t s) {
+  const int nq = g.ntiles * A.nsp;
+  k_adj_work<<<(nq + 255) / 256, 256, 0, s>>>(g, A, W, b.chunk);
+  k_adj_push<D><<<b.push_blocks, 256, adj_push_smem(D), s>>>(g, A, W);
+  k_adj_scatter<D><<<b.scat_blocks, 256, adj_scatter_smem(D), s>>>(g, S, W);
+  k_adj_fxsum<D><<<g.ntiles, 256, 0, s>>>(g, b.lfx, b.dirty, b.kst, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1],
+                                           lamB[2], b.emax, b.nwork);
 }
 
-// the particle adjoint of one step: reversed push with the position
-// derivatives of the gather (k_adj_push), the field-adjoint scatter
-// (k_adj_scatter), then the sum of the tile boxes into lamE, lamB
+// the particle adjoint of one step: the work list, the reversed push with
+// the position derivatives of the gather (k_adj_push), the field-adjoint
+// scatter (k_adj_scatter), then its sum into lamE, lamB (k_adj_fxsum)
 void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, float *const xb[], double *const acb[],
                      float *const eb[], const long long *cap, const float *const E[3], const float *const B[3],
-                     const float *const lamJ[3], float *box, unsigned char *occ, unsigned *emax, float *lamE[3],
-                     float *lamB[3], int *status, cudaStream_t s) {
+                     const float *const lamJ[3], const AdjBufs &b, float *lamE[3], float *lamB[3], int *status,
+                     cudaStream_t s) {
   AdjArgs A;
   memset(&A, 0, sizeof A);
   ScatArgs S;
@@ -1157,13 +1300,15 @@ void launch_adj_push(const GridP &g, int nsp, const SpecP *sp, const PartP *p, f
     A.B[c] = B[c];
     A.lamJ[c] = lamJ[c];
   }
-  A.emax = emax;
-  S.emax = emax;
-  S.box = box;
-  S.occ = occ;
-  if (g.D == 1) adj_launch_all<1>(g, A, S, lamE, lamB, emax, s);
-  else if (g.D == 2) adj_launch_all<2>(g, A, S, lamE, lamB, emax, s);
-  else adj_launch_all<3>(g, A, S, lamE, lamB, emax, s);
+  A.emax = b.emax;
+  S.emax = b.emax;
+  S.lfx = b.lfx;
+  S.dirty = b.dirty;
+  S.kst = b.kst;
+  AdjWork W{b.nwork, b.work, b.work_cap};
+  if (g.D == 1) adj_launch_all<1>(g, A, S, W, b, lamE, lamB, s);
+  else if (g.D == 2) adj_launch_all<2>(g, A, S, W, b, lamE, lamB, s);
+  else adj_launch_all<3>(g, A, S, W, b, lamE, lamB, s);
 }
 
 void launch_csr_sum(const int *ptr, const int *ids, int nrows, const float *xb, long long cap, int ncomp,

@@ -34,51 +34,6 @@ __device__ __forceinline__ int nbound(const GridP &g, int pat, const int c[3], i
 // stagger pattern of E_x, E_y, E_z (bit a: half cell along axis a)
 __device__ __forceinline__ int pat_e(int comp) { return 1 << comp; }
 
-// Four consecutive x cells per thread (rows hold a multiple of 8 cells, so a
-// group never straddles a row or a tile): float4 loads and stores of each
-// component, index arithmetic once per thread.
-struct Cell4 {
-  long long q;      // linear index of the group's first cell
-  int c[3];         // its coordinates
-  long long up[3];  // offset to the +1 neighbour along y, z (and x for the group's last cell)
-  long long dn[3];  // offset to the -1 neighbour along y, z (and x for the group's first cell)
-};
-
-template <int D>
-__device__ __forceinline__ bool row_cell4(const GridP &g, Cell4 &C) {
-  const int n0 = g.n[0], n4 = n0 >> 2;
-  const int chunks = (n4 + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int row = (int)blockIdx.x / chunks;
-  const int x4 = ((int)blockIdx.x - row * chunks) * (int)blockDim.x + (int)threadIdx.x;
-  if (x4 >= n4) return false;
-  C.c[0] = 4 * x4;
-  C.c[1] = D >= 2 ? row % g.n[1] : 0;
-  C.c[2] = D >= 3 ? row / g.n[1] : 0;
-  C.q = (long long)row * n0 + C.c[0];
-  // along x: the neighbour after the last cell and before the first one
-  C.up[0] = C.c[0] + 4 < n0 ? 4 : 4 - n0;
-  C.dn[0] = C.c[0] > 0 ? -1 : n0 - 1;
-  long long stride = n0;
-#pragma unroll
-  for (int a = 1; a < 3; ++a) {
-    const int n = g.n[a];
-    C.up[a] = C.c[a] + 1 < n ? stride : -stride * (n - 1);
-    C.dn[a] = C.c[a] > 0 ? -stride : stride * (n - 1);
-    stride *= n;
-  }
-  return true;
-}
-
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float el(const float4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
-__device__ __forceinline__ void set_el(float4 &v, int i, float x) {
-  if (i == 0) v.x = x;
-  else if (i == 1) v.y = x;
-  else if (i == 2) v.z = x;
-  else v.w = x;
-}
-
 // whether cell x of the group is an exterior position (open axis, half
 // stagger, last cell) or a Mur node (open axis, node stagger, first or last
 // cell) of a component with stagger pattern pat
@@ -584,12 +539,6 @@ __global__ void __launch_bounds__(Geo<D>::L0 * Geo<D>::L1 * Geo<D>::L2)
 __global__ void k_probe(const float *F, const long long *nodes, long long npts, float *buf) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
     buf[q] = F[nodes[q]];
-}
-
-// blocks of a four-cells-per-thread row launch (rows of n0 / 4 threads)
-int row_blocks4(const GridP &g, int bs) {
-  const long long rows = g.ncell / g.n[0];
-  return (int)(rows * ((g.n[0] / 4 + bs - 1) / bs));
 }
 
 int grid_blocks(long long n, int bs) {
