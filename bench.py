@@ -226,7 +226,10 @@ def run_bragg(steps, warmup):
     ctx.step(warmup)
     ctx.sync()
     stream = torch.cuda.current_stream()
-    ms, push_ms, push_n, full, quiet, launches = timed_window(ctx, steps, stream)
+    # the steps as a user runs them (graph replays), then as many with the
+    # push timed (launched directly) for the push's own time
+    ms, _, _, _, _, launches = timed_window(ctx, steps, stream, time_push=False)
+    ms_direct, push_ms, push_n, _, _, _ = timed_window(ctx, steps, stream)
     ctx.close()
     ncell = wl.n[0] * wl.n[1]
     hbm, src = peaks()
@@ -236,6 +239,7 @@ def run_bragg(steps, warmup):
             "steps": f"{warmup}..{warmup + steps}", "ms_per_step": ms / steps,
             "cell_updates_per_s": ncell * steps / (ms * 1e-3), "ion_pushes_per_s": len(sp.x) * steps / (ms * 1e-3),
             "push_ms_per_launch": push_ms / max(push_n, 1), "gpu_launches": launches,
+            "ms_per_step_launched_directly": ms_direct / steps,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "bytes_per_cell": BRAGG_BYTES_CELL, "peak_source": src,
                          "scope": "whole step (field kernels' algorithmic bytes)"}}
@@ -258,12 +262,16 @@ def run_neutral_1d(steps, warmup):
         ctx.add_laser(L.comp, L.a0, L.omega, L.theta, L.waist, L.fwhm, L.t0, L.ramp, L.phase, L.ia, L.yc, L.zc)
     ctx.step(warmup)
     ctx.sync()
-    ms, push_ms, push_n, full, quiet, launches = timed_window(ctx, steps, torch.cuda.current_stream())
+    stream = torch.cuda.current_stream()
+    ms, _, _, _, _, launches = timed_window(ctx, steps, stream, time_push=False)
+    ms_direct, push_ms, push_n, _, _, _ = timed_window(ctx, steps, stream)
     ctx.close()
     return {"workload": "neutral_1d: 2048 cells, dx=lambda/64, 16384 two-body ions, sorted deposit",
             "steps": f"{warmup}..{warmup + steps}", "ms_per_step": ms / steps,
             "ion_pushes_per_s": len(sp.x) * steps / (ms * 1e-3), "push_ms_per_launch": push_ms / max(push_n, 1),
-            "gpu_launches_per_step": launches / steps, "bound": "kernel launches (each kernel a few microseconds)"}
+            "gpu_launches_per_step": launches / steps, "ms_per_step_launched_directly": ms_direct / steps,
+            "bound": "kernel launches (a few microseconds of work per kernel): each step is two graph "
+                     "launches (the conditional re-sort, then the step's kernels)"}
 
 
 def run_adjoint_ratio(steps=400, K=20, reps=3):
@@ -345,11 +353,12 @@ def fp32_peak_tflops(sm_mhz):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
 
 
-def timed_window(ctx, steps, stream):
+def timed_window(ctx, steps, stream, time_push=True):
     """CUDA-event time of `steps` steps, with the push launches timed and
-    their work counted on the device."""
+    their work counted on the device (time_push); without push timing the
+    steps replay the library's graph of a step."""
     import torch
-    ctx.time_push(True)
+    ctx.time_push(time_push)
     launches0 = ctx.kernel_launches()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -419,6 +428,8 @@ def main():
     ap.add_argument("--late-start", type=int, default=LATE_START,
                     help="step at which the late (field-covered) window starts")
     ap.add_argument("--adjoint-reps", type=int, default=3, help="timed repetitions of each adjoint phase")
+    ap.add_argument("--small-legs-only", action="store_true",
+                    help="only the 2D Bragg crystal and 1D medium legs (one JSON line with their keys)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the 3D workload on 128x64x64 cells (profiling)")
     args = ap.parse_args()
@@ -430,6 +441,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.small_legs_only:
+        import torch
+        torch.cuda.set_device(local)
+        if rank == 0:
+            print(json.dumps({"bragg_2d": run_bragg(max(args.steps, 100), max(args.warmup, 3)),
+                              "neutral_1d": run_neutral_1d(1000, 5)}), flush=True)
+        return
+
     if args.adjoint_only:
         import torch
         torch.cuda.set_device(local)

@@ -305,10 +305,11 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->tile_n = (int *)dalloc(c, sizeof(int));
   c->status = (int *)dalloc(c, sizeof(int) * 4);
   c->work = (unsigned long long *)dalloc(c, sizeof(unsigned long long) * 2);
+  c->clk = (long long *)dalloc(c, sizeof(long long) * kClockWords);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
   if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n || !c->far_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
-      !c->work || (nf && !c->frame)) {
+      !c->work || !c->clk || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
@@ -334,6 +335,7 @@ void bp_destroy(bp_ctx *c) {
   cudaStreamSynchronize(c->stream);
   for (auto e : c->ev) cudaEventDestroy(e);
   if (c->sort_exec) cudaGraphExecDestroy(c->sort_exec);
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->read_stream) {
     cudaStreamSynchronize(c->read_stream);
@@ -753,28 +755,46 @@ bool sort_graph(bp_ctx *c) {
   return true;
 }
 
-// one leapfrog step; when snap_fields is given, E^n and B^n (after the first
-// half step) and the particle state before the push are copied there
-int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fields,
-             std::vector<bp_part_copy> *snap_parts) {
-  const GridP &g = c->g;
-  cudaStream_t st = c->stream;
-  float *E[3] = {c->F[0], c->F[1], c->F[2]}, *B[3] = {c->F[3], c->F[4], c->F[5]}, *J[3] = {c->F[6], c->F[7], c->F[8]};
-  const float *cE[3] = {E[0], E[1], E[2]}, *cB[3] = {B[0], B[1], B[2]}, *cJ[3] = {J[0], J[1], J[2]};
-  int nopen = 0;
-  for (int a = 0; a < g.D; ++a) nopen += g.bc[a] == BP_OPEN;
-  // re-sort when a particle left its tile margin in the previous step
-  if (nsp) {
-    if (sort_graph(c)) {
-      cudaGraphLaunch(c->sort_exec, st);
-      c->launches += 1;  // the condition kernel; a re-sort that ran is counted by bp_kernel_launches
-    } else {
-      for (auto &s : c->sp)
-        if (s.loaded) launch_sort(g, s.sp, s.p, c->sb, c->status, st);
-      launch_clear_sort_flag(c->status, st);
-      c->launches += nsp * sort_launches() + 1;
-    }
+// the step clock from the host's state (the step number, the probes' sample
+// counts and capacities); run before the first step of every call that steps
+void sync_clock(bp_ctx *c, cudaStream_t st) {
+  ClockState v;
+  memset(&v, 0, sizeof v);
+  v.step = c->step;
+  v.nprobe = (int)c->pr.size();
+  for (int p = 0; p < v.nprobe; ++p) {
+    v.count[p] = c->pr[p].count;
+    v.cap[p] = c->pr[p].cap;
   }
+  launch_clock_set(c->clk, v, st);
+  c->launches++;
+}
+
+// re-sort when a particle left its tile margin in the previous step
+void launch_resort(bp_ctx *c, int nsp, cudaStream_t st) {
+  if (!nsp) return;
+  if (sort_graph(c)) {
+    cudaGraphLaunch(c->sort_exec, st);
+    c->launches += 1;  // the condition kernel; a re-sort that ran is counted by bp_kernel_launches
+  } else {
+    for (auto &s : c->sp)
+      if (s.loaded) launch_sort(c->g, s.sp, s.p, c->sb, c->status, st);
+    launch_clear_sort_flag(c->status, st);
+    c->launches += nsp * sort_launches() + 1;
+  }
+}
+
+// The launches of one leapfrog step after the re-sort, on stream st.  They
+// are the same every step (the time and the probe slots come from the device
+// clock), so a plain step and a replay of their captured graph do the same
+// work.  When snap_fields is given, E^n and B^n (after the first half step)
+// and the particle state before the push are copied there; with push timing
+// on, events bracket the push.
+void step_launches(bp_ctx *c, const PushArgs &A, bool probes, cudaStream_t st, float *snap_fields,
+                   std::vector<bp_part_copy> *snap_parts) {
+  const GridP &g = c->g;
+  float *E[3] = {c->F[0], c->F[1], c->F[2]}, *B[3] = {c->F[3], c->F[4], c->F[5]}, *J[3] = {c->F[6], c->F[7], c->F[8]};
+  const float *cE[3] = {E[0], E[1], E[2]}, *cB[3] = {B[0], B[1], B[2]};
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
   if (snap_fields) {
     CopyList L;
@@ -799,25 +819,98 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
     cudaEventRecord(c->ev[c->ev_used + 1], st);
     c->ev_used += 2;
   }
-  const double th = ((double)c->step + 0.5) * g.dtd;  // the current's time level
-  if (!c->det) launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), th, st);
+  if (!c->det) launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), c->clk, st);
   launch_yee_b(g, B, cE, 0.5f * g.dt, st);
-  launch_yee_e(g, E, cB, J, c->frame, c->det ? c->jfx : nullptr, c->jinv, c->las.data(), (int)c->las.size(), th,
+  launch_yee_e(g, E, cB, J, c->frame, c->det ? c->jfx : nullptr, c->jinv, c->las.data(), (int)c->las.size(), c->clk,
                c->ant, st);
-  // quiet-tile pass, push, current sum (atomic deposit) or antenna (sorted deposit, with lasers), Yee (3), Mur
-  // (sorted: quiet pass, push, records, antenna if any, Yee (3); atomic: quiet pass, push, current sum, Yee (3))
-  c->launches += (c->det ? 6 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0);
+  if (probes)
+    for (size_t p = 0; p < c->pr.size(); ++p)
+      launch_probe(c->F[c->pr[p].comp], c->pr[p].nodes, c->pr[p].npts, c->pr[p].buf, c->clk, (int)p, st);
+  launch_clock_tick(c->clk, probes ? (int)c->pr.size() : 0, st);
+}
+
+// the host's record of one step (the device's is the clock)
+void step_account(bp_ctx *c, bool probes) {
+  int nopen = 0;
+  for (int a = 0; a < c->g.D; ++a) nopen += c->g.bc[a] == BP_OPEN;
+  // quiet-tile pass, push, records (sorted) or current sum (atomic), antenna (sorted, with lasers),
+  // Yee (3), Mur, the clock
+  c->launches += (c->det ? 6 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0) + 1;
   c->step++;
-  if (probes) {
+  if (probes)
     for (auto &p : c->pr) {
-      if (p.count < p.cap) {
-        launch_probe(c->F[p.comp], p.nodes, p.npts, p.buf, p.count, st);
-        c->launches++;
-        p.count++;
-      }
+      c->launches++;
+      if (p.count < p.cap) p.count++;
     }
-  }
+}
+
+// one leapfrog step, launched directly
+int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fields,
+             std::vector<bp_part_copy> *snap_parts) {
+  launch_resort(c, nsp, c->stream);
+  step_launches(c, A, probes, c->stream, snap_fields, snap_parts);
+  step_account(c, probes);
   return check_launch(c, "step");
+}
+
+// one step through the step graph (step_graph succeeded for the current arguments)
+int graph_step(bp_ctx *c, int nsp) {
+  launch_resort(c, nsp, c->stream);
+  cudaGraphLaunch(c->step_exec, c->stream);
+  step_account(c, true);
+  return check_launch(c, "step graph");
+}
+
+// The graph of a plain step's launches (probes recorded, no push timing, no
+// snapshots), captured on the capture stream; reused while every launch
+// argument is unchanged.  False when the runtime cannot capture or
+// instantiate it: the caller then launches the steps directly.
+bool step_graph(bp_ctx *c, const PushArgs &A) {
+  std::string key;
+  auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
+  put(&A, sizeof A);
+  put(&c->tmaps, sizeof c->tmaps);
+  put(&c->g, sizeof c->g);
+  put(c->F, sizeof c->F);
+  const void *ptrs[] = {c->jfx, c->jbox, c->occ, c->jbb, c->frame, c->ant, c->clk};
+  put(ptrs, sizeof ptrs);
+  put(&c->det, sizeof c->det);
+  put(&c->jinv, sizeof c->jinv);
+  if (!c->las.empty()) put(c->las.data(), sizeof(LaserP) * c->las.size());
+  for (auto &p : c->pr) {
+    const void *pp[] = {p.nodes, p.buf};
+    put(pp, sizeof pp);
+    put(&p.comp, sizeof p.comp);
+    put(&p.npts, sizeof p.npts);
+  }
+  if (c->step_exec && key == c->step_key) return true;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_stream = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  step_launches(c, A, true, c->cap_stream, nullptr, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    return false;
+  }
+  c->step_exec = ex;
+  c->step_key = key;
+  return true;
 }
 
 }  // namespace
@@ -826,10 +919,16 @@ extern "C" {
 
 int bp_step(bp_ctx *c, int64_t nsteps) {
   if (!c || nsteps < 0) return BP_ERR_ARG;
+  if (nsteps == 0) return BP_OK;
   int nsp = 0;
   PushArgs A = push_args(c, &nsp);
+  sync_clock(c, c->stream);
+  // two or more steps without push timing: the re-sort's graph and the step's
+  // graph per step (the kernels of a step launched by two calls)
+  const bool graph = nsteps >= 2 && !c->timing && step_graph(c, A);
   for (int64_t it = 0; it < nsteps; ++it) {
-    int rc = one_step(c, A, nsp, true, nullptr, nullptr);
+    int rc;
+    rc = graph ? graph_step(c, nsp) : one_step(c, A, nsp, true, nullptr, nullptr);
     if (rc) return rc;
   }
   return BP_OK;
@@ -1441,6 +1540,8 @@ int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
   int nsp = 0;
   PushArgs A = push_args(c, &nsp);
   cudaStream_t st = c->stream;
+  sync_clock(c, st);
+  const bool graph = !c->timing && step_graph(c, A);
   for (int k = 0; k < nseg; ++k) {
     // the state before step start + k K: E, B^{n-1/2}, particles
     CopyList L;
@@ -1451,7 +1552,7 @@ int bp_forward_ckpt(bp_ctx *c, int64_t nsteps, int K) {
     cl_flush(c, L);
     long long len = std::min<long long>(K, nsteps - (long long)k * K);
     for (long long j = 0; j < len; ++j) {
-      int rc = one_step(c, A, nsp, true, nullptr, nullptr);
+      int rc = graph ? graph_step(c, nsp) : one_step(c, A, nsp, true, nullptr, nullptr);
       if (rc) return rc;
     }
   }
@@ -1589,6 +1690,7 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
     const long long base = (long long)seg * K;
     const long long len = std::min<long long>(K, ad.nsteps - base);
     c->step = ad.start + base;
+    sync_clock(c, st);
     for (long long j = 0; j < len; ++j) {
       int rc = one_step(c, A, nsp, false, ad.st_fields[bank * K + j], &ad.st_parts[bank * K + j]);
       if (rc) return rc;

@@ -123,4 +123,10 @@ struct bp_ctx {
   int *sort_runs = nullptr;      // host-mapped counter of re-sorts that ran
   int *sort_runs_dev = nullptr;
   int sort_nsp = 0;              // species in the graph's sort pipeline
+  // the step clock (device; see kClockWords) and the graph of a step's
+  // launches after the re-sort, with the launch arguments it was captured
+  // with (rebuilt when any of them changes)
+  long long *clk = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  std::string step_key;
 };

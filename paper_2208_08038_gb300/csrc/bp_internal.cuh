@@ -428,13 +428,24 @@ void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s)
 // written to J, and the accumulator cleared;
 // without it J is read as the current sum left it.
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
-                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, double t, double *ant,
-                  cudaStream_t s);
+                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, const long long *clk,
+                  double *ant, cudaStream_t s);
 long long frame_floats(const GridP &g);
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
-                 const LaserP *las, int nlas, double t, cudaStream_t s);
-void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,
+                 const LaserP *las, int nlas, const long long *clk, cudaStream_t s);
+// the step clock (device): [0] step number, [1 + p] probe p's samples,
+// [1 + BP_MAX_PROBE + p] its capacity; read by the antenna, the current sum
+// and the probes, so that one captured step serves every step
+constexpr int kClockWords = 1 + 2 * BP_MAX_PROBE;
+struct ClockState {
+  long long step;
+  int nprobe;
+  long long count[BP_MAX_PROBE], cap[BP_MAX_PROBE];
+};
+void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, const long long *clk, int p,
                   cudaStream_t s);
+void launch_clock_tick(long long *clk, int nprobe, cudaStream_t s);
+void launch_clock_set(long long *clk, const ClockState &v, cudaStream_t s);
 
 struct SortBufs {
   int *hist;       // [ncell + 1]

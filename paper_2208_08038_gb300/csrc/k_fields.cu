@@ -163,10 +163,21 @@ __device__ __forceinline__ float fx_to_float(long long v, float s) {
   return fmaf(a, 16777216.0f * s, b * s);
 }
 
-// the antenna sheets' current at time t on their planes, FP64: ant[s][y + ny z]
-// for laser s (the value the current sum adds at cell (L.ia, y, z))
+// The step clock in device memory, so that a step's launches are the same
+// every step (one CUDA graph replayed): clk[0] the step number n,
+// clk[1 + p] probe p's samples so far, clk[1 + BP_MAX_PROBE + p] its
+// capacity.  The current J^{n+1/2} and the antenna's sheet take time
+// (n + 1/2) dt.
+__device__ __forceinline__ double current_time(const GridP &g, const long long *clk) {
+  return ((double)clk[0] + 0.5) * g.dtd;
+}
+
+// the antenna sheets' current on their planes at the current's time, FP64:
+// ant[s][y + ny z] for laser s (the value the current sum adds at cell
+// (L.ia, y, z))
 template <int D>
-__global__ void k_antenna(GridP g, LaserSet las, double t, double *ant) {
+__global__ void k_antenna(GridP g, LaserSet las, const long long *clk, double *ant) {
+  const double t = current_time(g, clk);
   const long long nyz = g.ncell / g.n[0];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < las.n * nyz;
        q += (long long)gridDim.x * blockDim.x) {
@@ -402,9 +413,10 @@ __global__ void k_mur(GridP g, float *Ex, float *Ey, float *Ez, const float *fra
 template <int D>
 __global__ void __launch_bounds__(256) k_jsum(GridP g, const float *__restrict__ jbox,
                                               const unsigned char *__restrict__ occ, const uint2 *__restrict__ jbb,
-                                              float *Jx, float *Jy, float *Jz, LaserSet las, double t) {
+                                              float *Jx, float *Jy, float *Jz, LaserSet las, const long long *clk) {
   Cell C;
   if (!row_cell<D>(g, C)) return;
+  const double t = current_time(g, clk);
   const int *c = C.c;
   // the (up to three per axis) tiles whose boxes cover the cell, ascending
   int tw[3][3], loc[3][3], nc[3];
@@ -473,8 +485,9 @@ __global__ void __launch_bounds__(256) k_jsum(GridP g, const float *__restrict__
 template <int D>
 __global__ void __launch_bounds__(Geo<D>::L0 * Geo<D>::L1 * Geo<D>::L2)
     k_jsum_tile(GridP g, const float *__restrict__ jbox, const unsigned char *__restrict__ occ,
-                const uint2 *__restrict__ jbb, float *Jx, float *Jy, float *Jz, LaserSet las, double t) {
+                const uint2 *__restrict__ jbb, float *Jx, float *Jy, float *Jz, LaserSet las, const long long *clk) {
   static_assert(D >= 2, "tile form for 2D and 3D");
+  const double t = current_time(g, clk);
   constexpr int L0 = Geo<D>::L0, L1 = Geo<D>::L1, L2 = Geo<D>::L2;
   constexpr int NC = D == 3 ? 27 : 9;
   __shared__ int ctile[NC], corg[NC][3];
@@ -536,9 +549,31 @@ __global__ void __launch_bounds__(Geo<D>::L0 * Geo<D>::L1 * Geo<D>::L2)
   Jz[q] = sz;
 }
 
-__global__ void k_probe(const float *F, const long long *nodes, long long npts, float *buf) {
+// probe p's sample of this step into its next slot, while it has room
+__global__ void k_probe(const float *F, const long long *nodes, long long npts, float *buf, const long long *clk,
+                        int p) {
+  const long long slot = clk[1 + p];
+  if (slot >= clk[1 + BP_MAX_PROBE + p]) return;
+  float *out = buf + slot * npts;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
-    buf[q] = F[nodes[q]];
+    out[q] = F[nodes[q]];
+}
+
+// the end of a step: the clock advances, and the sample count of each of
+// the first nprobe probes (those recorded this step) while it has room
+__global__ void k_clock_tick(long long *clk, int nprobe) {
+  if (threadIdx.x == 0) clk[0] += 1;
+  if ((int)threadIdx.x < nprobe && clk[1 + threadIdx.x] < clk[1 + BP_MAX_PROBE + threadIdx.x]) clk[1 + threadIdx.x] += 1;
+}
+
+// the clock set from the host's state
+__global__ void k_clock_set(long long *clk, ClockState v) {
+  const int i = threadIdx.x;
+  if (i == 0) clk[0] = v.step;
+  if (i < BP_MAX_PROBE) {
+    clk[1 + i] = i < v.nprobe ? v.count[i] : 0;
+    clk[1 + BP_MAX_PROBE + i] = i < v.nprobe ? v.cap[i] : 0;
+  }
 }
 
 int grid_blocks(long long n, int bs) {
@@ -564,8 +599,8 @@ void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], fl
 }
 
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
-                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, double t, double *ant,
-                  cudaStream_t s) {
+                  unsigned long long *jfx, float jinv, const LaserP *las, int nlas, const long long *clk,
+                  double *ant, cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
   const int nb = row_blocks4(g, 128);
@@ -583,9 +618,9 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
     const LaserSet ls = make_laser_set(las, nlas);
     const long long nant = (long long)nlas * (g.ncell / g.n[0]);
     // small blocks: the FP64 exp / sin of the antenna planes spread over many SMs
-    if (g.D == 1) k_antenna<1><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
-    else if (g.D == 2) k_antenna<2><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
-    else k_antenna<3><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, t, ant);
+    if (g.D == 1) k_antenna<1><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, clk, ant);
+    else if (g.D == 2) k_antenna<2><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, clk, ant);
+    else k_antenna<3><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, clk, ant);
   }
 #define YEE_E(DD, FF) \
   k_yee_e<DD, FF><<<nb, 128, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
@@ -617,16 +652,16 @@ void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s)
 }
 
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
-                 const LaserP *las, int nlas, double t, cudaStream_t s) {
+                 const LaserP *las, int nlas, const long long *clk, cudaStream_t s) {
   const LaserSet ls = make_laser_set(las, nlas);
   if (g.D == 1) {
-    k_jsum<1><<<row_blocks(g, 256), 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+    k_jsum<1><<<row_blocks(g, 256), 256, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, clk);
   } else if (g.D == 2) {
     constexpr int nt = Geo<2>::L0 * Geo<2>::L1 * Geo<2>::L2;
-    k_jsum_tile<2><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+    k_jsum_tile<2><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, clk);
   } else {
     constexpr int nt = Geo<3>::L0 * Geo<3>::L1 * Geo<3>::L2;
-    k_jsum_tile<3><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, t);
+    k_jsum_tile<3><<<g.ntiles, nt, 0, s>>>(g, jbox, occ, jbb, J[0], J[1], J[2], ls, clk);
   }
 }
 
@@ -653,7 +688,13 @@ void launch_copy_many(const CopyList &L, cudaStream_t s) {
   k_copy_many<<<dim3((unsigned)bx, (unsigned)L.n), 256, 0, s>>>(L);
 }
 
-void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, long long slot,
+void launch_probe(const float *F, const long long *nodes, long long npts, float *buf, const long long *clk, int p,
                   cudaStream_t s) {
-  k_probe<<<grid_blocks(npts, 256), 256, 0, s>>>(F, nodes, npts, buf + slot * npts);
+  k_probe<<<grid_blocks(npts, 256), 256, 0, s>>>(F, nodes, npts, buf, clk, p);
+}
+
+void launch_clock_tick(long long *clk, int nprobe, cudaStream_t s) { k_clock_tick<<<1, 32, 0, s>>>(clk, nprobe); }
+
+void launch_clock_set(long long *clk, const ClockState &v, cudaStream_t s) {
+  k_clock_set<<<1, BP_MAX_PROBE, 0, s>>>(clk, v);
 }
