@@ -336,14 +336,14 @@ def run_adjoint_ratio(steps=400, K=20, reps=3):
                            "backward (segment recompute + reverse steps) / plain forward"}
 
 
-def our_config(n_ion, mode, world, warmup, steps):
-    return {"workload": "neutral_3d: 512x256x256 cells, dx=lambda/16, 8 two-body ions/cell "
+def our_config(n_ion, mode, world, warmup, steps, n=(512, 256, 256)):
+    return {"workload": f"neutral_3d: {n[0]}x{n[1]}x{n[2]} cells, dx=lambda/16, 8 two-body ions/cell "
                         f"({n_ion} ions), thermal sigma=1e-3, omega_b=3, a0=1e-3 pulse, {mode} deposit",
             "timed": f"steps {warmup}..{warmup + steps} of the 500-step run from t=0: the quiet start (the "
                      "field has reached only the tiles near the antenna; the co-moving neutral ions ahead of "
                      "it are drifted by the quiet-tile pass without gather or deposit); the field-covered "
                      f"regime is timed separately from step {LATE_START} (key 'late')",
-            "l2": "inputs larger than L2 (particles 13.7 GB)", "parallelism": f"replicas x{world}"}
+            "l2": f"inputs larger than L2 (particles {n_ion * 52 / 1e9:.3g} GB)", "parallelism": f"replicas x{world}"}
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -535,7 +535,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": our_config(n_ion, args.mode, world, args.warmup, args.steps),
+        "config": our_config(n_ion, args.mode, world, args.warmup, args.steps, wl.n),
         "push_ms_per_launch": push_avg0,
         "push_work_per_launch": {"full": full0 / max(push_n, 1), "quiet": quiet0 / max(push_n, 1)},
         "late": {"steps": f"{done}..{done + late_steps}", "ms_per_step": lms_job / late_steps,

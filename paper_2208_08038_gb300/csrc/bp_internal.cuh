@@ -67,13 +67,17 @@ struct Box {
                        J2 = D >= 3 ? Geo<D>::L2 + 2 * M + 7 : 1;
   static constexpr int OG = M + 2, OJ = M + 3;
   // Shared-memory layout, x fastest.  The field box of a 3D tile is the
-  // image of one TMA box load per component: rows of GR = 16 floats (64
-  // bytes, the box's inner extent) whose first float lies SX = 1 cell before
-  // the box origin T0 - OG, so that the load starts at x = T0 - 4, a multiple
-  // of 4 floats (16 bytes); planes of GR * G1 floats; each component's
-  // stride rounded up to 32 floats (128 bytes).  1D/2D: rows of G0 floats.
-  // The current box: row stride J0, padded plane stride.
-  static constexpr int GR = D >= 3 ? 16 : G0, SX = D >= 3 ? 1 : 0;
+  // image of one TMA box load per component: rows of GR = 20 floats (80
+  // bytes, the box's inner extent; the box's 15 x cells need 16, the other 4
+  // are loaded and not read) whose first float lies SX = 1 cell before the
+  // box origin T0 - OG, so that the load starts at x = T0 - 4, a multiple of
+  // 4 floats (16 bytes); planes of GR * G1 = 300 floats; each component's
+  // stride rounded up to 32 floats (128 bytes).  A row of 20 words puts rows
+  // y and y + 1 .. y + 7 in banks 20, 8, 28, ... words apart (a 16-word row
+  // put row y + 2 in the same banks and doubled the gather's shared-load
+  // bank conflicts).  1D/2D: rows of G0 floats.  The current box: row stride
+  // J0, padded plane stride.
+  static constexpr int GR = D >= 3 ? 20 : G0, SX = D >= 3 ? 1 : 0;
   static constexpr int GP = GR * G1;
   static constexpr int JP = D >= 3 ? pad_plane(J0 * J1) : J0 * J1;
   static constexpr int GCELLS = D >= 3 ? (GP * G2 + 31) / 32 * 32 : GP * G2, JCELLS = JP * J2;

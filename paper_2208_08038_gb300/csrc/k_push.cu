@@ -1044,70 +1044,80 @@ __device__ __forceinline__ void zero_box(JT *J, int n, int tid, int bs) {
 constexpr unsigned char QS_PUSH = 0, QS_DONE = 1, QS_REST = 2;
 
 template <int D>
-__global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A) {
+__global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A, int qt) {
   static_assert(Box<D>::OG <= Geo<D>::L0 && Box<D>::G0 - Box<D>::OG <= 2 * Geo<D>::L0 &&
                     (D < 2 || (Box<D>::OG <= Geo<D>::L1 && Box<D>::G1 - Box<D>::OG <= 2 * Geo<D>::L1)) &&
                     (D < 3 || (Box<D>::OG <= Geo<D>::L2 && Box<D>::G2 - Box<D>::OG <= 2 * Geo<D>::L2)),
                 "field box within the neighbouring tiles");
   constexpr int QB = 2;  // particles in flight per thread (measured best of 1, 2, 4, 8)
-  const int t = blockIdx.x;
-  const int tid = threadIdx.x, bs = blockDim.x;
-  int tc[3];
-  tc[0] = t % g.nt[0];
-  tc[1] = (t / g.nt[0]) % g.nt[1];
-  tc[2] = t / (g.nt[0] * g.nt[1]);
-  bool marked = false;
-  if (tid < 27) {
-    const int o[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
-    bool use = true;
-    int nb[3];
+  // qt (1 to 4) tiles per block: one warp classifies each, then the whole
+  // block drifts the quiet ones in turn (several tiles per block on grids
+  // with many tiles, where a block per tile spent its time waiting on the
+  // classification loads; one on small grids, where tiles in turn would
+  // lengthen the pass)
+  __shared__ int quiet[4], nquiet;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int t = (int)blockIdx.x * qt + warp;
+  if (tid == 0) nquiet = 0;
+  bool marked = false, occupied = false;
+  if (warp < qt && t < g.ntiles) {
+    const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+    if (lane < 27) {
+      const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      bool use = true;
+      int nb[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      nb[a] = tc[a] + o[a];
-      if (a >= D) use &= o[a] == 0;
-      else if (g.bc[a] == BP_PERIODIC) nb[a] = wrap_once(nb[a], g.nt[a]);
-      else use &= nb[a] >= 0 && nb[a] < g.nt[a];
+      for (int a = 0; a < 3; ++a) {
+        nb[a] = tc[a] + o[a];
+        if (a >= D) use &= o[a] == 0;
+        else if (g.bc[a] == BP_PERIODIC) nb[a] = wrap_once(nb[a], g.nt[a]);
+        else use &= nb[a] >= 0 && nb[a] < g.nt[a];
+      }
+      if (use) marked = g.fnz[nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2])] != 0;
     }
-    if (use) marked = g.fnz[nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2])] != 0;
+    // a tile without particles has nothing to push or deposit, whatever its
+    // fields: done here, so the push neither stages its fields nor visits it
+    if (lane < A.nsp) occupied = A.p[lane].tstart[t + 1] > A.p[lane].tstart[t];
   }
-  // a tile without particles has nothing to push or deposit, whatever its
-  // fields: done here, so the push neither stages its fields nor visits it
-  bool occupied = false;
-  if (tid < A.nsp) occupied = A.p[tid].tstart[t + 1] > A.p[tid].tstart[t];
-  const bool any_marked = __syncthreads_or(marked);
-  if (!__syncthreads_or(occupied)) {
-    if (tid == 0) {
+  marked = __any_sync(0xFFFFFFFFu, marked);
+  occupied = __any_sync(0xFFFFFFFFu, occupied);
+  __syncthreads();  // nquiet cleared
+  if (warp < qt && t < g.ntiles && lane == 0) {
+    if (!occupied) {
       A.qstate[t] = QS_DONE;
       A.occ[t] = 0;
-    }
-    return;
-  }
-  if (any_marked) {
-    if (tid == 0) {
+    } else if (marked) {
       A.qstate[t] = QS_PUSH;
       A.tile_list[atomicAdd(A.tile_n, 1)] = t;
-    }
-    return;
-  }
-  const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
-  bool left = false;
-  unsigned moved = 0;
-  for (int s = 0; s < A.nsp; ++s) {
-    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
-    if (A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2) {
-      for (long long i0 = beg + tid; i0 < end; i0 += (long long)QB * bs)
-        left |= quiet_batch<D, QB>(g, A.p[s], i0, bs, end, T0, A.status, moved);
     } else {
-      left |= end > beg;
+      quiet[atomicAdd(&nquiet, 1)] = t;  // each quiet tile is drifted alone: their order changes nothing
+    }
+  }
+  __syncthreads();
+  const int nq = nquiet;
+  unsigned moved = 0;
+  for (int k = 0; k < nq; ++k) {
+    const int tq = quiet[k];
+    const int T0[3] = {(tq % g.nt[0]) * Geo<D>::L0, ((tq / g.nt[0]) % g.nt[1]) * Geo<D>::L1,
+                       (tq / (g.nt[0] * g.nt[1])) * Geo<D>::L2};
+    bool left = false;
+    for (int s = 0; s < A.nsp; ++s) {
+      const int beg = A.p[s].tstart[tq], end = A.p[s].tstart[tq + 1];
+      if (A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2) {
+        for (long long i0 = beg + tid; i0 < end; i0 += (long long)QB * bs)
+          left |= quiet_batch<D, QB>(g, A.p[s], i0, bs, end, T0, A.status, moved);
+      } else {
+        left |= end > beg;
+      }
+    }
+    left = __syncthreads_or(left);
+    if (tid == 0) {
+      A.qstate[tq] = left ? QS_REST : QS_DONE;
+      if (!left) A.occ[tq] = 0;
+      else A.tile_list[atomicAdd(A.tile_n, 1)] = tq;
     }
   }
   if (A.work) count_work(A.work + 1, moved);
-  left = __syncthreads_or(left);
-  if (tid == 0) {
-    A.qstate[t] = left ? QS_REST : QS_DONE;
-    if (!left) A.occ[t] = 0;
-    else A.tile_list[atomicAdd(A.tile_n, 1)] = t;
-  }
 }
 
 // byte offset of the field box in the push's dynamic shared memory (after the
@@ -1470,7 +1480,8 @@ __global__ void __launch_bounds__(128) k_push_far(GridP g, PushArgs A) {
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s) {
   cudaMemsetAsync(a.tile_n, 0, sizeof(int), s);
-  k_push_quiet<D><<<g.ntiles, 128, 0, s>>>(g, a);
+  const int qt = g.ntiles >= 2048 ? 4 : 1;  // tiles per quiet-pass block
+  k_push_quiet<D><<<(g.ntiles + qt - 1) / qt, 128, 0, s>>>(g, a, qt);
   const size_t smem = push_smem_bytes(g, DET);
   // as many persistent blocks as the device holds at once (worked out per
   // context for its grid and device when it was created)
