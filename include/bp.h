@@ -143,7 +143,14 @@ int bp_add_species(bp_ctx *ctx, const bp_species_desc *desc, int *species_id);
  * param_idx [n] (NULL: all 0).  Two-body ions get the initial conditions of
  * Sec. 2: r1 = r2 = x, p1 + p2 = p_c, q1 v1 + q2 v2 = 0 (u1 = u2 = u for
  * neutral ions; non-relativistic split otherwise).  Particles are then
- * sorted by tile.  May be called once per species. */
+ * sorted by tile.  May be called once per species.  The arrays stay the
+ * caller's and are not kept: page-locked arrays the device can address
+ * (pinned or registered host memory) are read in place by the conversion
+ * kernel; other host memory is copied through a device staging buffer.
+ * Returns when the particles are on the device.  BP_ERR_NONFINITE for a
+ * non-finite position or momentum, BP_ERR_DOMAIN for a position outside an
+ * open grid or a param_idx out of range (the species then stays unloaded
+ * and may be loaded again). */
 int bp_load_particles(bp_ctx *ctx, int species_id, const double *x, const double *u,
                       const int32_t *param_idx, int64_t n);
 

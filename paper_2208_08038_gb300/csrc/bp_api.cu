@@ -64,6 +64,17 @@ void dfree(bp_ctx *c, void *p) {
   else cudaFree(p);
 }
 
+// the device address of a host pointer into page-locked memory mapped for
+// the device (pinned or registered), else nullptr
+const void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int check_launch(bp_ctx *c, const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, what);
@@ -457,9 +468,11 @@ int bp_set_lattice(bp_ctx *c, int sid, const double *sites, int64_t n_sites, int
   int rc = alloc_particles(c, s, n, site_param != nullptr);
   if (rc) return rc;
   s.has_pidx = site_param != nullptr;
-  s.pidx_host.assign((size_t)n, 0);
-  if (site_param)
+  s.pidx_host.clear();
+  if (site_param) {
+    s.pidx_host.resize((size_t)n);
     for (long long q = 0; q < n; ++q) s.pidx_host[q] = site_param[q / per_site];
+  }
   cudaStream_t st = c->stream;
   const long long chunk = std::min<long long>(std::max<long long>(n, 1), 1LL << 25);
   const size_t rows = (size_t)chunk * (sizeof(double) * (D + 3) + sizeof(int));
@@ -500,16 +513,32 @@ int bp_load_particles(bp_ctx *c, int sid, const double *x, const double *u, cons
   if (rc) return rc;
   s.has_pidx = pidx != nullptr;
   if (pidx) s.pidx_host.assign(pidx, pidx + n);
-  else s.pidx_host.assign((size_t)n, 0);
+  else s.pidx_host.clear();  // all 0
   cudaStream_t st = c->stream;
-  // the caller's arrays are staged on the device in chunks and converted there
   const long long chunk = std::min<long long>(std::max<long long>(n, 1), 1LL << 25);
+  int zero = 0;
+  // Arrays in page-locked host memory that the device can address (pinned
+  // or registered, e.g. torch's pin_memory()): the conversion kernel reads
+  // them where they are, over the host link, with no staging copy.
+  // Otherwise they are copied to a device staging buffer chunk by chunk.
+  const void *dx = mapped_host(x), *du = u ? mapped_host(u) : nullptr, *dp = pidx ? mapped_host(pidx) : nullptr;
+  if (dx && (!u || du) && (!pidx || dp)) {
+    cudaMemcpyAsync(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    for (long long b = 0; b < n; b += chunk) {
+      const long long k = std::min(chunk, n - b);
+      launch_load_convert(g, s.sp, s.p, static_cast<const double *>(dx) + b * D,
+                          u ? static_cast<const double *>(du) + b * 3 : nullptr,
+                          pidx ? static_cast<const int *>(dp) + b : nullptr, b, k, c->status, st);
+      c->launches++;
+    }
+    if ((rc = check_launch(c, "load conversion"))) return rc;
+    return finish_load(c, s, n, nullptr);
+  }
   char *stage = (char *)dalloc(c, (size_t)chunk * (sizeof(double) * (D + 3) + sizeof(int)));
   if (!stage) return fail(c, BP_ERR_OOM, "load staging");
   double *sx = (double *)stage;
   double *su = sx + (size_t)chunk * D;
   int *sp_ = (int *)(su + (size_t)chunk * 3);
-  int zero = 0;
   cudaMemcpyAsync(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
   for (long long b = 0; b < n; b += chunk) {
     long long k = std::min(chunk, n - b);
@@ -543,7 +572,7 @@ int bp_set_medium(bp_ctx *c, int sid, const int64_t lo[3], const int64_t hi[3], 
   if (n >= (1LL << 31) - 1) return fail(c, BP_ERR_ARG, "too many particles");
   int rc = alloc_particles(c, s, n, false);
   if (rc) return rc;
-  s.pidx_host.assign((size_t)n, 0);
+  s.pidx_host.clear();  // all 0
   launch_gen_medium(g, s.sp, s.p, l, h, ppc, seed, sigma_u, 0, n, c->stream);
   c->launches++;
   if ((rc = check_launch(c, "medium generation"))) return rc;
@@ -1293,7 +1322,14 @@ int bp_save(bp_ctx *c, const char *path) {
         ok = ok && wr_dev(f, s.p.r + a * pc, sizeof(float) * cnt) && wr_dev(f, s.p.u2 + a * pc, sizeof(float) * cnt);
     if (s.p.pidx) ok = ok && wr_dev(f, s.p.pidx, sizeof(int) * cnt);
     ok = ok && wr_dev(f, s.p.tstart, sizeof(int) * (g.ntiles + 1));
-    ok = ok && wr(f, s.pidx_host.data(), sizeof(int) * s.pidx_host.size());
+    if (!s.pidx_host.empty()) {
+      ok = ok && wr(f, s.pidx_host.data(), sizeof(int) * s.pidx_host.size());
+    } else {
+      // no parameter indices: n zeros (the file holds one index per particle)
+      const std::vector<int> zeros(1 << 16, 0);
+      for (long long q = 0; ok && q < s.n; q += (long long)zeros.size())
+        ok = wr(f, zeros.data(), sizeof(int) * (size_t)std::min<long long>((long long)zeros.size(), s.n - q));
+    }
   }
   for (int k = 0; k < 6; ++k) ok = ok && wr_dev(f, c->F[k], sizeof(float) * g.ncell);
   ok = ok && wr_dev(f, c->status, sizeof(int));
@@ -1353,6 +1389,7 @@ int bp_load(bp_ctx *c, const char *path) {
     ok = ok && rd_dev(f, s.p.tstart, sizeof(int) * (g.ntiles + 1));
     s.pidx_host.assign((size_t)q.n, 0);
     ok = ok && rd(f, s.pidx_host.data(), sizeof(int) * (size_t)q.n);
+    if (!q.has_pidx) s.pidx_host.clear();  // all 0
     if (!ok) return bad(BP_ERR_IO, "truncated particle arrays");
     s.n = q.n;
     s.has_pidx = q.has_pidx != 0;
@@ -1781,10 +1818,13 @@ int bp_backward(bp_ctx *c, int probe_id, const float *dl_dprobe, int sid, double
   if (!dptr || !dids || !dout || !dscale) return fail(c, BP_ERR_OOM, "reduction buffers");
   int rc = BP_OK;
   if (grad_omega && S.sp.kind == BP_TWO_BODY) {
+    std::vector<int> zeros;
+    if (S.pidx_host.empty()) zeros.assign((size_t)n, 0);  // no parameter indices: all 0
+    const int *key = S.pidx_host.empty() ? zeros.data() : S.pidx_host.data();
     for (long long i = 0; i < n; ++i)
-      if (S.pidx_host[i] < 0 || S.pidx_host[i] >= S.sp.nac) rc = BP_ERR_STATE;
+      if (key[i] < 0 || key[i] >= S.sp.nac) rc = BP_ERR_STATE;
     if (!rc) {
-      build_csr(S.pidx_host.data(), S.sp.nac);
+      build_csr(key, S.sp.nac);
       // a_c = (|q1 q2| kappa / (m_r w^2))^{1/3}: d a_c / d w = -2 a_c / (3 w)
       std::vector<double> scale(S.sp.nac);
       const double mr = S.sp.m1d * S.sp.m2d / (S.sp.m1d + S.sp.m2d);

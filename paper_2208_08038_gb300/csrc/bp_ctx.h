@@ -12,7 +12,7 @@ struct bp_species_state {
   bool loaded = false;
   bool has_pidx = false;
   std::vector<double> omega;
-  std::vector<int> pidx_host;  // parameter index per particle, load order
+  std::vector<int> pidx_host;  // parameter index per particle, load order (empty: all 0)
   float *ac_dev = nullptr;
 };
 

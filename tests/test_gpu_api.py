@@ -199,6 +199,52 @@ def test_nonfinite_particles_are_rejected_at_load():
         ctx.close()
 
 
+def _load_pinned(B, ctx, sid, x, u, pidx=None):
+    """bp_load_particles from page-locked host arrays (read in place by the
+    conversion kernel) instead of the binding's pageable copies (staged)."""
+    import torch
+    xh = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).pin_memory()
+    uh = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float64)).pin_memory()
+    ph = None if pidx is None else torch.from_numpy(np.ascontiguousarray(pidx, dtype=np.int32)).pin_memory()
+    rc = B.lib().bp_load_particles(ctx._h, sid, B._ptr(xh.data_ptr()), B._ptr(uh.data_ptr()),
+                                   None if ph is None else B._ptr(ph.data_ptr()), len(x))
+    ctx._check(rc, "bp_load_particles")
+
+
+def test_pinned_and_pageable_loads_give_the_same_state():
+    """Both load paths (pinned arrays read in place; pageable arrays staged
+    on the device) give the same particles, bit for bit, with and without
+    parameter indices, and reject a non-finite position the same way."""
+    from paper_2208_08038_gb300 import binding as B
+    wl = small_periodic_3d()
+    sp = wl.species[0]
+    rng = np.random.default_rng(11)
+    pidx = rng.integers(0, 1, len(sp.x)).astype(np.int32)
+    for idx in (None, pidx):
+        out = []
+        for pinned in (False, True):
+            ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+            sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+            if pinned:
+                _load_pinned(B, ctx, sid, sp.x, sp.u, idx)
+            else:
+                ctx.load_particles(sid, sp.x, sp.u, idx)
+            ctx.step(2)
+            ctx.sync()
+            out.append((np.concatenate(ctx.read_particles(sid, len(sp.x)), axis=1), ctx.fields()))
+            ctx.close()
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1])
+    ctx = B.Context(wl.D, wl.n, wl.dx, wl.dt, wl.bc, deposit_mode=1, tile=wl.tile)
+    sid = ctx.add_two_body(sp.Zb, sp.qc, sp.mc, sp.w, sp.lambda0_m, sp.omega_b)
+    x = sp.x.copy()
+    x[len(x) // 2, 0] = np.inf
+    with pytest.raises(B.BPError) as e:
+        _load_pinned(B, ctx, sid, x, sp.u)
+    assert e.value.code == B.BP_ERR_NONFINITE
+    ctx.close()
+
+
 class _BudgetAllocator:
     """A bp_allocator that hands out torch caching-allocator blocks until a
     byte budget is spent, then returns NULL (a caller out of memory)."""
