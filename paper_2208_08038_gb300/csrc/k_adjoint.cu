@@ -879,7 +879,9 @@ __global__ void k_adj_work(GridP g, AdjArgs A, AdjWork W, int chunk) {
     W.item[at + k] = make_int4(t, s, beg + k * chunk, min(beg + (k + 1) * chunk, end));
 }
 
-// the staged boxes of tile t: E^n, B^n (gather box) and the J adjoint
+// The staged boxes of tile t: E^n, B^n (gather box) and the J adjoint, as
+// per-thread asynchronous 4-byte copies (zero fill outside open faces),
+// completed by cp.async.wait_all; T0 receives the tile's first cell.
 template <int D>
 __device__ __forceinline__ void adj_stage(const GridP &g, const AdjArgs &A, int t, int T0[3], float *Gsm, float *Jl) {
   using BX = Box<D>;
@@ -889,6 +891,7 @@ __device__ __forceinline__ void adj_stage(const GridP &g, const AdjArgs &A, int 
   T0[0] = tc[0] * Geo<D>::L0;
   T0[1] = tc[1] * Geo<D>::L1;
   T0[2] = tc[2] * Geo<D>::L2;
+  const unsigned gbase = (unsigned)__cvta_generic_to_shared(Gsm), jbase = (unsigned)__cvta_generic_to_shared(Jl);
   for (int q = tid; q < BX::GCOMP; q += bs) {
     int bidx[3] = {q % BX::G0, (q / BX::G0) % BX::G1, q / (BX::G0 * BX::G1)};
     const int si = BX::gi(bidx[0], bidx[1], bidx[2]);
@@ -904,10 +907,14 @@ __device__ __forceinline__ void adj_stage(const GridP &g, const AdjArgs &A, int 
       gi += (long long)x * stride;
       stride *= g.n[a];
     }
+    if (!ok) gi = 0;  // a zero fill: nothing is read
+    const unsigned src = ok ? 4u : 0u;
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      Gsm[cc * GC + si] = ok ? A.E[cc][gi] : 0.0f;
-      Gsm[(3 + cc) * GC + si] = ok ? A.B[cc][gi] : 0.0f;
+    for (int cc = 0; cc < 6; ++cc) {
+      const float *gp = (cc < 3 ? A.E[cc] : A.B[cc - 3]) + gi;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(gbase + 4u * (unsigned)(cc * GC + si)),
+                   "l"(gp), "r"(src)
+                   : "memory");
     }
   }
   for (int q = tid; q < BX::JCOMP; q += bs) {
@@ -925,34 +932,64 @@ __device__ __forceinline__ void adj_stage(const GridP &g, const AdjArgs &A, int 
       gi += (long long)x * stride;
       stride *= g.n[a];
     }
+    if (!ok) gi = 0;
+    const unsigned src = ok ? 4u : 0u;
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) Jl[cc * JC + si] = ok ? A.lamJ[cc][gi] : 0.0f;
+    for (int cc = 0; cc < 3; ++cc)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(jbase + 4u * (unsigned)(cc * JC + si)),
+                   "l"(A.lamJ[cc] + gi), "r"(src)
+                   : "memory");
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// the reversed push of the step's work items; a block restages its boxes
-// only when the tile changes
+// box sets of the reversed push in shared memory: two in 1D and 2D (the next
+// work item's boxes are staged while the current item is processed), one in
+// 3D (a set fills most of the shared memory)
+__host__ __device__ constexpr int adj_push_bufs(int D) { return D == 3 ? 1 : 2; }
+template <int D>
+__host__ __device__ constexpr int adj_box_floats() {
+  return 6 * Box<D>::GCELLS + 3 * Box<D>::JCELLS;
+}
+
+// the reversed push of the step's work items, round-robin over the
+// resident blocks
 template <int D>
 __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjArgs A, AdjWork W) {
   using BX = Box<D>;
-  constexpr int GC = BX::GCELLS;
+  constexpr int GC = BX::GCELLS, NB = adj_push_bufs(D), BOX = adj_box_floats<D>();
   extern __shared__ __align__(16) unsigned char smem[];
-  float *Gsm = reinterpret_cast<float *>(smem);  // E^n, B^n
-  float *Jl = Gsm + 6 * GC;                      // adjoint of J
+  float *buf = reinterpret_cast<float *>(smem);  // NB x [E^n, B^n (6 GC) | J adjoint (3 JC)]
   const int tid = threadIdx.x, bs = blockDim.x;
   const int nw = min(*W.n, W.cap);
-  int staged = -1, T0[3] = {0, 0, 0};
   float emax = 0.0f;
-  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-    const int4 it = W.item[w];
-    if (it.x != staged) {
-      __syncthreads();  // every thread is done with the previous boxes
-      adj_stage<D>(g, A, it.x, T0, Gsm, Jl);
-      staged = it.x;
-      __syncthreads();
+  int w = blockIdx.x, cur = 0, T0[3], Tn[3];
+  if (w < nw) {
+    int4 it = W.item[w];
+    adj_stage<D>(g, A, it.x, T0, buf, buf + 6 * GC);
+    for (;;) {
+      const int wn = w + (int)gridDim.x;
+      const bool more = wn < nw;
+      const int4 nx = more ? W.item[wn] : make_int4(0, 0, 0, 0);
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();  // the current boxes have landed; the other set is no longer read
+      float *Gsm = buf + cur * BOX;
+      if (NB == 2 && more) adj_stage<D>(g, A, nx.x, Tn, buf + (cur ^ 1) * BOX, buf + (cur ^ 1) * BOX + 6 * GC);
+      const int s = it.y;
+      for (long long i = it.z + tid; i < it.w; i += bs)
+        adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Gsm + 6 * GC, emax);
+      if (!more) break;
+      if (NB == 1) {
+        __syncthreads();  // every thread is done with the set before it is restaged
+        adj_stage<D>(g, A, nx.x, Tn, buf, buf + 6 * GC);
+      }
+      it = nx;
+      w = wn;
+      T0[0] = Tn[0];
+      T0[1] = Tn[1];
+      T0[2] = Tn[2];
+      if (NB == 2) cur ^= 1;
     }
-    const int s = it.y;
-    for (long long i = it.z + tid; i < it.w; i += bs) adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Jl, emax);
   }
   // non-negative floats order like their bit patterns
   const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(emax));
@@ -1227,9 +1264,9 @@ void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float
 }
 
 size_t adj_push_smem(int D) {
-  if (D == 1) return sizeof(float) * (6 * Box<1>::GCELLS + 3 * Box<1>::JCELLS);
-  if (D == 2) return sizeof(float) * (6 * Box<2>::GCELLS + 3 * Box<2>::JCELLS);
-  return sizeof(float) * (6 * Box<3>::GCELLS + 3 * Box<3>::JCELLS);
+  if (D == 1) return sizeof(float) * adj_push_bufs(1) * adj_box_floats<1>();
+  if (D == 2) return sizeof(float) * adj_push_bufs(2) * adj_box_floats<2>();
+  return sizeof(float) * adj_push_bufs(3) * adj_box_floats<3>();
 }
 size_t adj_scatter_smem(int D) {
   if (D == 1) return sizeof(unsigned) * 12 * Box<1>::GCELLS;
