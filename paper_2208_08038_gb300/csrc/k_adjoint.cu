@@ -1079,7 +1079,7 @@ __device__ __forceinline__ void scatter_comp(unsigned *A, const int d1[3], const
 template <int D>
 __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWork W) {
   using BX = Box<D>;
-  constexpr int GC = BX::GCELLS, GN = BX::GCOMP;
+  constexpr int GC = BX::GCELLS;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned *A = reinterpret_cast<unsigned *>(smem);  // [6][GC] low words, then [6][GC] high words
   const int tid = threadIdx.x, bs = blockDim.x;
@@ -1090,13 +1090,19 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWor
   frexpf(__uint_as_float(mbits), &ex);  // emax < 2^ex
   const int k = 30 - ex;
   if (blockIdx.x == 0 && tid == 0) *S.kst = k;
+  __shared__ int sbb[6];  // the chunk's body cells (box coordinates): lowest, highest per axis
   for (int q = tid; q < 12 * GC; q += bs) A[q] = 0u;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const int4 it = W.item[w];
     const int t = it.x, s = it.y;
     const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
     const int T0[3] = {tc[0] * Geo<D>::L0, tc[1] * Geo<D>::L1, tc[2] * Geo<D>::L2};
+    if (tid < 3) {
+      sbb[tid] = 1 << 30;
+      sbb[3 + tid] = -(1 << 30);
+    }
     __syncthreads();  // the box is clear (the previous item's flush cleared what it read)
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
     const PartP &P = S.p[s];
     const bool two = S.sp[s].kind == BP_TWO_BODY;
     const long long cap = P.cap, ec = S.ecap[s];
@@ -1124,6 +1130,11 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWor
         f2[a] = fr;
       }
       if (bad) continue;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        lo[a] = min(lo[a], min(d[a], d2[a]));
+        hi[a] = max(hi[a], max(d[a], d2[a]));
+      }
       float e[12];
 #pragma unroll
       for (int q = 0; q < 12; ++q) e[q] = ldexpf(S.eb[s][q * ec + i], k);
@@ -1134,12 +1145,32 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWor
       scatter_comp<D, 5>(A + 4 * GC, d, f, e[4], d2, f2, e[10], two);
       scatter_comp<D, 3>(A + 5 * GC, d, f, e[5], d2, f2, e[11], two);
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int l = __reduce_min_sync(0xFFFFFFFFu, lo[a]), h = __reduce_max_sync(0xFFFFFFFFu, hi[a]);
+      if ((tid & 31) == 0 && l <= h) {
+        atomicMin(&sbb[a], l);
+        atomicMax(&sbb[3 + a], h);
+      }
+    }
     __syncthreads();
     // the box's non-zero nodes into lfx (nodes beyond an open face carry no
-    // field the gather read), each node cleared once read
-    for (int q = tid; q < 6 * GN; q += bs) {
-      const int cc = q / GN, r = q - cc * GN;
-      const int bidx[3] = {r % BX::G0, (r / BX::G0) % BX::G1, r / (BX::G0 * BX::G1)};
+    // field the gather read), each node cleared once read.  A body in cell d
+    // (box coordinates) reaches the nodes d + OG - 1 .. d + OG + 2 along each
+    // axis, so only the chunk's bounding box of those is visited.
+    int b0[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      b0[a] = max(sbb[a] + BX::OG - 1, 0);
+      ext[a] = min(sbb[3 + a] + BX::OG + 2, (a == 0 ? BX::G0 : (a == 1 ? BX::G1 : BX::G2)) - 1) - b0[a] + 1;
+    }
+    const bool none = sbb[0] > sbb[3];
+    __syncthreads();  // every thread has read the bounds: the next item may reset them
+    if (none) continue;  // no body scattered
+    const int nb = ext[0] * ext[1] * ext[2];
+    for (int q = tid; q < 6 * nb; q += bs) {
+      const int cc = q / nb, r = q - cc * nb;
+      const int bidx[3] = {b0[0] + r % ext[0], b0[1] + (r / ext[0]) % ext[1], b0[2] + r / (ext[0] * ext[1])};
       const int si = cc * GC + BX::gi(bidx[0], bidx[1], bidx[2]);
       const unsigned lo = A[si], hi = A[si + 6 * GC];
       if ((lo | hi) == 0u) continue;

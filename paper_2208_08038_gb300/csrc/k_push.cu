@@ -1309,25 +1309,43 @@ __device__ __forceinline__ void push_tile(const GridP &g, const PushArgs &A, con
   int *const qcount = DET ? A.grec_n : nullptr;
   const int qmax = DET ? A.grec_cap : push_qmax(D);
   constexpr int NR0 = qrows<D>(0), NR1 = qrows<D>(1), IPB = NR0 + NR1 + qrows<D>(2);
-  __shared__ int qn;
+  __shared__ int qn, run;
   __shared__ unsigned sbb[6];
   if (tid < 6) sbb[tid] = tid < 3 ? 0xFFFFFFFFu : 0u;
   unsigned blo = 0xFFFFFFFFu, bhi = 0u;
   unsigned pushed = 0;
+  const int lane = tid & 31;
   for (int s = 0; s < A.nsp; ++s) {
-    if (tid == 0) qn = 0;
+    if (tid == 0) {
+      qn = 0;
+      run = 0;
+    }
     __syncthreads();
-    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1];
+    const int beg = A.p[s].tstart[t], end = A.p[s].tstart[t + 1], n = end - beg;
     // in a QS_REST tile the quiet ions of this species have already moved
     const bool moved = qs == QS_REST && A.sp[s].kind == BP_TWO_BODY && A.sp[s].qw1 == -A.sp[s].qw2;
-    // consecutive lanes take consecutive (cell-sorted) particles: their
-    // gather loads share addresses and their state loads coalesce
-    for (long long i = beg + tid; i < end; i += bs) {
-      if (moved && quiet_done(A.p[s], i)) continue;
-      if (i + bs < end) prefetch_particle<D>(A.p[s], i + bs, A.sp[s].kind == BP_TWO_BODY);
-      push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec,
-                                DET ? qcount : &qn, qmax, blo, bhi, nofield, A.far, A.far_n, A.far_cap, s, t);
-      ++pushed;
+    const bool two = A.sp[s].kind == BP_TWO_BODY;
+    // Each warp takes runs of 32 consecutive (cell-sorted) particles from a
+    // shared counter, one lane per particle: the lanes' gather loads share
+    // addresses and their state loads coalesce, and a warp whose particles
+    // took the rare paths does not hold the others at the tile's end.  The
+    // next run is taken before the current one is pushed, so that its
+    // particle can be prefetched.
+    int r = 0;
+    if (lane == 0) r = atomicAdd(&run, 32);
+    r = __shfl_sync(0xFFFFFFFFu, r, 0);
+    while (r < n) {
+      int rn = 0;
+      if (lane == 0) rn = atomicAdd(&run, 32);
+      rn = __shfl_sync(0xFFFFFFFFu, rn, 0);
+      const long long i = beg + r + lane;
+      if (i < end && !(moved && quiet_done(A.p[s], i))) {
+        if (rn + lane < n) prefetch_particle<D>(A.p[s], beg + rn + lane, two);
+        push_particle<D, DET, JT>(g, A.sp[s], A.p[s], i, T0, Gsm, Jsm, A.status, A.jscale, qrec,
+                                  DET ? qcount : &qn, qmax, blo, bhi, nofield, A.far, A.far_n, A.far_cap, s, t);
+        ++pushed;
+      }
+      r = rn;
     }
     __syncthreads();
     if constexpr (DET) continue;  // the records are deposited by k_records
