@@ -1498,7 +1498,7 @@ __global__ void __launch_bounds__(128) k_push_far(GridP g, PushArgs A) {
 template <int D, bool DET>
 void launch_one(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s) {
   cudaMemsetAsync(a.tile_n, 0, sizeof(int), s);
-  const int qt = g.ntiles >= 2048 ? 4 : 1;  // tiles per quiet-pass block
+  const int qt = g.ntiles >= 8192 ? 4 : 1;  // tiles per quiet-pass block
   k_push_quiet<D><<<(g.ntiles + qt - 1) / qt, 128, 0, s>>>(g, a, qt);
   const size_t smem = push_smem_bytes(g, DET);
   // as many persistent blocks as the device holds at once (worked out per
