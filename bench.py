@@ -48,7 +48,7 @@ FLOPS_FULL_ION = 2371
 # every tile (the field and current bytes included, so per ion at this
 # workload's 8 ions per cell) and k_push_quiet ahead of the field.
 TRAFFIC_FULL_ION = 107.4
-TRAFFIC_QUIET_ION = 54.8
+TRAFFIC_QUIET_ION = 54.7
 # the late window starts here: the field has crossed most of the medium
 LATE_START = 450
 UNIT = "ion-pushes/s"
