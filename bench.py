@@ -270,8 +270,8 @@ def run_neutral_1d(steps, warmup):
             "steps": f"{warmup}..{warmup + steps}", "ms_per_step": ms / steps,
             "ion_pushes_per_s": len(sp.x) * steps / (ms * 1e-3), "push_ms_per_launch": push_ms / max(push_n, 1),
             "gpu_launches_per_step": launches / steps, "ms_per_step_launched_directly": ms_direct / steps,
-            "bound": "kernel launches (a few microseconds of work per kernel): each step is two graph "
-                     "launches (the conditional re-sort, then the step's kernels)"}
+            "bound": "kernel launches (a few microseconds of work per kernel): each step is one graph "
+                     "launch (the conditional re-sort, then the step's kernels)"}
 
 
 def run_adjoint_ratio(steps=400, K=20, reps=3):

@@ -882,9 +882,11 @@ int one_step(bp_ctx *c, const PushArgs &A, int nsp, bool probes, float *snap_fie
   return check_launch(c, "step");
 }
 
-// one step through the step graph (step_graph succeeded for the current arguments)
+// one step through the step graph (step_graph succeeded for the current
+// arguments): one launch when the graph holds the re-sort, else two
 int graph_step(bp_ctx *c, int nsp) {
-  launch_resort(c, nsp, c->stream);
+  if (c->step_sorts) c->launches += 1;  // the re-sort's condition kernel
+  else launch_resort(c, nsp, c->stream);
   cudaGraphLaunch(c->step_exec, c->stream);
   step_account(c, true);
   return check_launch(c, "step graph");
@@ -901,8 +903,9 @@ bool step_graph(bp_ctx *c, const PushArgs &A) {
   put(&c->tmaps, sizeof c->tmaps);
   put(&c->g, sizeof c->g);
   put(c->F, sizeof c->F);
-  const void *ptrs[] = {c->jfx, c->jbox, c->occ, c->jbb, c->frame, c->ant, c->clk};
+  const void *ptrs[] = {c->jfx, c->jbox, c->occ, c->jbb, c->frame, c->ant, c->clk, c->sort_runs_dev};
   put(ptrs, sizeof ptrs);
+  put(&c->sb, sizeof c->sb);
   put(&c->det, sizeof c->det);
   put(&c->jinv, sizeof c->jinv);
   if (!c->las.empty()) put(c->las.data(), sizeof(LaserP) * c->las.size());
@@ -930,7 +933,27 @@ bool step_graph(bp_ctx *c, const PushArgs &A) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   cudaGraphExec_t ex = nullptr;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+  // the re-sort's conditional node first, the captured launches after it
+  // (one graph launch per step); else the captured launches alone
+  bool sorts = false;
+  if (e == cudaSuccess && A.nsp > 0 && sort_graph(c)) {
+    SpecP sp[BP_MAX_SPECIES];
+    PartP pp[BP_MAX_SPECIES];
+    int n = 0;
+    for (auto &s : c->sp)
+      if (s.loaded && n < BP_MAX_SPECIES) {
+        sp[n] = s.sp;
+        pp[n] = s.p;
+        ++n;
+      }
+    sorts = make_sort_graph(c->g, n, sp, pp, c->sb, c->status, c->sort_runs_dev, c->cap_stream, &ex, graph) ==
+            cudaSuccess;
+    if (!sorts) {
+      ex = nullptr;
+      cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && !sorts) e = cudaGraphInstantiate(&ex, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     if (ex) cudaGraphExecDestroy(ex);
@@ -938,6 +961,7 @@ bool step_graph(bp_ctx *c, const PushArgs &A) {
     return false;
   }
   c->step_exec = ex;
+  c->step_sorts = sorts;
   c->step_key = key;
   return true;
 }
@@ -952,8 +976,8 @@ int bp_step(bp_ctx *c, int64_t nsteps) {
   int nsp = 0;
   PushArgs A = push_args(c, &nsp);
   sync_clock(c, c->stream);
-  // two or more steps without push timing: the re-sort's graph and the step's
-  // graph per step (the kernels of a step launched by two calls)
+  // two or more steps without push timing: one graph launch per step (the
+  // conditional re-sort, then the step's kernels)
   const bool graph = nsteps >= 2 && !c->timing && step_graph(c, A);
   for (int64_t it = 0; it < nsteps; ++it) {
     int rc;

@@ -128,5 +128,6 @@ struct bp_ctx {
   // with (rebuilt when any of them changes)
   long long *clk = nullptr;
   cudaGraphExec_t step_exec = nullptr;
+  bool step_sorts = false;  // the step graph begins with the conditional re-sort
   std::string step_key;
 };

@@ -467,7 +467,7 @@ void launch_pick(const PartP &p, int D, int two, long long count, const int *sid
                  int *cell_out, float *out, unsigned char *found, cudaStream_t s);
 void launch_set_sort_flag(int *status, cudaStream_t s);
 cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, SortBufs &b, int *status, int *runs,
-                            cudaStream_t cap, cudaGraphExec_t *out);
+                            cudaStream_t cap, cudaGraphExec_t *out, cudaGraph_t tail = nullptr);
 
 void launch_gen_medium(const GridP &g, const SpecP &sp, PartP &p, const int lo[3], const int hi[3], int ppc,
                        uint64_t seed, double sigma, long long first, long long count, cudaStream_t s);

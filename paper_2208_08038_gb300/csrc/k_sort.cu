@@ -412,7 +412,7 @@ void launch_clear_sort_flag(int *status, cudaStream_t s) { k_clear_flag<<<1, 1, 
 // launched on any stream of the context.  Valid while the particle arrays,
 // the sort scratch and the status word keep their addresses.
 cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, SortBufs &b, int *status, int *runs,
-                            cudaStream_t cap, cudaGraphExec_t *out) {
+                            cudaStream_t cap, cudaGraphExec_t *out, cudaGraph_t tail) {
   *out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaGraphCreate(&graph, 0);
@@ -447,6 +447,10 @@ cudaError_t make_sort_graph(const GridP &g, int nsp, const SpecP *sp, PartP *p, 
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cap, &captured);
   }
+  // the rest of a step, when given, after the conditional re-sort (a copy of
+  // the tail graph becomes a child node)
+  cudaGraphNode_t ntail = nullptr;
+  if (e == cudaSuccess && tail) e = cudaGraphAddChildGraphNode(&ntail, graph, &nif, 1, tail);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) *out = nullptr;

@@ -29,20 +29,31 @@ def _same(a, b):
         assert np.array_equal(a[k], b[k]), f"{k}: {np.abs(a[k] - b[k]).max()}"
 
 
+def _hot_3d():
+    """Fast thermal ions that cross tile margins: the conditional re-sort at
+    the head of the step graph runs."""
+    wl = synth.neutral_3d(seed=2, steps=30, n=(48, 16, 16), ppc=4, sigma_u=0.15, margin=2)
+    wl.bc = (0, 0, 0)
+    wl.lasers[0].waist = 0.5 * synth.LAMBDA0
+    wl.lasers[0].yc, wl.lasers[0].zc = 0.5 * 16 * wl.dx[1], 0.5 * 16 * wl.dx[2]
+    wl.lasers[0].a0 = 0.05
+    return wl
+
+
 def _workloads():
     w1 = synth.neutral_1d(steps=60)
     w2 = synth.refraction_2d(n=(64, 48), steps=40)
-    return [("1d", w1, 60, 60), ("2d", w2, 40, 25)]
+    return [("1d", w1, 60, 60), ("2d", w2, 40, 25), ("3d", _hot_3d(), 30, 30)]
 
 
-@pytest.mark.parametrize("name,wl,steps,cap", _workloads(), ids=["1d", "2d"])
+@pytest.mark.parametrize("name,wl,steps,cap", _workloads(), ids=["1d", "2d", "3d-resorting"])
 def test_graph_steps_match_direct_steps(name, wl, steps, cap):
     """step(n) (graph replays) against n x step(1) (direct launches), with
     the probe's capacity below the step count in 2D."""
     n_probe = [len(sp.x) for sp in wl.species]
     a, sa, pa = gpu_from_workload(wl, probe_cap=cap)
     b, sb, pb = gpu_from_workload(wl, probe_cap=cap)
-    if pa is None:  # a line of E_z nodes across the 2D box
+    if pa is None:  # a line of E_z nodes across the box
         nodes = np.array([20 + wl.n[0] * j for j in range(wl.n[1])], dtype=np.int64)
         pa, pb = a.add_probe(2, nodes, cap), b.add_probe(2, nodes, cap)
     a.step(steps)
@@ -53,6 +64,9 @@ def test_graph_steps_match_direct_steps(name, wl, steps, cap):
     sa_, sb_ = _state(a, sa, pa, n_probe), _state(b, sb, pb, n_probe)
     assert sa_["probe"].shape[0] == min(steps, cap)
     _same(sa_, sb_)
+    # both paths count the same kernels, re-sorts that ran included (the
+    # single-step path has one more clock set per call)
+    assert a.kernel_launches() + (steps - 1) == b.kernel_launches()
     a.close()
     b.close()
 
