@@ -5,8 +5,11 @@ dx = lambda/16, 8 two-body ions per cell over x cells [4, 508) (y, z
 periodic, x open), thermal momenta sigma = 1e-3, omega_b = 3, n_b = 0.02 n_c,
 a0 = 1e-3 Gaussian pulse with waist 6 lambda: 264,241,152 ions.  A step is the
 whole hot path: re-sort check, B half step, gather + internal force + Boris
-+ drift + Esirkepov deposit, current-box sum with the antenna, B half step,
-E step with Mur faces.
++ drift + Esirkepov deposit (sorted mode: into the 64-bit fixed-point
+current), the antenna sheet, B half step, E step (J formed from the
+fixed-point current) with Mur faces.  Also reported: the end-to-end rate
+through the C ABI from pinned host arrays, the 2D Bragg crystal, the 1D
+medium and the adjoint's cost on the 2D adjoint workload.
 
 Metric: two-body ion pushes per second (ions x steps / time), whole job.
 One JSON line on rank 0.  Multi-GPU: independent replicas (the step is not

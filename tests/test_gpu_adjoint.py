@@ -85,8 +85,8 @@ def test_checkpoint_interval_does_not_change_gradients(case):
 
 def test_gradients_bit_exact_rerun(case):
     """The adjoint's only cross-particle sums are the field-adjoint scatter
-    (64-bit fixed point), the tile-box sum and the FP64 reductions (fixed
-    order): two runs give identical gradients."""
+    and its per-cell accumulation (64-bit fixed point, integer adds) and the
+    FP64 reductions (fixed order): two runs give identical gradients."""
     wl, steps, groups, target, probe_o, *_ = case
     out = []
     for _ in range(2):
