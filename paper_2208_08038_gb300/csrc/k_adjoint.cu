@@ -18,6 +18,14 @@
 
 namespace {
 
+// 2^k as two factors 2^(k/2) and 2^(k - k/2), each a normal float for
+// |k| <= 252: x * f.x * f.y scales by 2^k exactly while x 2^k is a normal
+// float (and the intermediate lies between x and the result)
+__device__ __forceinline__ float2 pow2_split(int k) {
+  const int a = k / 2, b = k - a;
+  return make_float2(__int_as_float((127 + a) << 23), __int_as_float((127 + b) << 23));
+}
+
 int blocks_for(long long n, int bs) {
   long long b = (n + bs - 1) / bs;
   long long cap = 152LL * 16;
@@ -1089,6 +1097,7 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWor
   int ex;
   frexpf(__uint_as_float(mbits), &ex);  // emax < 2^ex
   const int k = 30 - ex;
+  const float2 sk = pow2_split(k);  // the fixed-point scale 2^k
   if (blockIdx.x == 0 && tid == 0) *S.kst = k;
   __shared__ int sbb[6];  // the chunk's body cells (box coordinates): lowest, highest per axis
   for (int q = tid; q < 12 * GC; q += bs) A[q] = 0u;
@@ -1137,7 +1146,7 @@ __global__ void __launch_bounds__(256) k_adj_scatter(GridP g, ScatArgs S, AdjWor
       }
       float e[12];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) e[q] = ldexpf(S.eb[s][q * ec + i], k);
+      for (int q = 0; q < 12; ++q) e[q] = S.eb[s][q * ec + i] * sk.x * sk.y;
       scatter_comp<D, 1>(A + 0 * GC, d, f, e[0], d2, f2, e[6], two);
       scatter_comp<D, 2>(A + 1 * GC, d, f, e[1], d2, f2, e[7], two);
       scatter_comp<D, 4>(A + 2 * GC, d, f, e[2], d2, f2, e[8], two);
@@ -1224,7 +1233,7 @@ __global__ void __launch_bounds__(256) k_adj_fxsum(GridP g, unsigned long long *
   __syncthreads();  // every thread has read the mark before it is cleared
   if (!mine) return;
   float *out[6] = {E0, E1, E2, B0, B1, B2};
-  const int k = *kst;
+  const float2 sk = pow2_split(-*kst);  // back from the fixed-point scale
   constexpr int L0 = Geo<D>::L0, L1 = Geo<D>::L1, L2 = Geo<D>::L2;
   const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
   for (int q = tid; q < L0 * L1 * L2; q += blockDim.x) {
@@ -1236,7 +1245,7 @@ __global__ void __launch_bounds__(256) k_adj_fxsum(GridP g, unsigned long long *
       const long long v = (long long)*p;
       if (v == 0) continue;
       *p = 0ull;
-      out[cc][cell] += ldexpf(__ll2float_rn(v), -k);
+      out[cc][cell] += __ll2float_rn(v) * sk.x * sk.y;
     }
   }
   if (tid == 0) dirty[t] = 0;
