@@ -191,7 +191,11 @@ int bp_add_probe(bp_ctx *ctx, int comp, const int64_t *nodes, int64_t npts, int6
  * q_{1,2} v_{1,2} / dV added to the total current that updates the fields;
  * Sec. 3.1 -- Maxwell's equations with the vacuum permittivity.  Returns
  * BP_ERR_ARG for n_steps < 0; kernel problems (a particle off its tile's
- * reach, a non-finite momentum) surface at the next bp_sync. */
+ * reach, a non-finite momentum) surface at the next bp_sync.  With two or
+ * more steps and push timing off, the steps replay a CUDA graph of one step
+ * (captured on first use and again whenever a launch argument has changed:
+ * particle arrays, lasers, probes, parameters); single steps and timed steps
+ * launch the same kernels directly, with the same results bit for bit. */
 int bp_step(bp_ctx *ctx, int64_t n_steps);
 
 /* Wait for the stream and return the device status word as a bp_status:
@@ -361,7 +365,8 @@ int bp_backward(bp_ctx *ctx, int probe_id, const float *dl_dprobe, int species_i
 int64_t bp_kernel_launches(const bp_ctx *ctx);
 
 /* Per-kernel CUDA-event timing of the push/deposit launches: when enabled,
- * bp_step records events around each push launch; bp_push_time returns
+ * bp_step records events around each push launch (and launches directly,
+ * not through the step graph); bp_push_time returns
  * the summed milliseconds and launch count since the last reset (bp_time_push
  * resets both, and the work counters of bp_push_work).  (The paper has no
  * counterpart; instrumentation.) */
