@@ -325,14 +325,20 @@ __device__ __forceinline__ void boris_adj(float h, const float E[3], const float
   }
 }
 
-// Gather transposed, part 1 (here): the derivative of a gathered component
-// with respect to the body position, e * d/dX sum_ijk w_i w_j w_k g_ijk,
-// written in factored form (sum_i dw_i sum_jk w_j w_k g_ijk, and the same
-// along y and z).  Part 2, the scatter of e w into the field adjoints, is
-// the separate kernel k_adj_scatter (fixed point, exact and order-free).
+// Gather transposed, part 1: the derivatives of the gathered fields with
+// respect to the bodies' positions, taken with the forward recompute (the
+// field adjoints that weight them come later, from the Boris transpose).
+// Part 2, the scatter of e w into the field adjoints, is the separate kernel
+// k_adj_scatter (fixed point, exact and order-free).
+//
+// One gathered component (stagger PAT) at one body, with its derivatives
+// with respect to the body's position (in cells) along each simulated axis:
+// the value by the forward gather's arithmetic (the same contractions in the
+// same order: x, then y, then z), the derivatives from the same node loads
+// with the weights' derivatives in place of the weights along one axis.
 template <int D, int PAT>
-__device__ __forceinline__ void gather_deriv_comp(const float *__restrict__ G, const int d[3], const float f[3], float e,
-                                                  float X[3]) {
+__device__ __forceinline__ float gather_vd(const float *__restrict__ G, const int d[3], const float f[3],
+                                           float dv[3]) {
   int b[3];
   float w[3][3], dw[3][3];
 #pragma unroll
@@ -354,81 +360,59 @@ __device__ __forceinline__ void gather_deriv_comp(const float *__restrict__ G, c
       dw[a][2] = 0.5f + xi;
     } else {
       b[a] = 0;
+      w[a][0] = 1.0f;
+      w[a][1] = w[a][2] = 0.0f;
+      dw[a][0] = dw[a][1] = dw[a][2] = 0.0f;
     }
   }
-  if constexpr (D == 1) {
-    float dx = 0.0f;
+  constexpr int NJ = D >= 2 ? 3 : 1, NK = D >= 3 ? 3 : 1;
+  float sa = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dx = fmaf(dw[0][i], G[Box<D>::gi(b[0] + i, 0, 0)], dx);
-    X[0] += e * dx;
-  } else if constexpr (D == 2) {
-    float c[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f};
+  for (int k = 0; k < NK; ++k) {
+    float pa = 0.0f, px = 0.0f, py = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float v = G[Box<D>::gi(b[0] + i, b[1] + j, 0)];
-        c[i] = fmaf(w[1][j], v, c[i]);
-        r[j] = fmaf(w[0][i], v, r[j]);
-      }
-    float dx = 0.0f, dy = 0.0f;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      dx = fmaf(dw[0][m], c[m], dx);
-      dy = fmaf(dw[1][m], r[m], dy);
-    }
-    X[0] += e * dx;
-    X[1] += e * dy;
-  } else {
-    // s_ij = sum_k w_k g_ijk, t_ij = sum_k dw_k g_ijk
-    float c[3] = {0.0f, 0.0f, 0.0f}, r[3] = {0.0f, 0.0f, 0.0f}, u[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
+    for (int j = 0; j < NJ; ++j) {
+      const float *row = G + Box<D>::gi(b[0], b[1] + j, b[2] + k);
+      float ra = 0.0f, rd = 0.0f;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        float sij = 0.0f, tij = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float v = G[Box<D>::gi(b[0] + i, b[1] + j, b[2] + k)];
-          sij = fmaf(w[2][k], v, sij);
-          tij = fmaf(dw[2][k], v, tij);
-        }
-        c[i] = fmaf(w[1][j], sij, c[i]);
-        r[j] = fmaf(w[0][i], sij, r[j]);
-        u[i] = fmaf(w[1][j], tij, u[i]);
+        const float v = row[i];
+        ra = fmaf(w[0][i], v, ra);
+        rd = fmaf(dw[0][i], v, rd);
       }
-    float dx = 0.0f, dy = 0.0f, dz = 0.0f;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      dx = fmaf(dw[0][m], c[m], dx);
-      dy = fmaf(dw[1][m], r[m], dy);
-      dz = fmaf(w[0][m], u[m], dz);
+      pa = fmaf(w[1][j], ra, pa);
+      px = fmaf(w[1][j], rd, px);
+      py = fmaf(dw[1][j], ra, py);
     }
-    X[0] += e * dx;
-    X[1] += e * dy;
-    X[2] += e * dz;
+    sa = fmaf(w[2][k], pa, sa);
+    sx = fmaf(w[2][k], px, sx);
+    sy = fmaf(w[2][k], py, sy);
+    sz = fmaf(dw[2][k], pa, sz);
   }
+  dv[0] = sx;
+  dv[1] = sy;
+  dv[2] = sz;
+  return sa;
 }
 
+// the six components at one body (E_x, E_y, E_z, B_x, B_y, B_z), their
+// derivatives to the thread's slice of shared memory: component q, axis a
+// at dst[(q D + a) * stride]
 template <int D>
-__device__ __forceinline__ void gather_deriv_all(const float *G, const int d1[3], const float f1[3], const float Eb1[3],
-                                                 const float Bb1[3], float X1[3], const int d2[3], const float f2[3],
-                                                 const float Eb2[3], const float Bb2[3], float X2[3], bool two) {
+__device__ __forceinline__ void gather_vd_body(const float *G, const int d[3], const float f[3], float E[3], float B[3],
+                                               float *dst, int stride) {
   constexpr int gc = Box<D>::GCELLS;
-  gather_deriv_comp<D, 1>(G + 0 * gc, d1, f1, Eb1[0], X1);
-  gather_deriv_comp<D, 2>(G + 1 * gc, d1, f1, Eb1[1], X1);
-  gather_deriv_comp<D, 4>(G + 2 * gc, d1, f1, Eb1[2], X1);
-  gather_deriv_comp<D, 6>(G + 3 * gc, d1, f1, Bb1[0], X1);
-  gather_deriv_comp<D, 5>(G + 4 * gc, d1, f1, Bb1[1], X1);
-  gather_deriv_comp<D, 3>(G + 5 * gc, d1, f1, Bb1[2], X1);
-  if (two) {
-    gather_deriv_comp<D, 1>(G + 0 * gc, d2, f2, Eb2[0], X2);
-    gather_deriv_comp<D, 2>(G + 1 * gc, d2, f2, Eb2[1], X2);
-    gather_deriv_comp<D, 4>(G + 2 * gc, d2, f2, Eb2[2], X2);
-    gather_deriv_comp<D, 6>(G + 3 * gc, d2, f2, Bb2[0], X2);
-    gather_deriv_comp<D, 5>(G + 4 * gc, d2, f2, Bb2[1], X2);
-    gather_deriv_comp<D, 3>(G + 5 * gc, d2, f2, Bb2[2], X2);
-  }
+  float dv[3];
+  auto put = [&](int q) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) dst[(q * D + a) * stride] = dv[a];
+  };
+  E[0] = gather_vd<D, 1>(G + 0 * gc, d, f, dv); put(0);
+  E[1] = gather_vd<D, 2>(G + 1 * gc, d, f, dv); put(1);
+  E[2] = gather_vd<D, 4>(G + 2 * gc, d, f, dv); put(2);
+  B[0] = gather_vd<D, 6>(G + 3 * gc, d, f, dv); put(3);
+  B[1] = gather_vd<D, 5>(G + 4 * gc, d, f, dv); put(4);
+  B[2] = gather_vd<D, 3>(G + 5 * gc, d, f, dv); put(5);
 }
 
 // Esirkepov transposed on a window of W nodes per axis (W = 3: every
@@ -658,7 +642,7 @@ struct AdjArgs {
 
 template <int D>
 __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, AdjState &S, long long i,
-                             const int T0[3], const float *Gsm, const float *Jl, float &emax) {
+                             const int T0[3], const float *Gsm, const float *Jl, float *stash, float &emax) {
   const long long cap = P.cap;
   const bool two = sp.kind == BP_TWO_BODY;
   const int cell = P.cell[i];
@@ -701,14 +685,13 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
     atomicOr(S.status, ST_DOMAIN);
     return;
   }
-  // forward recompute
-  float E1[3], B1[3], E2[3], B2[3];
-  {
-    Loc L1, L2;
-    make_loc<D>(d, f, L1);
-    make_loc<D>(two ? d2 : d, two ? f2 : f, L2);
-    gather_all<D>(Gsm, L1, L2, E1, B1, E2, B2);
-  }
+  // forward recompute: the gathered fields, and their derivatives with
+  // respect to the bodies' positions kept in the thread's slice of shared
+  // memory for the gather's transpose below
+  float E1[3], B1[3], E2[3] = {0.0f, 0.0f, 0.0f}, B2[3] = {0.0f, 0.0f, 0.0f};
+  float *dvs = stash + threadIdx.x;
+  gather_vd_body<D>(Gsm, d, f, E1, B1, dvs, blockDim.x);
+  if (two) gather_vd_body<D>(Gsm, d2, f2, E2, B2, dvs + 6 * D * blockDim.x, blockDim.x);
   float ac = 0.0f, rr = 1.0f, s3 = 0.0f;
   if (two) {
     const int pi = P.pidx ? P.pidx[i] : 0;
@@ -851,7 +834,19 @@ __device__ void adj_particle(const GridP &g, const SpecP &sp, const PartP &P, Ad
   // gather transposed: position derivatives here, the field-adjoint scatter
   // by k_adj_scatter from the stored Eb, Bb; old positions through the deposit
   float Xg1[3] = {0, 0, 0}, Xg2[3] = {0, 0, 0};
-  gather_deriv_all<D>(Gsm, d, f, Eb1, Bb1, Xg1, d2, f2, Eb2, Bb2, Xg2, two);
+  {
+    const float e1[6] = {Eb1[0], Eb1[1], Eb1[2], Bb1[0], Bb1[1], Bb1[2]};
+    const float e2[6] = {Eb2[0], Eb2[1], Eb2[2], Bb2[0], Bb2[1], Bb2[2]};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int a = 0; a < D; ++a) Xg1[a] += e1[q] * dvs[(q * D + a) * blockDim.x];
+    if (two)
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+#pragma unroll
+        for (int a = 0; a < D; ++a) Xg2[a] += e2[q] * dvs[((6 + q) * D + a) * blockDim.x];
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     S.eb[(0 + a) * sc + i] = Eb1[a];
@@ -968,6 +963,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
   constexpr int GC = BX::GCELLS, NB = adj_push_bufs(D), BOX = adj_box_floats<D>();
   extern __shared__ __align__(16) unsigned char smem[];
   float *buf = reinterpret_cast<float *>(smem);  // NB x [E^n, B^n (6 GC) | J adjoint (3 JC)]
+  float *stash = buf + NB * BOX;                 // [12 D][blockDim]: the gather's position derivatives
   const int tid = threadIdx.x, bs = blockDim.x;
   const int nw = min(*W.n, W.cap);
   float emax = 0.0f;
@@ -985,7 +981,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 1 : 2) k_adj_push(GridP g, AdjAr
       if (NB == 2 && more) adj_stage<D>(g, A, nx.x, Tn, buf + (cur ^ 1) * BOX, buf + (cur ^ 1) * BOX + 6 * GC);
       const int s = it.y;
       for (long long i = it.z + tid; i < it.w; i += bs)
-        adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Gsm + 6 * GC, emax);
+        adj_particle<D>(g, A.sp[s], A.p[s], A.st[s], i, T0, Gsm, Gsm + 6 * GC, stash, emax);
       if (!more) break;
       if (NB == 1) {
         __syncthreads();  // every thread is done with the set before it is restaged
@@ -1303,10 +1299,12 @@ void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float
   else k_adj_b<3><<<nb, 128, 0, s>>>(g, lamE[0], lamE[1], lamE[2], lamB[0], lamB[1], lamB[2], h, z0, z1, z2);
 }
 
+// box sets, then the 256 threads' slices of gather derivatives (12 D floats each)
 size_t adj_push_smem(int D) {
-  if (D == 1) return sizeof(float) * adj_push_bufs(1) * adj_box_floats<1>();
-  if (D == 2) return sizeof(float) * adj_push_bufs(2) * adj_box_floats<2>();
-  return sizeof(float) * adj_push_bufs(3) * adj_box_floats<3>();
+  const size_t stash = sizeof(float) * 12 * (size_t)D * 256;
+  if (D == 1) return sizeof(float) * adj_push_bufs(1) * adj_box_floats<1>() + stash;
+  if (D == 2) return sizeof(float) * adj_push_bufs(2) * adj_box_floats<2>() + stash;
+  return sizeof(float) * adj_push_bufs(3) * adj_box_floats<3>() + stash;
 }
 size_t adj_scatter_smem(int D) {
   if (D == 1) return sizeof(unsigned) * 12 * Box<1>::GCELLS;
