@@ -409,7 +409,10 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(our_config(n_ion, "oracle", world, args.warmup, args.steps), sample=sample),
+            "data": "synthetic", "config": dict(our_config(n_ion, "oracle", world, args.warmup, args.steps), sample=sample,
+                                                          timed=f"{args.steps} steps of the sample after "
+                                                                f"{args.warmup} untimed ones (every ion "
+                                                                "takes the oracle's full step)"),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
