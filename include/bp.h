@@ -381,6 +381,15 @@ int bp_push_time(bp_ctx *ctx, double *ms, int64_t *launches);
  * enabled; synchronous.  (The paper has no counterpart; instrumentation.) */
 int bp_push_work(bp_ctx *ctx, int64_t *full, int64_t *quiet);
 
+/* Work of the field updates since the last call: *active_tiles receives the
+ * tiles the field kernels updated, summed over the steps (on grids of 1024
+ * tiles or more they skip tiles whose neighbourhood has never held a field
+ * and receives no current: their E, B and J stay exactly zero), *steps the
+ * steps counted; the count restarts at zero.  Smaller grids update every
+ * tile and count nothing.  Synchronous.  (The paper has no counterpart;
+ * instrumentation.) */
+int bp_field_work(bp_ctx *ctx, int64_t *active_tiles, int64_t *steps);
+
 /* (The paper has no counterpart: a resource limit of this implementation.)
  * Capacity of the sorted deposit's general-case record buffer, in records
  * (BP_DEPOSIT_SORTED only).  A particle whose positions change their nearest

@@ -96,6 +96,7 @@ _SIGS = {
     "bp_read_field_async": (_i, [_p, _i, _p]),
     "bp_push_time": (_i, [_p, C.POINTER(_d), C.POINTER(_i64)]),
     "bp_push_work": (_i, [_p, C.POINTER(_i64), C.POINTER(_i64)]),
+    "bp_field_work": (_i, [_p, C.POINTER(_i64), C.POINTER(_i64)]),
 }
 
 
@@ -384,3 +385,12 @@ class Context:
         quiet = C.c_int64()
         self._check(self._L.bp_push_work(self._h, C.byref(full), C.byref(quiet)), "bp_push_work")
         return full.value, quiet.value
+
+    def field_work(self):
+        """(tiles the field kernels updated, summed over the steps; steps
+        counted) since the last call (bp_field_work; zero on grids of fewer
+        than 1024 tiles, where every tile is updated)."""
+        tiles = C.c_int64()
+        steps = C.c_int64()
+        self._check(self._L.bp_field_work(self._h, C.byref(tiles), C.byref(steps)), "bp_field_work")
+        return tiles.value, steps.value

@@ -2,6 +2,7 @@
 // split and a_c mapping of arXiv 2208.08038 Sec. 2 / Sec. 3.1, initial
 // conditions of Sec. 2), and the step schedule on the caller's stream.
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -93,6 +94,8 @@ void refresh_marks(bp_ctx *c) {
   const float *F[6] = {c->F[0], c->F[1], c->F[2], c->F[3], c->F[4], c->F[5]};
   launch_field_marks(c->g, F, c->stream);
   c->launches += 1;
+  // every tile active until the next push recomputes the flags
+  if (c->act) cudaMemsetAsync(c->act, 1, (size_t)c->g.ntiles, c->stream);
 }
 
 void update_jscale(bp_ctx *c) {
@@ -305,12 +308,20 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
     c->ant = (double *)dalloc(c, sizeof(double) * BP_MAX_LASER * (size_t)(ncell / g.n[0]));
     c->grec_n = (int *)dalloc(c, sizeof(int));
     c->far_n = (int *)dalloc(c, sizeof(int));
+    c->far_any = (int *)dalloc(c, sizeof(int));
   }
   else c->jbox = (float *)dalloc(c, sizeof(float) * 3 * (size_t)g.jcells * g.ntiles);
   c->occ = (unsigned char *)dalloc(c, g.ntiles);
   c->jbb = (uint2 *)dalloc(c, sizeof(uint2) * g.ntiles);
   g.fnz = (unsigned char *)dalloc(c, g.ntiles);  // zero fields: no tile marked
   c->qstate = (unsigned char *)dalloc(c, g.ntiles);
+  // the field kernels' active tiles (all, until the first push has run):
+  // on small grids the flag's kernel would cost more than the tiles it skips
+  if (g.ntiles >= 1024) {
+    c->act = (unsigned char *)dalloc(c, g.ntiles);
+    c->act_n = (unsigned long long *)dalloc(c, 2 * sizeof(unsigned long long));
+    if (c->act) cudaMemsetAsync(c->act, 1, (size_t)g.ntiles, c->stream);
+  }
   c->tile_ctr = (int *)dalloc(c, sizeof(int));
   c->tile_list = (int *)dalloc(c, sizeof(int) * g.ntiles);
   c->tile_n = (int *)dalloc(c, sizeof(int));
@@ -319,8 +330,8 @@ int bp_create(const bp_grid_desc *gd, const bp_allocator *al, void *stream, bp_c
   c->clk = (long long *)dalloc(c, sizeof(long long) * kClockWords);
   long long nf = frame_floats(g);
   c->frame = nf ? (float *)dalloc(c, sizeof(float) * nf) : nullptr;
-  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n || !c->far_n)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
-      !c->work || !c->clk || (nf && !c->frame)) {
+  if (!(c->det ? (void *)c->jfx : (void *)c->jbox) || (c->det && (!c->ant || !c->grec_n || !c->far_n || !c->far_any)) || !c->tile_ctr || !c->tile_list || !c->tile_n || !c->occ || !c->jbb || !g.fnz || !c->qstate || !c->status ||
+      !c->work || !c->clk || (g.ntiles >= 1024 && (!c->act || !c->act_n)) || (nf && !c->frame)) {
     bp_destroy(c);
     return BP_ERR_OOM;
   }
@@ -676,6 +687,7 @@ PushArgs push_args(bp_ctx *c, int *nsp_out) {
   A.far = c->far;
   A.far_n = c->far_n;
   A.far_cap = (int)c->far_cap;
+  A.far_any = c->far_any;
   A.grec_cap = (int)c->grec_cap;
   A.occ = c->occ;
   A.jbb = c->jbb;
@@ -824,7 +836,7 @@ void step_launches(bp_ctx *c, const PushArgs &A, bool probes, cudaStream_t st, f
   const GridP &g = c->g;
   float *E[3] = {c->F[0], c->F[1], c->F[2]}, *B[3] = {c->F[3], c->F[4], c->F[5]}, *J[3] = {c->F[6], c->F[7], c->F[8]};
   const float *cE[3] = {E[0], E[1], E[2]}, *cB[3] = {B[0], B[1], B[2]};
-  launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+  launch_yee_b(g, B, cE, 0.5f * g.dt, c->act, st);
   if (snap_fields) {
     CopyList L;
     for (int k = 0; k < 6; ++k) cl_add(c, L, c->F[k], snap_fields + (size_t)k * g.ncell, sizeof(float) * g.ncell);
@@ -849,9 +861,17 @@ void step_launches(bp_ctx *c, const PushArgs &A, bool probes, cudaStream_t st, f
     c->ev_used += 2;
   }
   if (!c->det) launch_jsum(g, c->jbox, c->occ, c->jbb, J, c->las.data(), (int)c->las.size(), c->clk, st);
-  launch_yee_b(g, B, cE, 0.5f * g.dt, st);
+  if (c->act) {
+    int ia_lo = INT_MAX, ia_hi = INT_MIN;
+    for (auto &L : c->las) {
+      ia_lo = std::min(ia_lo, L.ia);
+      ia_hi = std::max(ia_hi, L.ia);
+    }
+    launch_tile_active(g, c->qstate, c->far_any, ia_lo, ia_hi, c->act, c->act_n, st);
+  }
+  launch_yee_b(g, B, cE, 0.5f * g.dt, c->act, st);
   launch_yee_e(g, E, cB, J, c->frame, c->det ? c->jfx : nullptr, c->jinv, c->las.data(), (int)c->las.size(), c->clk,
-               c->ant, st);
+               c->ant, c->act, st);
   if (probes)
     for (size_t p = 0; p < c->pr.size(); ++p)
       launch_probe(c->F[c->pr[p].comp], c->pr[p].nodes, c->pr[p].npts, c->pr[p].buf, c->clk, (int)p, st);
@@ -864,7 +884,7 @@ void step_account(bp_ctx *c, bool probes) {
   for (int a = 0; a < c->g.D; ++a) nopen += c->g.bc[a] == BP_OPEN;
   // quiet-tile pass, push, records (sorted) or current sum (atomic), antenna (sorted, with lasers),
   // Yee (3), Mur, the clock
-  c->launches += (c->det ? 6 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0) + 1;
+  c->launches += (c->det ? 6 + (c->las.empty() ? 0 : 1) : 6) + (nopen ? 1 + nopen : 0) + 1 + (c->act ? 1 : 0);
   c->step++;
   if (probes)
     for (auto &p : c->pr) {
@@ -1498,6 +1518,18 @@ int bp_push_work(bp_ctx *c, int64_t *full, int64_t *quiet) {
   return BP_OK;
 }
 
+int bp_field_work(bp_ctx *c, int64_t *active_tiles, int64_t *steps) {
+  if (!c) return BP_ERR_ARG;
+  unsigned long long w[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && c->act_n) e = cudaMemcpy(w, c->act_n, sizeof w, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && c->act_n) e = cudaMemset(c->act_n, 0, sizeof w);
+  if (e != cudaSuccess) return cuda_fail(c, e, "field work");
+  if (active_tiles) *active_tiles = (int64_t)w[0];
+  if (steps) *steps = (int64_t)w[1];
+  return BP_OK;
+}
+
 int bp_push_time(bp_ctx *c, double *ms, int64_t *launches) {
   if (!c) return BP_ERR_ARG;
   if (ms) *ms = c->push_ms;
@@ -1517,6 +1549,7 @@ int bp_reset(bp_ctx *c) {
   cudaStream_t st = c->stream;
   for (int k = 0; k < 9; ++k) cudaMemsetAsync(c->F[k], 0, sizeof(float) * c->g.ncell, st);
   cudaMemsetAsync(c->g.fnz, 0, (size_t)c->g.ntiles, st);
+  if (c->act) cudaMemsetAsync(c->act, 1, (size_t)c->g.ntiles, st);
   if (c->jfx) cudaMemsetAsync(c->jfx, 0, sizeof(unsigned long long) * 3 * (size_t)c->g.ncell, st);
   cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st);
   c->step = 0;

@@ -77,12 +77,15 @@ struct bp_ctx {
   int *grec_n = nullptr;             // their count (device, cleared after each step)
   int4 *far = nullptr;               // sorted deposit: ions with a far bound electron, moved after the push
   int *far_n = nullptr;              // their count (device, cleared after each step)
+  int *far_any = nullptr;            // whether the last push moved any (device)
   long long far_cap = 0;
   long long grec_cap = 0;
   long long grec_fixed = 0;          // capacity set by the caller (0: default)
   unsigned char *occ = nullptr;
   uint2 *jbb = nullptr;
   unsigned char *qstate = nullptr;  // per tile: left by the quiet-tile pass for the push
+  unsigned char *act = nullptr;     // per tile: updated by the field kernels (grids of 1024 tiles or more)
+  unsigned long long *act_n = nullptr;  // [2]: active tiles summed over steps, steps (see bp_field_work)
   int *tile_ctr = nullptr;           // the push's tile counter
   int *tile_list = nullptr;          // tiles left for the push by the quiet-tile pass, and their number
   int *tile_n = nullptr;

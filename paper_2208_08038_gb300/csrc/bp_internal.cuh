@@ -144,6 +144,7 @@ struct PushArgs {
   int4 *far;                // sorted deposit: two-body ions whose bound electron is a cell or more away,
   int *far_n;               //   (species, particle, tile), moved after the push by k_push_far; their count
   int far_cap;
+  int *far_any;             // set by k_push_far when it moved any this step (their current may land anywhere)
   int push_blocks;          // persistent push blocks for this grid on this device
   int sms;                  // multiprocessors of the device
 };
@@ -418,12 +419,17 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t k
 
 void launch_push(const GridP &g, const PushArgs &a, const TmaMaps &tm, cudaStream_t s);
 size_t push_smem_bytes(const GridP &g, int det);
-size_t push_record_bytes();  // one general-case deposit record
+size_t push_record_bytes();
+// the tiles the field kernels update (see k_tile_active); ia_lo..ia_hi: the antenna planes' x range
+void launch_tile_active(const GridP &g, const unsigned char *qstate, const int *far_any, int ia_lo, int ia_hi,
+                        unsigned char *act, unsigned long long *act_n, cudaStream_t s);  // one general-case deposit record
 // set the push kernel's shared-memory limit for this grid and return, in
 // *blocks, the number of push blocks resident on the current device at once
 int push_prepare(const GridP &g, int det, int *blocks);
 
-void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s);
+// act (per tile, optional): tiles to update; the others keep zero E, B, J
+void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, const unsigned char *act,
+                  cudaStream_t s);
 // recompute the tile marks (g.fnz) from E, B (F[0..5]) after a write from outside the step
 void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s);
 // E <- E + dt (curl B - J).  With jfx (sorted deposit) the current is first
@@ -433,7 +439,7 @@ void launch_field_marks(const GridP &g, const float *const F[6], cudaStream_t s)
 // without it J is read as the current sum left it.
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
                   unsigned long long *jfx, float jinv, const LaserP *las, int nlas, const long long *clk,
-                  double *ant, cudaStream_t s);
+                  double *ant, const unsigned char *act, cudaStream_t s);
 long long frame_floats(const GridP &g);
 void launch_jsum(const GridP &g, const float *jbox, const unsigned char *occ, const uint2 *jbb, float *const J[3],
                  const LaserP *las, int nlas, const long long *clk, cudaStream_t s);

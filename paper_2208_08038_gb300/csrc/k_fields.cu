@@ -61,9 +61,11 @@ __device__ __forceinline__ void mark_nonzero4(const GridP &g, const int c[3], bo
 // B <- B - h curl E (forward differences to the B locations)
 template <int D>
 __global__ void __launch_bounds__(128) k_yee_b(GridP g, float *Bx, float *By, float *Bz, const float *__restrict__ Ex,
-                                               const float *__restrict__ Ey, const float *__restrict__ Ez, float h) {
+                                               const float *__restrict__ Ey, const float *__restrict__ Ez, float h,
+                                               const unsigned char *__restrict__ act) {
   Cell4 C;
   if (!row_cell4<D>(g, C)) return;
+  if (act && !act[tile_of(g, C.c)]) return;  // E and B zero around the tile: B stays zero
   const long long q = C.q;
   const float4 ex = ld4(Ex + q), ey = ld4(Ey + q), ez = ld4(Ez + q);
   const float eyn = Ey[q + C.up[0]], ezn = Ez[q + C.up[0]];  // x neighbours of the last cell
@@ -209,9 +211,11 @@ template <int D, bool FX>
 __global__ void __launch_bounds__(128) k_yee_e(GridP g, float *Ex, float *Ey, float *Ez, const float *__restrict__ Bx,
                                                const float *__restrict__ By, const float *__restrict__ Bz, float *Jx,
                                                float *Jy, float *Jz, unsigned long long *jfx, float jinv,
-                                               AntSet as, const double *__restrict__ ant) {
+                                               AntSet as, const double *__restrict__ ant,
+                                               const unsigned char *__restrict__ act) {
   Cell4 C;
   if (!row_cell4<D>(g, C)) return;
+  if (act && !act[tile_of(g, C.c)]) return;  // no field and no current around the tile: E stays zero
   const long long q = C.q;
   float4 jx, jy, jz;
   if constexpr (FX) {
@@ -591,16 +595,17 @@ long long frame_floats(const GridP &g) {
   return t;
 }
 
-void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, cudaStream_t s) {
+void launch_yee_b(const GridP &g, float *const B[3], const float *const E[3], float h, const unsigned char *act,
+                  cudaStream_t s) {
   const int nb = row_blocks4(g, 128);
-  if (g.D == 1) k_yee_b<1><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
-  else if (g.D == 2) k_yee_b<2><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
-  else k_yee_b<3><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h);
+  if (g.D == 1) k_yee_b<1><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h, act);
+  else if (g.D == 2) k_yee_b<2><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h, act);
+  else k_yee_b<3><<<nb, 128, 0, s>>>(g, B[0], B[1], B[2], E[0], E[1], E[2], h, act);
 }
 
 void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], float *const J[3], float *frame,
                   unsigned long long *jfx, float jinv, const LaserP *las, int nlas, const long long *clk,
-                  double *ant, cudaStream_t s) {
+                  double *ant, const unsigned char *act, cudaStream_t s) {
   long long nf = frame_floats(g);
   if (nf) k_frame_save<<<grid_blocks(nf, 256), 256, 0, s>>>(g, E[0], E[1], E[2], frame, nf);
   const int nb = row_blocks4(g, 128);
@@ -623,7 +628,7 @@ void launch_yee_e(const GridP &g, float *const E[3], const float *const B[3], fl
     else k_antenna<3><<<grid_blocks(nant, 64), 64, 0, s>>>(g, ls, clk, ant);
   }
 #define YEE_E(DD, FF) \
-  k_yee_e<DD, FF><<<nb, 128, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant)
+  k_yee_e<DD, FF><<<nb, 128, 0, s>>>(g, E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], jfx, jinv, as, ant, act)
   if (jfx) {
     if (g.D == 1) YEE_E(1, true);
     else if (g.D == 2) YEE_E(2, true);

@@ -1120,6 +1120,46 @@ __global__ void __launch_bounds__(128, 8) k_push_quiet(GridP g, PushArgs A, int 
   if (A.work) count_work(A.work + 1, moved);
 }
 
+// Tiles whose cells the field updates can change: a tile of the 3^D
+// neighbourhood has held a non-zero E or B (the sticky marks), or holds
+// particles the push moved this step (QS_PUSH, QS_REST: their current reaches
+// the neighbouring tiles), or an antenna plane lies within one tile of it.
+// Elsewhere E, B and J are zero and the Yee updates keep them exactly zero,
+// so the field kernels skip those tiles.  Computed after the push; it serves
+// that step's field updates and the next step's first B half step, over
+// which fields spread by at most three cells, less than one tile.
+template <int D>
+__global__ void k_tile_active(GridP g, const unsigned char *qstate, const int *far_any, int ia_lo, int ia_hi,
+                              unsigned char *act, unsigned long long *act_n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) atomicAdd(act_n + 1, 1ull);  // the steps counted
+  bool a = false;
+  if (t < g.ntiles) {
+    const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
+    const int x0 = tc[0] * Geo<D>::L0;
+    // a far bound electron deposits at its own position: every tile then
+    a = (far_any && *far_any) || (ia_hi >= x0 - Geo<D>::L0 && ia_lo < x0 + 2 * Geo<D>::L0);
+    for (int o = 0; o < 27 && !a; ++o) {
+      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      bool use = true;
+      int nb[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        nb[k] = tc[k] + off[k];
+        if (k >= D) use &= off[k] == 0;
+        else if (g.bc[k] == BP_PERIODIC) nb[k] = wrap_once(nb[k], g.nt[k]);
+        else use &= nb[k] >= 0 && nb[k] < g.nt[k];
+      }
+      if (!use) continue;
+      const int u = nb[0] + g.nt[0] * (nb[1] + g.nt[1] * nb[2]);
+      a = g.fnz[u] != 0 || qstate[u] != QS_DONE;
+    }
+    act[t] = a ? 1 : 0;
+  }
+  const unsigned k = __reduce_add_sync(0xFFFFFFFFu, a ? 1u : 0u);
+  if ((threadIdx.x & 31u) == 0 && k) atomicAdd(act_n, (unsigned long long)k);
+}
+
 // byte offset of the field box in the push's dynamic shared memory (after the
 // current box, 128-byte aligned for the TMA loads)
 __host__ __device__ constexpr size_t push_gbox_offset(int D, bool det) {
@@ -1484,6 +1524,7 @@ __global__ void __launch_bounds__(256) k_records(GridP g, const QRec *__restrict
 template <int D>
 __global__ void __launch_bounds__(128) k_push_far(GridP g, PushArgs A) {
   const int n = min(*A.far_n, A.far_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.far_any) *A.far_any = n > 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int4 e = A.far[k];
     const int t = e.z;
@@ -1542,6 +1583,14 @@ size_t push_smem_bytes(const GridP &g, int det) {
 }
 
 size_t push_record_bytes() { return sizeof(QRec); }
+
+void launch_tile_active(const GridP &g, const unsigned char *qstate, const int *far_any, int ia_lo, int ia_hi,
+                        unsigned char *act, unsigned long long *act_n, cudaStream_t s) {
+  const int nb = (g.ntiles + 255) / 256;
+  if (g.D == 1) k_tile_active<1><<<nb, 256, 0, s>>>(g, qstate, far_any, ia_lo, ia_hi, act, act_n);
+  else if (g.D == 2) k_tile_active<2><<<nb, 256, 0, s>>>(g, qstate, far_any, ia_lo, ia_hi, act, act_n);
+  else k_tile_active<3><<<nb, 256, 0, s>>>(g, qstate, far_any, ia_lo, ia_hi, act, act_n);
+}
 
 int push_prepare(const GridP &g, int det, int *blocks) {
   switch (g.D * 2 + (det ? 1 : 0)) {

@@ -176,18 +176,25 @@ def test_neutral_3d_full_gauss_and_bit_exact_rerun():
 # the 2D Bragg crystal on its full 2048^2 grid
 
 def test_bragg_2d_full_grid_parity():
+    """Full grid (16,384 tiles: the field kernels skip the tiles the beam has
+    not reached): element by element against the oracle, in the relative L2
+    of E and B and in the largest difference against the largest value, while
+    the beam crosses the grid."""
     wl = synth.bragg_2d()
     ora, osid, _ = oracle_from_workload(wl, probe_cap=1)
     gpu, gsid, _ = gpu_from_workload(wl, probe_cap=1)
-    out = []
+    out, worst = [], []
     done = 0
-    for s in (1, 120):
+    for s in (1, 120, 300):
         ora.step(s - done)
         gpu.step(s - done)
         gpu.sync()
         done = s
-        out.append(field_rel_l2(gpu.fields(), ora.fields()))
-    assert out[0] < 1e-5 and out[1] < 1e-3, out
+        g, o = gpu.fields(), ora.fields()
+        out.append(field_rel_l2(g, o))
+        worst.append(float(np.abs(g[:6] - o[:6]).max() / np.abs(o[:6]).max()))
+    assert out[0] < 1e-5 and out[1] < 1e-3 and out[2] < 1e-3, out
+    assert max(worst) < 1e-4, worst
     x1o, _, u1o, _ = ora.bodies(osid[0])
     x1g, _, u1g, _ = gpu.read_particles(gsid[0], len(x1o))
     assert np.abs(x1g - x1o).max() < 1e-5 * wl.dx[0]
