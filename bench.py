@@ -50,7 +50,7 @@ FLOPS_FULL_ION = 2371
 # (128x64x64 cells, 3,932,160 ions; one launch each): k_push with a field in
 # every tile (the field and current bytes included, so per ion at this
 # workload's 8 ions per cell) and k_push_quiet ahead of the field.
-TRAFFIC_FULL_ION = 107.4
+TRAFFIC_FULL_ION = 108.1
 TRAFFIC_QUIET_ION = 54.7
 # the late window starts here: the field has crossed most of the medium
 LATE_START = 450
