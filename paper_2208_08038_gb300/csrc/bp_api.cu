@@ -726,7 +726,7 @@ int copy_alloc(bp_ctx *c, const PartP &src, int D, bool two, PartP &dst) {
 // batched device-to-device copies (one kernel per up to 32 arrays)
 void cl_flush(bp_ctx *c, CopyList &L) {
   if (L.n) {
-    launch_copy_many(L, c->stream);
+    launch_copy_many(L, c->sms, c->stream);
     c->launches++;
     L.n = 0;
   }

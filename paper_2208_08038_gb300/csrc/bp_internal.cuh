@@ -493,7 +493,7 @@ struct CopyList {
   void *dst[MAX];
   long long words[MAX];
 };
-void launch_copy_many(const CopyList &L, cudaStream_t s);
+void launch_copy_many(const CopyList &L, int sms, cudaStream_t s);
 // zero (optional): three arrays cleared on the way
 void launch_adj_b(const GridP &g, float *lamE[3], float *lamB[3], float h, float *zero[3], cudaStream_t s);
 size_t adj_push_smem(int D);

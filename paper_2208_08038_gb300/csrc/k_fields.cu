@@ -684,12 +684,13 @@ __global__ void k_copy_many(CopyList L) {
   for (long long i = 4 * nv + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
 }
 
-void launch_copy_many(const CopyList &L, cudaStream_t s) {
+void launch_copy_many(const CopyList &L, int sms, cudaStream_t s) {
   if (L.n <= 0) return;
   long long most = 0;
   for (int k = 0; k < L.n; ++k) most = most > L.words[k] ? most : L.words[k];
   long long bx = (most / 4 + 255) / 256;
-  bx = bx < 1 ? 1 : (bx > 152 * 8 ? 152 * 8 : bx);
+  const long long cap = 8LL * (sms > 0 ? sms : 1);  // grid-stride: any count >= 1 covers the copy
+  bx = bx < 1 ? 1 : (bx > cap ? cap : bx);
   k_copy_many<<<dim3((unsigned)bx, (unsigned)L.n), 256, 0, s>>>(L);
 }
 
