@@ -7,9 +7,15 @@
 //       pass first) + k_adj_e (gathers curl^T of the interior adjoint, J adjoint)
 //   B^{n+1/2} = B^n - dt/2 curl E^n                          ->  k_adj_b
 //   per particle: Esirkepov deposit, drift, Boris, internal modified-Coulomb
-//       field (arXiv 2208.08038 Sec. 2), gather              ->  k_adj_push
-//       (the deposit's transpose reads the current adjoint like a gather; the
-//       gather's transpose scatters like a deposit, into a shared-memory box)
+//       field (arXiv 2208.08038 Sec. 2), gather              ->  k_adj_work
+//       (the step's list of 256-ion chunks of the occupied tiles), k_adj_push
+//       (recompute of the push; the deposit's transpose reads the current
+//       adjoint like a gather; Boris, force and drift transposes; the
+//       gather's position derivatives; stores each ion's gathered-field
+//       adjoints), k_adj_scatter (the gather's transpose: those adjoints
+//       scattered like a deposit into a 64-bit fixed-point box per chunk,
+//       added into a per-cell accumulator), k_adj_fxsum (the accumulator
+//       converted once and added to the field adjoints, then cleared)
 //   B^n = B^{n-1/2} - dt/2 curl E^n                          ->  k_adj_b
 // The particle adjoints are indexed by load order, so re-sorting between
 // steps does not disturb them.
@@ -26,14 +32,13 @@ __device__ __forceinline__ float2 pow2_split(int k) {
   return make_float2(__int_as_float((127 + a) << 23), __int_as_float((127 + b) << 23));
 }
 
+// blocks for n items; the kernels launched with it are grid-stride loops, so
+// the cap (two waves of 256-thread blocks on 152 SMs) only bounds the grid
 int blocks_for(long long n, int bs) {
   long long b = (n + bs - 1) / bs;
   long long cap = 152LL * 16;
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
-
-
-
 
 __device__ __forceinline__ bool ext(const GridP &g, int pat, const int c[3]) {
   bool e = false;

@@ -3,9 +3,12 @@
 // first-order Mur open faces, the laser antenna, the current (sorted deposit:
 // formed in the E update from the 64-bit fixed-point accumulator; atomic
 // deposit: the fixed-order sum of the per-tile boxes), the tile marks of
-// non-zero fields, and probes.  All FP32, memory bound: the Yee updates take
-// four consecutive x cells per thread (16-byte vector loads and stores,
-// coalesced along x); the other kernels one cell per thread.
+// non-zero fields, the device step clock (step number and probe sample
+// counts, so a step's launches are the same every step), and probes.  All
+// FP32, memory bound: the Yee updates take four consecutive x cells per
+// thread (16-byte vector loads and stores, coalesced along x) and return at
+// once in tiles the per-step activity flags mark inactive (E, B and J are
+// zero there and would stay zero); the other kernels one cell per thread.
 #include "bp_internal.cuh"
 
 namespace {
@@ -580,6 +583,8 @@ __global__ void k_clock_set(long long *clk, ClockState v) {
   }
 }
 
+// blocks for n items; the kernels launched with it are grid-stride loops, so
+// the cap (two waves of 256-thread blocks on 152 SMs) only bounds the grid
 int grid_blocks(long long n, int bs) {
   long long b = (n + bs - 1) / bs;
   long long cap = 152LL * 16;

@@ -24,7 +24,13 @@
 //        for the current-sum kernel (and deposit the records from a
 //        shared-memory queue before that),
 //   k_records     sorted mode: the records' rows added to the fixed-point
-//                 current.
+//                 current,
+//   k_push_far    sorted mode: the ions k_push left on the far list (a bound
+//                 electron a cell or more from its nucleus), pushed with the
+//                 global fields and deposited as one-body records,
+//   k_tile_active the tiles the field kernels update this step: those whose
+//                 neighbourhood has held a field or holds moved particles,
+//                 those next to an antenna plane, every tile after a far push.
 #include <type_traits>
 
 #include "bp_internal.cuh"

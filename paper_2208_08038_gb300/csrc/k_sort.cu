@@ -10,6 +10,8 @@ constexpr int SCAN_BS = 1024;
 constexpr int SCAN_PER = 4;                 // elements per thread
 constexpr int SCAN_TILE = SCAN_BS * SCAN_PER;
 
+// blocks for n items; the kernels launched with it are grid-stride loops, so
+// the cap (two waves of 256-thread blocks on 152 SMs) only bounds the grid
 int blocks_for(long long n, int bs, long long cap = 152LL * 16) {
   long long b = (n + bs - 1) / bs;
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
