@@ -122,23 +122,29 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if f[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        sm.sort()
-        med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi's CSV lines (ClockSampler.FIELDS, no header, no units)."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for k, nm in enumerate(names):
+            if f[5 + k].lower().startswith("active"):
+                reasons.add(nm)
+    sm.sort()
+    med = sm[len(sm) // 2] if sm else None
+    return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def cpu_baseline_neutral_3d(seconds_target: float = 10.0):
@@ -210,6 +216,14 @@ def run_e2e(wl, n_ion, mode, steps, rank, world, dist=None):
 BRAGG_BYTES_CELL = 168  # per cell and step: 2 B half steps (36 B), E step (72 B), clearing the current (24 B)
 
 
+def updated_cells(act_tiles, act_steps, ncell, ntiles, steps):
+    """Cells the field kernels updated over `steps` steps: the device's count
+    of active tiles (summed over the steps it flagged) times the cells of a
+    tile, or every cell every step on a grid that keeps no flags (fewer than
+    1,024 tiles: act_steps = 0)."""
+    return act_tiles * (ncell // ntiles) if act_steps else ncell * steps
+
+
 def run_bragg(steps, warmup):
     """The 2D Bragg crystal (2048^2 cells, dx = lambda/32, 40 x 40 sites of
     4 two-body ions, 30-degree p-polarised beam): grid cells advanced per
@@ -241,7 +255,7 @@ def run_bragg(steps, warmup):
     ctx.close()
     ncell = wl.n[0] * wl.n[1]
     ntiles = ncell // (wl.tile[0] * wl.tile[1])
-    cells = act_tiles * (ncell // ntiles) if act_steps else ncell * steps
+    cells = updated_cells(act_tiles, act_steps, ncell, ntiles, steps)
     hbm, src = peaks()
     gbs = BRAGG_BYTES_CELL * cells / (ms * 1e-3) / 1e9
     return {"workload": "bragg_2d: 2048x2048 cells, dx=lambda/32, 6400 two-body ions on a 40x40 lattice, "
@@ -360,11 +374,40 @@ def our_config(n_ion, mode, world, warmup, steps, n=(512, 256, 256)):
             "l2": f"inputs larger than L2 (particles {n_ion * 52 / 1e9:.3g} GB)", "parallelism": f"replicas x{world}"}
 
 
-def fp32_peak_tflops(sm_mhz):
+def fp32_peak_tflops(sm_mhz, sms=None):
     """FP32 non-tensor peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
-    import torch
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def push_roofline(full, quiet, launches, push_ms, ncell, hbm, hbm_src, sm_max, sms=None):
+    """Roofline of the push launch (k_push_quiet + k_push + k_records) over a
+    timed window: `full` and `quiet` are the device-counted full pushes and
+    quiet drifts of the window's `launches` push launches, `push_ms` their
+    summed CUDA-event time.  FP32 operations (the binding roof) from the full
+    pushes only; algorithmic bytes from both kinds of work plus the per-cell
+    field and current bytes; traffic from ncu's DRAM bytes per ion of each
+    kernel (small 3D case)."""
+    per = max(launches, 1)
+    avg_ms = push_ms / per
+    alg = (full * BYTES_FULL_ION + quiet * BYTES_QUIET_ION) / per + ncell * BYTES_CELL
+    flops = full * FLOPS_FULL_ION / per
+    achieved_gbs = alg / (avg_ms * 1e-3) / 1e9
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    fp32_peak, sms = fp32_peak_tflops(sm_max, sms)
+    traffic = None
+    if TRAFFIC_FULL_ION is not None and TRAFFIC_QUIET_ION is not None:
+        traffic = (full * TRAFFIC_FULL_ION + quiet * TRAFFIC_QUIET_ION) / per
+    return {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved_tf / fp32_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "window": "late", "kernel": "push launch: k_push_quiet<3> + k_push<3,sorted> + k_records<3>",
+            "peak_source": f"FP32 lanes: {sms} SMs x 128 x 2 flops x {sm_max:.0f} MHz (max SM clock)",
+            "flops_per_full_push": FLOPS_FULL_ION,
+            "limiter": "instruction issue (ncu on the small 3D case with a field in every tile)",
+            "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                    "bytes_per_launch": alg, "peak_source": hbm_src}}
 
 
 def timed_window(ctx, steps, stream, time_push=True):
@@ -537,15 +580,8 @@ def main():
     # full pushes
     per = max(lpush_n, 1)
     lpush_avg = lpush_ms / per
-    alg = (lfull * BYTES_FULL_ION + lquiet * BYTES_QUIET_ION) / per + ncell * BYTES_CELL
-    flops = lfull * FLOPS_FULL_ION / per
-    achieved_gbs = alg / (lpush_avg * 1e-3) / 1e9
-    achieved_tf = flops / (lpush_avg * 1e-3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    fp32_peak, sms = fp32_peak_tflops(sm_max)
-    traffic = None
-    if TRAFFIC_FULL_ION is not None and TRAFFIC_QUIET_ION is not None:
-        traffic = (lfull * TRAFFIC_FULL_ION + lquiet * TRAFFIC_QUIET_ION) / per
+    roofline = push_roofline(lfull, lquiet, lpush_n, lpush_ms, ncell, hbm, src, sm_max)
     push_avg0 = push_ms / max(push_n, 1)
     value = units / (ms * 1e-3)
     line = {
@@ -559,14 +595,7 @@ def main():
                  "value": lunits / (lms_job * 1e-3), "unit": UNIT, "push_ms_per_launch": lpush_avg,
                  "full_pushes_per_launch": lfull / per, "quiet_per_launch": lquiet / per,
                  "full_fraction": lfull / max(lfull + lquiet, 1), "gpu_launches": llaunch},
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp32_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                     "window": "late", "kernel": "push launch: k_push_quiet<3> + k_push<3,sorted> + k_records<3>",
-                     "peak_source": f"FP32 lanes: {sms} SMs x 128 x 2 flops x {sm_max:.0f} MHz (max SM clock)",
-                     "flops_per_full_push": FLOPS_FULL_ION,
-                     "limiter": "instruction issue (ncu on the small 3D case with a field in every tile)",
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                             "bytes_per_launch": alg, "peak_source": src}},
+        "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,
