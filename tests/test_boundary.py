@@ -72,3 +72,56 @@ def test_entry_points_reject_a_null_context(libpath):
             assert out == err_arg, name
             checked += 1
     assert checked >= 25
+
+
+def _grid(dims, n, dx, dt, tile=(0, 0, 0), boundary=(0, 0, 0)):
+    g = binding.GridDesc()
+    g.dims = dims
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+        g.dx[a] = dx[a] if a < len(dx) else 1.0
+        g.boundary[a] = boundary[a]
+        g.tile[a] = tile[a]
+    g.dt = dt
+    g.deposit_mode = binding.BP_DEPOSIT_SORTED
+    return g
+
+
+@pytest.mark.parametrize("desc, code", [
+    (_grid(0, (64,), (1.0,), 0.5), binding.BP_ERR_ARG),                        # no such dimension
+    (_grid(4, (64,) * 3, (1.0,) * 3, 0.5), binding.BP_ERR_ARG),
+    (_grid(1, (3,), (1.0,), 0.5), binding.BP_ERR_ARG),                         # fewer than 4 cells
+    (_grid(1, (64,), (0.0,), 0.5), binding.BP_ERR_ARG),                        # zero cell size
+    (_grid(1, (24,), (1.0,), 0.5), binding.BP_ERR_ARG),                        # not whole 16-cell tiles
+    (_grid(2, (64, 64), (1.0, 1.0), 0.5, tile=(8, 16, 0)), binding.BP_ERR_ARG),  # a tile other than 16 x 16
+    (_grid(1, (64,), (1.0,), 0.0), binding.BP_ERR_CFL),                        # dt = 0
+    (_grid(1, (64,), (1.0,), 1.0), binding.BP_ERR_CFL),                        # c dt = dx
+    (_grid(2, (64, 64), (1.0, 1.0), 0.75), binding.BP_ERR_CFL),                # 0.75 sqrt(2) > 1
+    (_grid(3, (2048, 1024, 1024), (1.0,) * 3, 0.5), binding.BP_ERR_ARG),      # 2^31 cells
+    (_grid(3, (1032, 1032, 1032), (1.0,) * 3, 0.5), binding.BP_ERR_ARG),      # cell index needs 33 bits
+])
+def test_create_rejects_a_bad_grid_before_any_cuda_call(libpath, desc, code):
+    """bp_create checks the grid description (dimensions, sizes, tile shape,
+    the Courant limit c dt sqrt(sum 1/dx^2) < 1 of the Yee scheme, the 31-bit
+    cell index) before it touches the device, so these run without a GPU."""
+    L = binding.lib()
+    out = ctypes.c_void_p(1234)
+    rc = L.bp_create(ctypes.byref(desc), None, None, ctypes.byref(out))
+    assert rc == code
+    assert out.value is None  # *out is cleared and set only on BP_OK
+
+
+def test_create_rejects_null_pointers(libpath):
+    L = binding.lib()
+    out = ctypes.c_void_p()
+    g = _grid(1, (64,), (1.0,), 0.5)
+    assert L.bp_create(None, None, None, ctypes.byref(out)) == binding.BP_ERR_ARG
+    assert L.bp_create(ctypes.byref(g), None, None, None) == binding.BP_ERR_ARG
+
+
+def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the library missing the binding raises."""
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libbp.so"))
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        binding.lib()
